@@ -1,0 +1,175 @@
+/*
+ * mfgb.h -- C ABI of libmfgb.so: the frequency-domain matched filter of
+ * Chung, Wen, Blair, Cannon & Datta (arXiv:0906.4175) on one GB300 (sm_103a).
+ *
+ * Equations are numbered in order of appearance in the paper:
+ *   (1) z(t) = x(t) + i y(t) = 4 int_0^inf h~_c(f) s~*(f) / S_n(f) e^{2 pi i f t} df
+ *   (2) S_n(f), the initial-LIGO noise PSD, f0 = 150 Hz
+ *   (3) rho(t) = |z(t)| / sigma
+ *   (4) sigma^2 = 4 int_0^inf |h~_c(f)|^2 / S_n(f) df
+ * Templates (Sec. 1.1): 2PN stationary-phase phase, Newtonian amplitude,
+ * band f_low .. min(Nyquist, f_isco).  The integrals are Riemann sums over the
+ * bins k of an N-sample segment: f_k = k df, df = fs/N.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MF_OK (0) or one of the MF_E* codes below; nothing aborts
+ *    and nothing throws.  mf_last_error() gives a message for the calling
+ *    thread's last failure.
+ *  - "device" pointers are CUDA device (or managed) memory on the current
+ *    device; "host" pointers are ordinary host memory.  The caller owns every
+ *    pointer it passes in; handles own the device memory they allocate and
+ *    free it in their destroy call.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Work
+ *    is queued on it asynchronously; device outputs are valid once the stream
+ *    has synchronised.  Host inputs are consumed before the call returns.
+ *  - All kernels are hand-written CUDA for sm_103a; there is no CPU fallback.
+ */
+#ifndef MFGB_H
+#define MFGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MF_OK        0
+#define MF_EINVAL    1  /* bad argument: N not a power of two in range, m <= 0, NaN, f_low >= f_cut, ... */
+#define MF_ENOMEM    2  /* a device or host allocation failed */
+#define MF_ECUDA     3  /* a CUDA runtime call failed (message has the CUDA error string) */
+#define MF_EOVERFLOW 4  /* more triggers than trig_cap: the stored ones are a subset, *n_trig is the true count */
+#define MF_ETIMEOUT  5  /* a bounded device-side wait ran out; the launch's outputs are invalid */
+#define MF_ENOTSUP   6  /* a mode or size this build does not implement */
+
+typedef struct mf_bank_s *mf_bank;
+typedef struct mf_segment_s *mf_segment;
+
+/* Template-bank parameters (Sec. 1.1). */
+typedef struct {
+    double f_low;     /* low-frequency cut-off in Hz (the paper uses 40) */
+    int pn_order;     /* phase order in half-PN steps; only 4 (= 2PN, the paper's choice) */
+    int amp_order;    /* amplitude order; only 0 (Newtonian, the paper's choice) */
+    int phase_mode;   /* MF_PHASE_* below */
+    int fft_mode;     /* MF_FFT_FP32 (only mode in this build) */
+} mf_bank_params;
+
+#define MF_PHASE_ANCHOR 0  /* default: Psi in FP64 at anchor bins, reduced mod 2 pi, FP32 cubic Taylor between them */
+#define MF_PHASE_FP64   1  /* Psi in FP64 at every bin (anchor spacing 1) */
+#define MF_PHASE_FP32   2  /* Psi in FP32 only, no FP64 reduction (precision-sweep reference; loses accuracy) */
+#define MF_FFT_FP32     0
+
+/* Per-(template, segment) peak: the argmax over j of rho_j (lowest j on ties). */
+typedef struct {
+    float rho;        /* rho at the peak, Eq. (3) */
+    int32_t j;        /* sample index of the peak in z (literal Eq. 1: a signal coalescing at
+                         sample j0 peaks at j = (N - j0) mod N) */
+    float z_re, z_im; /* z_j = x + i y at the peak, Eq. (1), amplitude constant A = Mc^(5/6) */
+} mf_peak;
+
+/* One sample with rho_j > threshold. */
+typedef struct {
+    int32_t tmpl;     /* template index in the bank */
+    int32_t seg;      /* index into the segs[] array of the mf_filter_bank call */
+    int32_t j;        /* sample index */
+    float rho;
+    float z_re, z_im;
+} mf_trigger;
+
+/* A frequency-domain injection for mf_synth_segment. */
+typedef struct {
+    double m1, m2;    /* component masses, solar masses */
+    double snr;       /* optimal SNR the injection is scaled to */
+    int64_t j0;       /* time shift in samples: h(t - j0 dt) */
+    double phi;       /* constant phase added to the injection */
+} mf_injection;
+
+/* Message for the calling thread's last failure ("" if none). */
+const char *mf_last_error(void);
+/* Library version string. */
+const char *mf_version(void);
+
+/* mf_bank_create -- per-template constants for Sec. 1.1's templates.
+ * m1, m2: host arrays of n > 0 component masses in solar masses (> 0, finite).
+ * params: host; NULL means f_low = 40, 2PN, Newtonian, MF_PHASE_ANCHOR, MF_FFT_FP32.
+ * Computes in FP64 on the host the 2PN phase coefficients, f_isco and the
+ * amplitude constant of each template and copies them to the device.
+ * *out receives the handle (free with mf_bank_destroy).
+ * Errors: MF_EINVAL (n <= 0, bad mass, unsupported order), MF_ENOMEM, MF_ECUDA. */
+int mf_bank_create(const double *m1, const double *m2, int64_t n,
+                   const mf_bank_params *params, mf_bank *out);
+int mf_bank_destroy(mf_bank bank);
+/* Number of templates (host out). */
+int mf_bank_size(mf_bank bank, int64_t *n);
+
+/* mf_segment_upload -- data conditioning for Eq. (1), once per segment.
+ * s: N float32 samples of s(t) at rate fs (device if s_on_device, else host).
+ * N: power of two, 2^10 <= N <= 2^22.  fs > 0.
+ * psd: NULL -> Eq. (2) with f0 = psd_f0 and overall scale psd_S0 (the paper
+ *      prints no scale; S0 = 1 gives whitened units, rho does not depend on it);
+ *      else a host array of N/2+1 FP64 values S_k at f_k = k fs/N (> 0).
+ * Queues on cuda_stream: the forward FFT s~_k = dt sum s_n e^{-2 pi i n k/N},
+ * the weighting W_k = f_k^(-7/6) conj(s~_k)/S_k (scaled so that rho is O(1) for
+ * any PSD scale) and the FP64 prefix table of f^(-7/3)/S_k that gives sigma^2
+ * of Eq. (4) for any band in O(1).  *out owns that device memory.
+ * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+int mf_segment_upload(const float *s, int64_t N, double fs, const double *psd,
+                      double psd_f0, double psd_S0, int s_on_device, void *cuda_stream,
+                      mf_segment *out);
+int mf_segment_destroy(mf_segment seg);
+/* Segment length and sample rate (host outs; either may be NULL). */
+int mf_segment_info(mf_segment seg, int64_t *N, double *fs);
+
+/* mf_filter_bank -- Eqs. (1), (3), (4) for every (template, segment) pair.
+ * For template t and segment s (segs[s]), with the band of Sec. 1.1:
+ *   z_j = 4 df sum_band h~_k conj(s~_k)/S_k e^{+2 pi i j k/N},  rho_j = |z_j|/sigma.
+ * Writes peaks[t * n_seg + s] (device array of n_templates * n_seg) and every
+ * sample with rho_j > threshold to trig (device array of trig_cap records),
+ * sorted by (tmpl, seg, j).  *n_trig (device int64) receives the true count,
+ * also when it exceeds trig_cap.  Neither h~(f) nor z(t) is stored.
+ * segs: host array of n_seg >= 1 handles.  The call queues work on
+ * cuda_stream and returns; mf_bank_check() reports overflow and device-side
+ * timeouts of the last call on this bank.
+ * The first call for a given (segment length, bank size, trig_cap) allocates
+ * the bank's workspace; later calls allocate nothing.
+ * Errors: MF_EINVAL (f_low >= f_cut for some pair, bad sizes), MF_ENOMEM, MF_ECUDA. */
+int mf_filter_bank(mf_bank bank, const mf_segment *segs, int n_seg, float threshold,
+                   mf_peak *peaks, mf_trigger *trig, int64_t trig_cap, int64_t *n_trig,
+                   void *cuda_stream);
+
+/* mf_bank_check -- synchronises cuda_stream, then returns MF_OK, MF_EOVERFLOW
+ * (the last mf_filter_bank on this bank found more than trig_cap triggers) or
+ * MF_ETIMEOUT (a bounded device-side wait of that call expired). */
+int mf_bank_check(mf_bank bank, void *cuda_stream);
+
+/* mf_synth_segment -- seeded synthetic data: stationary Gaussian noise
+ * coloured by S_n (Eq. 2, or psd) plus frequency-domain injections, the
+ * stand-in for the paper's coloured-noise test data (Sec. 3).
+ *   s~_k = noise_scale sqrt(T S_k / 4)(g_{2k} + i g_{2k+1}) for k_lo <= k < N/2
+ *          (k_lo = ceil(f_low N/fs): the data are high-passed at f_low),
+ *   s~_k += (snr/sigma_i) h~_i,k e^{-2 pi i k j0_i/N} e^{i phi_i} on injection i's band,
+ *   s_n = 2 df Re sum_k s~_k e^{+2 pi i n k/N}.
+ * g: device array of 2*(N/2) FP64 standard normals.  inj: host array of n_inj
+ * records (may be NULL if n_inj = 0).  s_out: device array of N float32.
+ * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+int mf_synth_segment(const double *g, int64_t N, double fs, double f_low, const double *psd,
+                     double psd_f0, double psd_S0, const mf_injection *inj, int64_t n_inj,
+                     double noise_scale, float *s_out, void *cuda_stream);
+
+/* mf_refine_triggers -- objective and adjoint for gradient refinement.
+ * For each i < n with theta[i] = (m1, m2, t) (device FP64 [n][3], t in
+ * seconds) evaluates the Eq. (1) sum directly at continuous t,
+ *   z(t) = 4 df sum_band h~_k(m1, m2) conj(s~_k)/S_k e^{2 pi i f_k t},
+ * obj[i] = rho^2 = |z(t)|^2 / sigma^2 (Eqs. 3-4) and the analytic gradient
+ * grad[i] = d obj / d(m1, m2, t) (device FP64 [n][3]).  The band of each row is
+ * band[2i], band[2i+1] (device int64 [n][2], half-open bins) when band is not
+ * NULL, else the Sec. 1.1 band at that row's masses; it is held fixed while
+ * differentiating.  params: as for mf_bank_create (NULL = defaults).
+ * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, const double *theta,
+                       int64_t n, const int64_t *band, double *obj, double *grad,
+                       void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFGB_H */

@@ -1,0 +1,234 @@
+"""GB300-native frequency-domain matched filter of arXiv:0906.4175.
+
+For each template (m1, m2) of a bank and each data segment the library forms
+Eq. (1)  z(t) = 4 int h~_c(f) s~*(f)/S_n(f) e^{2 pi i f t} df  with the 2PN
+stationary-phase template (Sec. 1.1), Eq. (3) rho = |z|/sigma with Eq. (4)
+sigma^2 = 4 int |h~_c|^2/S_n df, the per-segment argmax and every sample
+above threshold -- all in hand-written sm_103a CUDA behind the C ABI of
+include/mfgb.h.  This module only marshals arguments: PyTorch supplies device
+memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import (INJ_DTYPE, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
+                      MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
+
+__all__ = ["Bank", "Segment", "filter_bank", "synth_segment", "refine", "RefineFn", "MFError",
+           "PEAK_DTYPE", "TRIG_DTYPE", "INJ_DTYPE", "MF_PHASE_ANCHOR", "MF_PHASE_FP64", "MF_PHASE_FP32",
+           "peaks_to_numpy", "triggers_to_numpy", "version"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def version() -> str:
+    return _native.lib().mf_version().decode()
+
+
+def params(f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR, pn_order: int = 4,
+           amp_order: int = 0, fft_mode: int = MF_FFT_FP32) -> BankParams:
+    return BankParams(f_low, pn_order, amp_order, phase_mode, fft_mode)
+
+
+class Bank:
+    """mf_bank_create: template constants for masses m1, m2 (solar masses)."""
+
+    def __init__(self, m1, m2, f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR):
+        m1 = np.ascontiguousarray(m1, dtype=np.float64)
+        m2 = np.ascontiguousarray(m2, dtype=np.float64)
+        if m1.shape != m2.shape or m1.ndim != 1:
+            raise ValueError("m1 and m2 must be 1-D arrays of the same length")
+        self.params = params(f_low, phase_mode)
+        h = ctypes.c_void_p()
+        L = _native.lib()
+        check(L.mf_bank_create(m1.ctypes.data, m2.ctypes.data, m1.size, ctypes.byref(self.params),
+                               ctypes.byref(h)))
+        self._h = h
+        self.n = int(m1.size)
+        self.m1, self.m2 = m1, m2
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, stream=None) -> int:
+        """mf_bank_check: sync and return MF_OK / MF_EOVERFLOW (raises on timeout)."""
+        return check(_native.lib().mf_bank_check(self._h, _stream_ptr(stream)), allow=(MF_EOVERFLOW,))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.lib().mf_bank_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Segment:
+    """mf_segment_upload: s (torch float32 tensor on cuda, or numpy float32 on host)."""
+
+    def __init__(self, s, fs: float, psd=None, psd_f0: float = 150.0, psd_S0: float = 1.0, stream=None):
+        torch = _torch()
+        on_dev = isinstance(s, torch.Tensor) and s.is_cuda
+        if on_dev:
+            if s.dtype != torch.float32 or not s.is_contiguous():
+                raise ValueError("device s must be a contiguous float32 tensor")
+            ptr, N, keep = s.data_ptr(), s.numel(), s
+        else:
+            keep = np.ascontiguousarray(s, dtype=np.float32)
+            ptr, N = keep.ctypes.data, keep.size
+        psd_a = None if psd is None else np.ascontiguousarray(psd, dtype=np.float64)
+        if psd_a is not None and psd_a.size != N // 2 + 1:
+            raise ValueError("psd must hold N/2+1 values")
+        h = ctypes.c_void_p()
+        check(_native.lib().mf_segment_upload(ptr, N, fs, None if psd_a is None else psd_a.ctypes.data,
+                                              psd_f0, psd_S0, 1 if on_dev else 0, _stream_ptr(stream),
+                                              ctypes.byref(h)))
+        self._h = h
+        self._keep = keep
+        self.N = int(N)
+        self.fs = float(fs)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.lib().mf_segment_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def filter_bank(bank: Bank, segments, threshold: float, trig_cap: int = 1 << 20, stream=None,
+                out=None):
+    """mf_filter_bank over all (template, segment) pairs.
+
+    Returns (peaks, triggers, n_trig) as torch device tensors:
+    peaks  int32/float32 [n_templates * n_seg, 4] laid out as PEAK_DTYPE,
+    triggers [trig_cap, 6] laid out as TRIG_DTYPE, n_trig int64 [1] (true count).
+    ``out`` may pass preallocated (peaks, triggers, n_trig) tensors."""
+    torch = _torch()
+    segs = list(segments) if isinstance(segments, (list, tuple)) else [segments]
+    arr = (ctypes.c_void_p * len(segs))(*[s.handle.value for s in segs])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        peaks = torch.empty((bank.n * len(segs), 4), dtype=torch.float32, device=dev)
+        trig = torch.empty((max(trig_cap, 1), 6), dtype=torch.float32, device=dev)
+        n_trig = torch.zeros(1, dtype=torch.int64, device=dev)
+    else:
+        peaks, trig, n_trig = out
+    check(_native.lib().mf_filter_bank(bank.handle, arr, len(segs), float(threshold), peaks.data_ptr(),
+                                       trig.data_ptr(), int(trig_cap), n_trig.data_ptr(),
+                                       _stream_ptr(stream)))
+    return peaks, trig, n_trig
+
+
+def peaks_to_numpy(peaks) -> np.ndarray:
+    a = peaks.detach().cpu().contiguous().numpy()
+    return a.view(PEAK_DTYPE).reshape(-1)
+
+
+def triggers_to_numpy(trig, n_trig) -> np.ndarray:
+    n = int(n_trig.item()) if hasattr(n_trig, "item") else int(n_trig)
+    n = min(n, trig.shape[0])
+    a = trig[:n].detach().cpu().contiguous().numpy()
+    return a.view(TRIG_DTYPE).reshape(-1)
+
+
+def synth_segment(g, N: int, fs: float, f_low: float = 40.0, injections=None, psd=None,
+                  psd_f0: float = 150.0, psd_S0: float = 1.0, noise_scale: float = 1.0, stream=None):
+    """mf_synth_segment: coloured Gaussian noise + injections -> float32 cuda tensor [N].
+    g: 2*(N/2) standard normals (numpy or cuda float64 tensor)."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gt = g if isinstance(g, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(g, dtype=np.float64))
+    gt = gt.to(device=dev, dtype=torch.float64).contiguous()
+    if gt.numel() != 2 * (N // 2):
+        raise ValueError("g must hold 2*(N/2) normals")
+    inj = np.zeros(0, dtype=INJ_DTYPE) if injections is None else np.ascontiguousarray(injections, dtype=INJ_DTYPE)
+    psd_a = None if psd is None else np.ascontiguousarray(psd, dtype=np.float64)
+    s = torch.empty(N, dtype=torch.float32, device=dev)
+    check(_native.lib().mf_synth_segment(gt.data_ptr(), N, fs, f_low,
+                                         None if psd_a is None else psd_a.ctypes.data, psd_f0, psd_S0,
+                                         inj.ctypes.data if inj.size else None, inj.size, noise_scale,
+                                         s.data_ptr(), _stream_ptr(stream)))
+    return s
+
+
+def refine(segment: Segment, theta, band=None, f_low: float = 40.0, stream=None):
+    """mf_refine_triggers: rho^2 and d rho^2 / d(m1, m2, t) for theta [n, 3] (float64 cuda)."""
+    torch = _torch()
+    theta = theta.contiguous()
+    if theta.dtype != torch.float64 or not theta.is_cuda or theta.dim() != 2 or theta.shape[1] != 3:
+        raise ValueError("theta must be a float64 cuda tensor of shape [n, 3]")
+    n = theta.shape[0]
+    obj = torch.empty(n, dtype=torch.float64, device=theta.device)
+    grad = torch.empty((n, 3), dtype=torch.float64, device=theta.device)
+    bp = None
+    if band is not None:
+        band = band.contiguous()
+        if band.dtype != torch.int64 or not band.is_cuda or tuple(band.shape) != (n, 2):
+            raise ValueError("band must be an int64 cuda tensor of shape [n, 2]")
+        bp = band.data_ptr()
+    p = params(f_low)
+    check(_native.lib().mf_refine_triggers(segment.handle, ctypes.byref(p), theta.data_ptr(), n, bp,
+                                           obj.data_ptr(), grad.data_ptr(), _stream_ptr(stream)))
+    return obj, grad
+
+
+def _make_refine_fn():
+    torch = _torch()
+
+    class RefineFn(torch.autograd.Function):
+        """rho^2(m1, m2, t) of each trigger row with the hand-written adjoint.
+
+        forward(theta [n, 3] float64 cuda, segment, band=None, f_low=40) -> rho^2 [n];
+        backward returns grad_out[:, None] * d rho^2 / d theta (no gradient for
+        segment, band, f_low)."""
+
+        @staticmethod
+        def forward(ctx, theta, segment, band=None, f_low=40.0):
+            obj, grad = refine(segment, theta.detach(), band=band, f_low=f_low)
+            ctx.save_for_backward(grad)
+            return obj
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (grad,) = ctx.saved_tensors
+            return grad_out[:, None] * grad, None, None, None
+
+    return RefineFn
+
+
+class _LazyRefineFn:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _LazyRefineFn._cls is None:
+            _LazyRefineFn._cls = _make_refine_fn()
+        return getattr(_LazyRefineFn._cls, name)
+
+
+RefineFn = _LazyRefineFn()

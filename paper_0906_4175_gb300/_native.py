@@ -1,0 +1,87 @@
+"""ctypes loader for libmfgb.so (the C ABI declared in include/mfgb.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Loading fails loudly when the library has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libmfgb.so")
+
+MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ETIMEOUT, MF_ENOTSUP = range(7)
+MF_PHASE_ANCHOR, MF_PHASE_FP64, MF_PHASE_FP32 = 0, 1, 2
+MF_FFT_FP32 = 0
+_NAMES = {0: "MF_OK", 1: "MF_EINVAL", 2: "MF_ENOMEM", 3: "MF_ECUDA", 4: "MF_EOVERFLOW",
+          5: "MF_ETIMEOUT", 6: "MF_ENOTSUP"}
+
+# exported entry points (name -> (restype, argtypes)); include/mfgb.h is the reference
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_F = ctypes.c_float
+SIGNATURES = {
+    "mf_last_error": (ctypes.c_char_p, []),
+    "mf_version": (ctypes.c_char_p, []),
+    "mf_bank_create": (_I, [_P, _P, _I64, _P, _P]),
+    "mf_bank_destroy": (_I, [_P]),
+    "mf_bank_size": (_I, [_P, _P]),
+    "mf_segment_upload": (_I, [_P, _I64, _D, _P, _D, _D, _I, _P, _P]),
+    "mf_segment_destroy": (_I, [_P]),
+    "mf_segment_info": (_I, [_P, _P, _P]),
+    "mf_filter_bank": (_I, [_P, _P, _I, _F, _P, _P, _I64, _P, _P]),
+    "mf_bank_check": (_I, [_P, _P]),
+    "mf_synth_segment": (_I, [_P, _I64, _D, _D, _P, _D, _D, _P, _I64, _D, _P, _P]),
+    "mf_refine_triggers": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
+}
+
+
+class BankParams(ctypes.Structure):
+    _fields_ = [("f_low", ctypes.c_double), ("pn_order", ctypes.c_int), ("amp_order", ctypes.c_int),
+                ("phase_mode", ctypes.c_int), ("fft_mode", ctypes.c_int)]
+
+
+PEAK_DTYPE = np.dtype([("rho", "f4"), ("j", "i4"), ("z_re", "f4"), ("z_im", "f4")])
+TRIG_DTYPE = np.dtype([("tmpl", "i4"), ("seg", "i4"), ("j", "i4"), ("rho", "f4"), ("z_re", "f4"),
+                       ("z_im", "f4")])
+INJ_DTYPE = np.dtype([("m1", "f8"), ("m2", "f8"), ("snr", "f8"), ("j0", "i8"), ("phi", "f8")])
+
+
+class MFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libmfgb.so is not built (run paper_0906_4175_gb300.build.build()); "
+                                  "there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(rc: int, allow=()):
+    if rc != MF_OK and rc not in allow:
+        raise MFError(rc, lib().mf_last_error().decode("utf-8", "replace"))
+    return rc

@@ -1,0 +1,538 @@
+// mf_api.cu -- host side of libmfgb: handles, argument checks, workspace,
+// launch schedule, and the extern "C" entry points declared in mfgb.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "mf_internal.h"
+#include "mf_tmpl.cuh"
+
+namespace mf {
+cudaError_t filter_kernel_attributes();
+cudaError_t prep_kernel_attributes();
+cudaError_t synth_kernel_attributes();
+cudaError_t refine_kernel_attributes();
+}  // namespace mf
+
+using namespace mf;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static int set_err(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define MF_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t _e = (call);                                                                       \
+        if (_e != cudaSuccess) {                                                                       \
+            if (_e == cudaErrorMemoryAllocation)                                                       \
+                return set_err(MF_ENOMEM, "%s: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__,  \
+                               __LINE__);                                                              \
+            return set_err(MF_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__,        \
+                           __LINE__);                                                                  \
+        }                                                                                              \
+    } while (0)
+
+extern "C" const char *mf_last_error(void) { return g_err; }
+extern "C" const char *mf_version(void) { return "mfgb 0.1 (sm_103a)"; }
+
+// One-time per-device kernel attribute set-up (dynamic shared memory > 48 KB).
+static int ensure_device_init() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return MF_OK;
+    MF_CUDA(filter_kernel_attributes());
+    MF_CUDA(prep_kernel_attributes());
+    MF_CUDA(synth_kernel_attributes());
+    MF_CUDA(refine_kernel_attributes());
+    done.push_back(dev);
+    return MF_OK;
+}
+
+static bool is_pow2_in(int64_t N, int lo, int hi) {
+    if (N < ((int64_t)1 << lo) || N > ((int64_t)1 << hi)) return false;
+    return (N & (N - 1)) == 0;
+}
+
+static int ilog2(int64_t n) {
+    int r = 0;
+    while (((int64_t)1 << (r + 1)) <= n) ++r;
+    return r;
+}
+
+static int bits_for(int64_t n) {   // bits to hold values 0..n-1
+    int b = 0;
+    while (((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+// |d^n psi / df^n| bound at f from the coefficient magnitudes
+static double psi_deriv_bound(const double *rec, double f, int n) {
+    const int pw[4] = {1, 2, 3, 5};
+    const double c[4] = {rec[TF_C1], rec[TF_C2], rec[TF_C3], rec[TF_C5]};
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        const double q = pw[i] / 3.0;
+        double fac = 1.0;
+        for (int m = 0; m < n; ++m) fac *= (q + m);
+        s += fabs(c[i]) * fac * pow(f, -q - n);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct Workspace {
+    int64_t N = 0, n_t = 0, cap = 0, batch = 0, max_anc = 0, nblk = 0;
+    UnitInfo *units = nullptr;
+    float2 *exch = nullptr;
+    float4 *anchors = nullptr;
+    float4 *partials = nullptr;
+    mf_trigger *staged = nullptr;
+    uint64_t *keys = nullptr, *keys_tmp = nullptr;
+    uint32_t *idx_a = nullptr, *idx_b = nullptr;
+    unsigned long long *counter = nullptr;
+    int *status = nullptr;
+    void release() {
+        cudaFree(units); cudaFree(exch); cudaFree(anchors); cudaFree(partials);
+        cudaFree(staged); cudaFree(keys); cudaFree(keys_tmp); cudaFree(idx_a); cudaFree(idx_b);
+        cudaFree(counter); cudaFree(status);
+        *this = Workspace();
+    }
+};
+
+struct mf_bank_s {
+    int64_t n = 0;
+    mf_bank_params params{};
+    double *d_tmpl = nullptr;
+    double B1 = 0.0, B4 = 0.0, fisco_min = 0.0;
+    int device = 0;
+    Workspace ws;
+};
+
+struct mf_segment_s {
+    int64_t N = 0;
+    double fs = 0.0;
+    int log2N = 0;
+    float2 *W = nullptr;
+    double *P = nullptr;
+    SegConsts *consts = nullptr;
+    int device = 0;
+};
+
+static mf_bank_params default_params() {
+    mf_bank_params p;
+    p.f_low = 40.0;
+    p.pn_order = 4;
+    p.amp_order = 0;
+    p.phase_mode = MF_PHASE_ANCHOR;
+    p.fft_mode = MF_FFT_FP32;
+    return p;
+}
+
+static int check_params(const mf_bank_params &p) {
+    if (!(p.f_low > 0.0) || !isfinite(p.f_low)) return set_err(MF_EINVAL, "f_low must be > 0 and finite");
+    if (p.pn_order != 4) return set_err(MF_ENOTSUP, "pn_order %d: only 4 (2PN) is implemented", p.pn_order);
+    if (p.amp_order != 0) return set_err(MF_ENOTSUP, "amp_order %d: only 0 (Newtonian) is implemented", p.amp_order);
+    if (p.phase_mode < 0 || p.phase_mode > 2) return set_err(MF_EINVAL, "phase_mode %d", p.phase_mode);
+    if (p.fft_mode != MF_FFT_FP32) return set_err(MF_ENOTSUP, "fft_mode %d: only MF_FFT_FP32", p.fft_mode);
+    return MF_OK;
+}
+
+extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                              mf_bank *out) {
+    if (!out) return set_err(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!m1 || !m2 || n <= 0) return set_err(MF_EINVAL, "need n > 0 masses");
+    if (n > (int64_t)1 << 24) return set_err(MF_EINVAL, "at most 2^24 templates per bank");
+    mf_bank_params p = params ? *params : default_params();
+    int rc = check_params(p);
+    if (rc) return rc;
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    std::vector<double> rec((size_t)n * kTmplStride);
+    double B1 = 0.0, B4 = 0.0, fmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(m1[i] > 0.0) || !(m2[i] > 0.0) || !isfinite(m1[i]) || !isfinite(m2[i]))
+            return set_err(MF_EINVAL, "template %lld: masses must be finite and > 0", (long long)i);
+        double *r = &rec[(size_t)i * kTmplStride];
+        template_constants(m1[i], m2[i], r);
+        B1 = std::max(B1, psi_deriv_bound(r, p.f_low, 1));
+        B4 = std::max(B4, psi_deriv_bound(r, p.f_low, 4));
+        fmin = std::min(fmin, r[TF_FISCO]);
+    }
+    mf_bank b = new (std::nothrow) mf_bank_s();
+    if (!b) return set_err(MF_ENOMEM, "host allocation");
+    b->n = n;
+    b->params = p;
+    b->B1 = B1;
+    b->B4 = B4;
+    b->fisco_min = fmin;
+    cudaGetDevice(&b->device);
+    cudaError_t e = cudaMalloc(&b->d_tmpl, sizeof(double) * rec.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tmpl, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_tmpl);
+        delete b;
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "bank upload: %s",
+                       cudaGetErrorString(e));
+    }
+    *out = b;
+    return MF_OK;
+}
+
+extern "C" int mf_bank_destroy(mf_bank b) {
+    if (!b) return MF_OK;
+    b->ws.release();
+    cudaFree(b->d_tmpl);
+    delete b;
+    return MF_OK;
+}
+
+extern "C" int mf_bank_size(mf_bank b, int64_t *n) {
+    if (!b || !n) return set_err(MF_EINVAL, "NULL argument");
+    *n = b->n;
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// segments
+// ---------------------------------------------------------------------------
+extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const double *psd, double psd_f0,
+                                 double psd_S0, int s_on_device, void *cuda_stream, mf_segment *out) {
+    if (!out) return set_err(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!s) return set_err(MF_EINVAL, "s is NULL");
+    if (!is_pow2_in(N, 10, 22)) return set_err(MF_EINVAL, "N = %lld must be a power of two in [2^10, 2^22]", (long long)N);
+    if (!(fs > 0.0) || !isfinite(fs)) return set_err(MF_EINVAL, "fs must be > 0");
+    if (!psd && (!(psd_f0 > 0.0) || !(psd_S0 > 0.0) || !isfinite(psd_f0) || !isfinite(psd_S0)))
+        return set_err(MF_EINVAL, "psd_f0 and psd_S0 must be > 0");
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t half = N / 2;
+    mf_segment g = new (std::nothrow) mf_segment_s();
+    if (!g) return set_err(MF_ENOMEM, "host allocation");
+    g->N = N;
+    g->fs = fs;
+    g->log2N = ilog2(N);
+    cudaGetDevice(&g->device);
+    float *s_dev = nullptr;
+    float2 *exch = nullptr, *X = nullptr;
+    double *q = nullptr, *btmp = nullptr, *psd_dev = nullptr;
+    const int64_t nbt = prefix_block_tmp_count(half);
+    cudaError_t e = cudaMalloc(&g->W, sizeof(float2) * half);
+    if (e == cudaSuccess) e = cudaMalloc(&g->P, sizeof(double) * (half + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->consts, sizeof(SegConsts));
+    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * N, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&X, sizeof(float2) * (half + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&q, sizeof(double) * half, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&btmp, sizeof(double) * nbt, st);
+    if (e == cudaSuccess && !s_on_device) {
+        e = cudaMallocAsync(&s_dev, sizeof(float) * N, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s_dev, s, sizeof(float) * N, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && psd) {
+        e = cudaMallocAsync(&psd_dev, sizeof(double) * (half + 1), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(psd_dev, psd, sizeof(double) * (half + 1), cudaMemcpyHostToDevice, st);
+    }
+    const float *s_use = s_on_device ? s : s_dev;
+    if (e == cudaSuccess) e = launch_forward_fft(s_use, N, exch, X, st);
+    if (e == cudaSuccess) e = launch_psd_weights(X, psd_dev, psd_f0, psd_S0, N, fs, q, st);
+    if (e == cudaSuccess) e = launch_prefix_f64(q, half, g->P, btmp, st);
+    if (e == cudaSuccess) e = launch_weight_data(X, psd_dev, psd_f0, psd_S0, N, fs, g->P, g->consts, g->W, st);
+    if (s_dev) cudaFreeAsync(s_dev, st);
+    if (psd_dev) cudaFreeAsync(psd_dev, st);
+    if (exch) cudaFreeAsync(exch, st);
+    if (X) cudaFreeAsync(X, st);
+    if (q) cudaFreeAsync(q, st);
+    if (btmp) cudaFreeAsync(btmp, st);
+    if (e == cudaSuccess && !s_on_device) e = cudaStreamSynchronize(st);   // host s / psd consumed before return
+    else if (e == cudaSuccess && psd) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(g->W); cudaFree(g->P); cudaFree(g->consts);
+        delete g;
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "segment_upload: %s",
+                       cudaGetErrorString(e));
+    }
+    *out = g;
+    return MF_OK;
+}
+
+extern "C" int mf_segment_destroy(mf_segment g) {
+    if (!g) return MF_OK;
+    cudaFree(g->W);
+    cudaFree(g->P);
+    cudaFree(g->consts);
+    delete g;
+    return MF_OK;
+}
+
+extern "C" int mf_segment_info(mf_segment g, int64_t *N, double *fs) {
+    if (!g) return set_err(MF_EINVAL, "NULL segment");
+    if (N) *N = g->N;
+    if (fs) *fs = g->fs;
+    return MF_OK;
+}
+
+static SegDev seg_dev(const mf_segment_s *g) {
+    SegDev d;
+    d.W = g->W;
+    d.P = g->P;
+    d.consts = g->consts;
+    d.fs = g->fs;
+    d.df = g->fs / (double)g->N;
+    d.N = g->N;
+    d.log2N = g->log2N;
+    d.log2N2 = g->log2N / 2;
+    d.log2N1 = g->log2N - d.log2N2;
+    return d;
+}
+
+// Anchor spacing D = 2^log2D for a (bank, segment): the largest power of two
+// (<= 256) for which the cubic-Taylor remainder max|psi''''| (D/2)^4/24 stays
+// below 5e-7 turns and |psi'| D/2 below 8 turns (FP32 magnitude), both bounded
+// at f_low over the whole bank.
+static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
+    if (b->params.phase_mode == MF_PHASE_FP64) return 0;
+    const double df = g->fs / (double)g->N;
+    int lg = 0;
+    while (lg < 8) {
+        const double D2 = (double)(1 << (lg + 1));
+        const double h = D2 / 2.0;
+        const double taylor = b->B4 * pow(df, 4) * h * h * h * h / 24.0;
+        const double mag = b->B1 * df * h;
+        if (taylor > 5e-7 || mag > 8.0) break;
+        ++lg;
+    }
+    return lg;
+}
+
+// templates in flight per batch (exchange ring of batch * N complex64)
+static int64_t choose_batch(int64_t N, int64_t n_t) {
+    int64_t b = ((int64_t)64 << 20) / (8 * N);
+    if (const char *env = getenv("MFGB_BATCH")) b = atoll(env);
+    if (b < 1) b = 1;
+    if (b > 65535) b = 65535;
+    if (b > n_t) b = n_t;
+    return b;
+}
+
+static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch, int64_t max_anc, int64_t nblk) {
+    Workspace &w = b->ws;
+    if (w.units && w.N >= N && w.n_t >= b->n && w.cap >= cap && w.batch >= batch && w.max_anc >= max_anc &&
+        w.nblk >= nblk)
+        return MF_OK;
+    const int64_t nN = std::max(w.N, N), ncap = std::max(std::max(w.cap, cap), (int64_t)1);
+    const int64_t nb = std::max(w.batch, batch), na = std::max(w.max_anc, max_anc);
+    const int64_t nbl = std::max(w.nblk, nblk);
+    MF_CUDA(cudaDeviceSynchronize());
+    w.release();
+    MF_CUDA(cudaMalloc(&w.units, sizeof(UnitInfo) * b->n));
+    MF_CUDA(cudaMalloc(&w.exch, sizeof(float2) * nN * nb));
+    MF_CUDA(cudaMalloc(&w.anchors, sizeof(float4) * na * nb));
+    MF_CUDA(cudaMalloc(&w.partials, sizeof(float4) * nbl * b->n));
+    MF_CUDA(cudaMalloc(&w.staged, sizeof(mf_trigger) * ncap));
+    MF_CUDA(cudaMalloc(&w.keys, sizeof(uint64_t) * ncap));
+    MF_CUDA(cudaMalloc(&w.keys_tmp, sizeof(uint64_t) * ncap));
+    MF_CUDA(cudaMalloc(&w.idx_a, sizeof(uint32_t) * ncap));
+    MF_CUDA(cudaMalloc(&w.idx_b, sizeof(uint32_t) * ncap));
+    MF_CUDA(cudaMalloc(&w.counter, sizeof(unsigned long long)));
+    MF_CUDA(cudaMalloc(&w.status, sizeof(int)));
+    MF_CUDA(cudaMemset(w.status, 0, sizeof(int)));
+    w.N = nN; w.n_t = b->n; w.cap = ncap; w.batch = nb; w.max_anc = na; w.nblk = nbl;
+    return MF_OK;
+}
+
+extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, float threshold, mf_peak *peaks,
+                              mf_trigger *trig, int64_t trig_cap, int64_t *n_trig, void *cuda_stream) {
+    if (!b || !segs || n_seg < 1) return set_err(MF_EINVAL, "need a bank and n_seg >= 1 segments");
+    if (!peaks || !n_trig) return set_err(MF_EINVAL, "peaks and n_trig must not be NULL");
+    if (trig_cap < 0 || trig_cap > ((int64_t)1 << 31)) return set_err(MF_EINVAL, "trig_cap out of range");
+    if (trig_cap > 0 && !trig) return set_err(MF_EINVAL, "trig is NULL with trig_cap > 0");
+    if (!isfinite(threshold) || threshold < 0.f) return set_err(MF_EINVAL, "threshold must be finite and >= 0");
+    if (n_seg > 65535) return set_err(MF_EINVAL, "at most 65535 segments per call");
+    int64_t maxN = 0;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != b->device) return set_err(MF_EINVAL, "bank was created on device %d, current is %d", b->device, cur);
+    for (int s = 0; s < n_seg; ++s) {
+        const mf_segment_s *g = segs[s];
+        if (!g) return set_err(MF_EINVAL, "segs[%d] is NULL", s);
+        if (g->device != cur) return set_err(MF_EINVAL, "segs[%d] lives on device %d", s, g->device);
+        maxN = std::max(maxN, g->N);
+        // every template's band must be non-empty: the smallest f_cut decides
+        const double fc = std::min(b->fisco_min, 0.5 * g->fs);
+        const int64_t lo = std::max((int64_t)1, (int64_t)ceil(b->params.f_low * (double)g->N / g->fs));
+        const int64_t hi = std::min((int64_t)floor(fc * (double)g->N / g->fs) + 1, g->N / 2);
+        if (hi <= lo)
+            return set_err(MF_EINVAL, "segs[%d]: f_low %.3f Hz >= f_cut %.3f Hz for some template", s,
+                           b->params.f_low, fc);
+    }
+    KeyLayout kl;
+    kl.j_bits = ilog2(maxN);
+    kl.seg_bits = bits_for(n_seg);
+    kl.tmpl_bits = bits_for(b->n);
+    const int key_bits = kl.j_bits + kl.seg_bits + kl.tmpl_bits;
+    if (key_bits > 64) return set_err(MF_EINVAL, "trigger key needs %d bits", key_bits);
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t batch = choose_batch(maxN, b->n);
+    int64_t max_anc = 0, nblk = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        const int lgD = choose_log2D(b, segs[s]);
+        max_anc = std::max(max_anc, ((segs[s]->N / 2) >> lgD) + 2);
+        nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
+    }
+    int rc = ensure_workspace(b, maxN, trig_cap, batch, max_anc, nblk);
+    if (rc) return rc;
+    Workspace &w = b->ws;
+    MF_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st));
+    MF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    const int n_t = (int)b->n;
+    for (int s = 0; s < n_seg; ++s) {
+        const SegDev sd = seg_dev(segs[s]);
+        const int lgD = choose_log2D(b, segs[s]);
+        const int man = (int)(((segs[s]->N / 2) >> lgD) + 2);
+        const int nbk = pass2_blocks(sd.log2N);
+        MF_CUDA(launch_units(sd, b->d_tmpl, n_t, b->params.f_low, threshold, lgD, w.units, st));
+        for (int u0 = 0; u0 < n_t; u0 += (int)batch) {
+            const int nb = (int)std::min<int64_t>(batch, n_t - u0);
+            if (b->params.phase_mode != MF_PHASE_FP32)
+                MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, u0, nb, lgD, man, w.anchors, st));
+            MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors, w.exch, b->params.phase_mode,
+                                 b->d_tmpl, st));
+            MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
+                                 std::max<int64_t>(trig_cap, 0), st));
+        }
+        MF_CUDA(launch_reduce_peaks(sd, w.units, n_t, w.partials, nbk, s, n_seg, peaks, st));
+    }
+    MF_CUDA(launch_sort_triggers(w.counter, trig_cap, key_bits, w.staged, w.keys, w.keys_tmp, w.idx_a, w.idx_b,
+                                 trig, n_trig, w.status, st));
+    return MF_OK;
+}
+
+extern "C" int mf_bank_check(mf_bank b, void *cuda_stream) {
+    if (!b) return set_err(MF_EINVAL, "NULL bank");
+    MF_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    if (!b->ws.status) return MF_OK;
+    int st = 0;
+    MF_CUDA(cudaMemcpy(&st, b->ws.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 2) return set_err(MF_ETIMEOUT, "a bounded device wait expired in the last mf_filter_bank");
+    if (st & 1) return set_err(MF_EOVERFLOW, "more triggers than trig_cap in the last mf_filter_bank");
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// synthesis
+// ---------------------------------------------------------------------------
+extern "C" int mf_synth_segment(const double *g, int64_t N, double fs, double f_low, const double *psd,
+                                double psd_f0, double psd_S0, const mf_injection *inj, int64_t n_inj,
+                                double noise_scale, float *s_out, void *cuda_stream) {
+    if (!g || !s_out) return set_err(MF_EINVAL, "g and s_out must not be NULL");
+    if (!is_pow2_in(N, 10, 22)) return set_err(MF_EINVAL, "N must be a power of two in [2^10, 2^22]");
+    if (!(fs > 0.0) || !(f_low > 0.0) || !isfinite(noise_scale)) return set_err(MF_EINVAL, "bad fs/f_low/noise_scale");
+    if (n_inj < 0 || (n_inj > 0 && !inj) || n_inj > 4096) return set_err(MF_EINVAL, "bad injections");
+    if (!psd && (!(psd_f0 > 0.0) || !(psd_S0 > 0.0))) return set_err(MF_EINVAL, "psd_f0 and psd_S0 must be > 0");
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t half = N / 2;
+    std::vector<double> rec((size_t)std::max<int64_t>(n_inj, 1) * 10, 0.0);
+    for (int64_t i = 0; i < n_inj; ++i) {
+        const mf_injection &J = inj[i];
+        if (!(J.m1 > 0.0) || !(J.m2 > 0.0) || !isfinite(J.snr) || !isfinite(J.phi))
+            return set_err(MF_EINVAL, "injection %lld: bad parameters", (long long)i);
+        double t[kTmplStride];
+        template_constants(J.m1, J.m2, t);
+        double *r = &rec[(size_t)i * 10];
+        r[0] = t[TF_C1]; r[1] = t[TF_C2]; r[2] = t[TF_C3]; r[3] = t[TF_C5];
+        const double fc = std::min(t[TF_FISCO], 0.5 * fs);
+        int64_t lo = (int64_t)ceil(f_low * (double)N / fs), hi = (int64_t)floor(fc * (double)N / fs) + 1;
+        if (lo < 1) lo = 1;
+        if (hi > half) hi = half;
+        if (hi <= lo) return set_err(MF_EINVAL, "injection %lld: empty band", (long long)i);
+        r[4] = (double)lo; r[5] = (double)hi;
+        int64_t j0 = J.j0 % N;
+        if (j0 < 0) j0 += N;
+        r[6] = (double)j0;
+        r[7] = J.phi / (2.0 * M_PI);
+        r[8] = J.snr;
+    }
+    double *inj_dev = nullptr, *q = nullptr, *P = nullptr, *btmp = nullptr, *psd_dev = nullptr;
+    float2 *Y = nullptr, *exch = nullptr;
+    const int64_t nbt = prefix_block_tmp_count(half);
+    cudaError_t e = cudaMallocAsync(&inj_dev, sizeof(double) * rec.size(), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(inj_dev, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&q, sizeof(double) * half, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&P, sizeof(double) * (half + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&btmp, sizeof(double) * nbt, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&Y, sizeof(float2) * half, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * N, st);
+    if (e == cudaSuccess && psd) {
+        e = cudaMallocAsync(&psd_dev, sizeof(double) * (half + 1), st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(psd_dev, psd, sizeof(double) * (half + 1), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = launch_psd_weights(nullptr, psd_dev, psd_f0, psd_S0, N, fs, q, st);
+    if (e == cudaSuccess) e = launch_prefix_f64(q, half, P, btmp, st);
+    if (e == cudaSuccess)
+        e = launch_synth_spectrum(g, N, fs, f_low, psd_dev, psd_f0, psd_S0, inj_dev, n_inj, P, noise_scale, Y, st);
+    if (e == cudaSuccess) e = launch_inverse_real_fft(Y, N, 2.0 * fs / (double)N, exch, s_out, st);
+    if (inj_dev) cudaFreeAsync(inj_dev, st);
+    if (q) cudaFreeAsync(q, st);
+    if (P) cudaFreeAsync(P, st);
+    if (btmp) cudaFreeAsync(btmp, st);
+    if (Y) cudaFreeAsync(Y, st);
+    if (exch) cudaFreeAsync(exch, st);
+    if (psd_dev) cudaFreeAsync(psd_dev, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host injection table consumed
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "synth_segment: %s",
+                       cudaGetErrorString(e));
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// refinement
+// ---------------------------------------------------------------------------
+extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, const double *theta, int64_t n,
+                                  const int64_t *band, double *obj, double *grad, void *cuda_stream) {
+    if (!seg || !theta || !obj || !grad) return set_err(MF_EINVAL, "NULL argument");
+    if (n < 0) return set_err(MF_EINVAL, "n < 0");
+    if (n == 0) return MF_OK;
+    mf_bank_params p = params ? *params : default_params();
+    int rc = check_params(p);
+    if (rc) return rc;
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const SegDev sd = seg_dev(seg);
+    const int bpr = refine_blocks_per_row();
+    double *partial = nullptr;
+    cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * 8 * bpr * n, st);
+    if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, st);
+    if (partial) cudaFreeAsync(partial, st);
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers: %s",
+                       cudaGetErrorString(e));
+    return MF_OK;
+}

@@ -1,0 +1,263 @@
+// mf_fft.cuh -- FP32 complex FFT building blocks for sm_103a.
+//
+// The inverse FFT of Eq. (1) (and the forward FFT of the data) is a four-step
+// transform N = N1 * N2: pass 1 runs N1 column FFTs of length N2 (stride N1 in
+// the spectrum), multiplies by the inter-pass twiddles exp(+-2 pi i j2 k1 / N)
+// and writes one complex64 exchange array; pass 2 runs N2 row FFTs of length
+// N1.  Each CTA transforms C sequences of length L = 2^m (32 <= L <= 4096) held
+// in shared memory, with a Stockham autosort schedule (the index mapping of
+// Govindaraju et al., "High Performance Discrete Fourier Transforms on Graphics
+// Processors", SC 2008): stage radices (32, min(32, L/32), L/1024), every
+// thread holding 32 complex values in registers per stage, radix-32/16/8/4/2
+// butterflies fully unrolled with compile-time twiddle constants.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mf {
+
+// ----------------------------------------------------------------------------
+// Compile-time cos/sin of 2 pi num/den: exact integer reduction to the first
+// octant, then Taylor series in double (|x| <= pi/4, 14 terms: < 1e-30).
+// ----------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+struct CxCS { double c, s; };
+
+__host__ __device__ constexpr double cx_sin_series(double x) {
+    double t = x, s = x;
+    for (int n = 1; n < 14; ++n) { t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0)); s += t; }
+    return s;
+}
+__host__ __device__ constexpr double cx_cos_series(double x) {
+    double t = 1.0, s = 1.0;
+    for (int n = 1; n < 14; ++n) { t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n)); s += t; }
+    return s;
+}
+__host__ __device__ constexpr CxCS cx_sincos_turn(long long num, long long den) {
+    long long m = num % den;
+    if (m < 0) m += den;
+    long long q = (4 * m) / den;          // quadrant
+    long long r = 4 * m - q * den;        // angle within quadrant = (pi/2) r / den
+    double c = 0.0, s = 0.0;
+    if (2 * r <= den) {
+        double x = (kPi / 2.0) * (double)r / (double)den;
+        c = cx_cos_series(x); s = cx_sin_series(x);
+    } else {
+        double y = (kPi / 2.0) * (double)(den - r) / (double)den;
+        c = cx_sin_series(y); s = cx_cos_series(y);
+    }
+    if (q == 0) return CxCS{c, s};
+    if (q == 1) return CxCS{-s, c};
+    if (q == 2) return CxCS{-c, -s};
+    return CxCS{s, -c};
+}
+
+__host__ __device__ constexpr int cx_ilog2(long long x) {
+    int r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+// ----------------------------------------------------------------------------
+// complex helpers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 czero() { return make_float2(0.f, 0.f); }
+
+// x * exp(SIGN * 2 pi i Q / R), Q and R compile-time
+template <int Q, int R, int SIGN>
+__device__ __forceinline__ float2 tw_const(float2 x) {
+    constexpr long long g = Q % R;
+    if constexpr (g == 0) {
+        return x;
+    } else if constexpr (4 * g == R) {                  // exp(+-i pi/2) = +-i
+        return SIGN > 0 ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    } else if constexpr (2 * g == R) {                  // -1
+        return make_float2(-x.x, -x.y);
+    } else if constexpr (4 * g == 3 * R) {              // exp(+-3 i pi/2) = -+i
+        return SIGN > 0 ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);
+    } else {
+        constexpr CxCS w = cx_sincos_turn(SIGN * g, R);
+        constexpr float c = (float)w.c;
+        constexpr float s = (float)w.s;
+        return make_float2(fmaf(c, x.x, -s * x.y), fmaf(c, x.y, s * x.x));
+    }
+}
+
+// ----------------------------------------------------------------------------
+// In-register DFT of length R (natural order in and out), radix-2 DIT
+// recursion with compile-time twiddles:  X_q = sum_r v_r exp(SIGN 2 pi i r q / R)
+// ----------------------------------------------------------------------------
+template <int R, int SIGN, int Q>
+struct Combine {
+    static __device__ __forceinline__ void run(float2 *v, const float2 *e, const float2 *o) {
+        if constexpr (Q < R / 2) {
+            float2 t = tw_const<Q, R, SIGN>(o[Q]);
+            v[Q] = cadd(e[Q], t);
+            v[Q + R / 2] = csub(e[Q], t);
+            Combine<R, SIGN, Q + 1>::run(v, e, o);
+        }
+    }
+};
+
+template <int R, int SIGN>
+struct Dft {
+    static __device__ __forceinline__ void run(float2 *v) {
+        if constexpr (R == 1) {
+            return;
+        } else if constexpr (R == 2) {
+            float2 a = v[0], b = v[1];
+            v[0] = cadd(a, b);
+            v[1] = csub(a, b);
+        } else {
+            float2 e[R / 2], o[R / 2];
+#pragma unroll
+            for (int i = 0; i < R / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+            Dft<R / 2, SIGN>::run(e);
+            Dft<R / 2, SIGN>::run(o);
+            Combine<R, SIGN, 0>::run(v, e, o);
+        }
+    }
+};
+
+// 32-point DFT whose inputs v[16..31] are zero (upper half of a one-sided
+// spectrum): even outputs are the 16-point DFT of v, odd outputs the 16-point
+// DFT of v_r exp(SIGN 2 pi i r/32).
+template <int SIGN, int Q>
+struct HalfZeroTw {
+    static __device__ __forceinline__ void run(const float2 *v, float2 *b) {
+        if constexpr (Q < 16) {
+            b[Q] = tw_const<Q, 32, SIGN>(v[Q]);
+            HalfZeroTw<SIGN, Q + 1>::run(v, b);
+        }
+    }
+};
+template <int SIGN>
+__device__ __forceinline__ void dft32_halfzero(float2 *v) {
+    float2 a[16], b[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = v[i];
+    HalfZeroTw<SIGN, 0>::run(v, b);
+    Dft<16, SIGN>::run(a);
+    Dft<16, SIGN>::run(b);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) { v[2 * p] = a[p]; v[2 * p + 1] = b[p]; }
+}
+
+// v[r] *= w^r for r = 1..R-1 (w^r by repeated multiplication)
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 *v, float2 w) {
+    float2 cur = w;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        v[r] = cmul(v[r], cur);
+        if (r + 1 < R) cur = cmul(cur, w);
+    }
+}
+
+// exp(SIGN * 2 pi i num / den) for den a power of two (FP32, argument exact)
+template <int SIGN>
+__device__ __forceinline__ float2 unit_root(uint32_t num, uint32_t log2den) {
+    uint32_t m = num & ((1u << log2den) - 1u);
+    float a = __uint_as_float((uint32_t)(127 - (int)log2den + 1) << 23) * (float)m;  // 2 m / den, exact
+    float s, c;
+    sincospif(a, &s, &c);
+    return make_float2(c, SIGN > 0 ? s : -s);
+}
+
+// ----------------------------------------------------------------------------
+// Stockham schedule for one CTA: C sequences of length L, T = L/32 threads per
+// sequence.  Shared memory holds the sequences with one pad element every 32
+// and a column stride congruent to 2 mod 16 (float2 units) to spread banks.
+// ----------------------------------------------------------------------------
+template <int L>
+struct FftShape {
+    static_assert(L >= 32 && L <= 4096 && (L & (L - 1)) == 0, "L must be a power of two in [32, 4096]");
+    static constexpr int T = L / 32;
+    static constexpr int R1 = (L / 32 <= 32) ? L / 32 : 32;
+    static constexpr int R2 = (L > 1024) ? L / 1024 : 1;
+    static constexpr int NST = (L == 32) ? 1 : ((L <= 1024) ? 2 : 3);
+    static constexpr int PADDED = L + L / 32;
+    static constexpr int STRIDE = PADDED + ((2 - (PADDED % 16)) + 16) % 16;   // = 2 mod 16
+};
+
+__device__ __forceinline__ int spad(int m) { return m + (m >> 5); }
+
+// One Stockham stage reading from and (unless LAST) writing to shared memory.
+// Ns = product of earlier radices; each thread runs 32/R butterflies b = t + i*T.
+template <int L, int R, int Ns, int SIGN, bool LAST, class Snk>
+__device__ __forceinline__ void stockham_stage(float2 *sq, int seq, int t, Snk &snk) {
+    constexpr int T = L / 32;
+    constexpr int NB = 32 / R;
+    constexpr int SPAN = L / R;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = t + i * T;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = sq[spad(b + r * SPAN)];
+    }
+    if constexpr (!LAST) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = t + i * T;
+        const int k = b & (Ns - 1);
+        if constexpr (Ns > 1) {
+            constexpr int LG = cx_ilog2(Ns * R);
+            twiddle_powers<R>(v + i * R, unit_root<SIGN>((uint32_t)k, LG));
+        }
+        Dft<R, SIGN>::run(v + i * R);
+        if constexpr (LAST) {
+            snk.template store<R>(seq, b, Ns, v + i * R);    // outputs b + r * Ns
+        } else {
+            const int idxD = (b / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sq[spad(idxD + r * Ns)] = v[i * R + r];
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+// Full CTA FFT.  Src::load(seq, t, v) fills v[r] = x[t + r*T], r < 32
+// (Src::kHalfZero: v[16..31] are zero and are not read).
+// Snk::store<R>(seq, b, stride, v) receives outputs b + r*stride, r < R.
+// The last stage does not synchronise: a sink that reuses shared memory
+// afterwards must __syncthreads() first.
+// smem: C * FftShape<L>::STRIDE float2.  Must be called by all C*T threads.
+template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
+__device__ __forceinline__ void cta_fft(float2 *smem, Src &src, Snk &snk) {
+    using S = FftShape<L>;
+    constexpr int T = S::T;
+    const int tid = threadIdx.x;
+    const int seq = SEQ_FAST ? (tid % C) : (tid / T);
+    const int t = SEQ_FAST ? (tid / C) : (tid % T);
+    float2 *sq = smem + seq * S::STRIDE;
+
+    {
+        float2 v[32];
+        src.load(seq, t, v);
+        if constexpr (Src::kHalfZero) dft32_halfzero<SIGN>(v);
+        else Dft<32, SIGN>::run(v);
+        if constexpr (S::NST == 1) {
+            snk.template store<32>(seq, t, T, v);
+            return;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) sq[spad(32 * t + r)] = v[r];
+        }
+    }
+    __syncthreads();
+    if constexpr (S::NST == 2) {
+        stockham_stage<L, S::R1, 32, SIGN, true>(sq, seq, t, snk);
+    } else if constexpr (S::NST == 3) {
+        stockham_stage<L, S::R1, 32, SIGN, false>(sq, seq, t, snk);
+        stockham_stage<L, S::R2, 32 * S::R1, SIGN, true>(sq, seq, t, snk);
+    }
+}
+
+}  // namespace mf

@@ -1,0 +1,97 @@
+// mf_internal.h -- structures shared by the host code and the kernels of
+// libmfgb (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mfgb.h"
+
+namespace mf {
+
+// G Msun / c^3 in seconds (IAU 2015 nominal solar mass parameter).
+constexpr double kMsunS = 4.925490947e-6;
+constexpr int kTmplStride = 8;   // doubles per template record
+
+// Per-template constants, FP64, written by mf_bank_create (host):
+//   psi(f) = C0 + c1 u + c2 u^2 + c3 u^3 + c5 u^5 in turns (cycles), u = f^(-1/3), f in Hz,
+// the 2PN stationary-phase phase Psi/(2 pi) with t_c = phi_c = 0 (C0 = -1/8).
+enum TmplField { TF_C1 = 0, TF_C2 = 1, TF_C3 = 2, TF_C5 = 3, TF_FISCO = 4, TF_AMP = 5, TF_M = 6, TF_ETA = 7 };
+
+// Segment constants that kernels read on the device (written by segment prep).
+struct SegConsts {
+    double P_tot;   // sum_{1 <= k < N/2} f_k^(-7/3) / S_k
+    double alpha;   // sqrt(4 df / P_tot): scale of W so that rho is O(1)
+};
+
+// What the filter kernels need to know about a segment.
+struct SegDev {
+    const float2 *W;          // [N/2]  alpha f^(-7/6) conj(s~_k) / S_k, 0 at k = 0
+    const double *P;          // [N/2+1] exclusive prefix of f^(-7/3)/S_k
+    const SegConsts *consts;  // device
+    double fs, df;
+    int64_t N;
+    int log2N, log2N1, log2N2;   // N = N1 * N2, N2 = column (pass-1) length
+};
+
+// Per (template, segment) unit, computed on the device for each filter call.
+struct UnitInfo {
+    int32_t k_lo, k_hi;   // band [k_lo, k_hi)
+    int32_t g_lo, n_anc;  // first anchor index and anchor count
+    float rho_scale;      // rho = |raw| * rho_scale, raw = sum_band W_k e^{-i Psi_k} e^{2 pi i jk/N}
+    float thr2;           // |raw|^2 > thr2  <=>  rho > threshold
+    float z_scale;        // z = raw * z_scale (Eq. 1 with A = Mc^(5/6))
+    int32_t tmpl;         // template index
+};
+
+// Stable trigger keys: (tmpl, seg, j) packed into 64 bits.
+struct KeyLayout {
+    int j_bits, seg_bits, tmpl_bits;
+};
+
+// ---- launch wrappers (defined in the .cu files; return cudaError_t) -----
+
+// segment preparation (mf_prep.cu)
+cudaError_t launch_forward_fft(const float *s, int64_t N, float2 *exch, float2 *X, cudaStream_t st);
+cudaError_t launch_psd_weights(const float2 *X, const double *psd, double psd_f0, double psd_S0,
+                               int64_t N, double fs, double *q, cudaStream_t st);
+cudaError_t launch_prefix_f64(const double *q, int64_t n, double *P, double *block_tmp, cudaStream_t st);
+cudaError_t launch_weight_data(const float2 *X, const double *psd, double psd_f0, double psd_S0,
+                               int64_t N, double fs, const double *P, SegConsts *consts, float2 *W,
+                               cudaStream_t st);
+int64_t prefix_block_tmp_count(int64_t n);
+
+// synthesis (mf_synth.cu)
+cudaError_t launch_synth_spectrum(const double *g, int64_t N, double fs, double f_low, const double *psd,
+                                  double psd_f0, double psd_S0, const double *inj_dev, int64_t n_inj,
+                                  const double *P, double noise_scale, float2 *Y, cudaStream_t st);
+cudaError_t launch_inverse_real_fft(const float2 *Y, int64_t N, double scale, float2 *exch, float *s,
+                                    cudaStream_t st);
+
+// filter (mf_filter.cu)
+cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double f_low, float thr,
+                         int log2D, UnitInfo *units, cudaStream_t st);
+cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0,
+                           int n_units, int log2D, int max_anc, float4 *anchors, cudaStream_t st);
+cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
+                         int max_anc, const float4 *anchors, float2 *exch, int phase_mode,
+                         const double *tmpl, cudaStream_t st);
+cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units,
+                         const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
+                         mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
+                         cudaStream_t st);
+int pass2_blocks(int log2N);
+cudaError_t launch_reduce_peaks(const SegDev &seg, const UnitInfo *units, int n_units, const float4 *partials,
+                                int nblk, int seg_idx, int n_seg, mf_peak *peaks, cudaStream_t st);
+cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,
+                                 const mf_trigger *staged, const uint64_t *keys, uint64_t *keys_tmp,
+                                 uint32_t *idx_a, uint32_t *idx_b, mf_trigger *out, int64_t *n_out,
+                                 int *status, cudaStream_t st);
+
+// refinement (mf_refine.cu)
+cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,
+                          const int64_t *band, double *obj, double *grad, double *partial, cudaStream_t st);
+int refine_blocks_per_row();
+
+cudaError_t init_kernel_attributes();
+
+}  // namespace mf

@@ -1,0 +1,185 @@
+// mf_passes.cuh -- the two passes of the four-step FFT as kernels templated on
+// their data source and sink, plus the generic sources/sinks used by segment
+// preparation and synthesis.  Geometry: N = N1 * N2 with N2 = 2^floor(log2 N / 2)
+// the pass-1 (column) length and N1 = N / N2 the pass-2 (row) length;
+// spectrum index k = k1 + N1 k2, time index j = j2 + N2 j1, exchange layout
+// E[j2 * N1 + k1] (row j2 contiguous).
+#pragma once
+#include "mf_fft.cuh"
+#include "mf_internal.h"
+
+namespace mf {
+
+template <int L>
+__host__ __device__ constexpr int seqs_per_cta(int other) {
+    return (8192 / L) < other ? (8192 / L) : other;
+}
+
+template <int L, int C>
+__host__ __device__ constexpr size_t pass_smem_bytes() {
+    return (size_t)C * FftShape<L>::STRIDE * sizeof(float2);
+}
+
+// Generic pass kernel: grid.x = N_other / C tiles, grid.y = batch.
+template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
+__global__ void __launch_bounds__(C *(L / 32), (C * (L / 32) >= 256) ? 2 : 1)
+    k_fft_pass(typename Src::Params sp, typename Snk::Params kp) {
+    extern __shared__ float2 smem[];
+    Src src(sp);
+    Snk snk(kp);
+    cta_fft<L, C, SEQ_FAST, SIGN>(smem, src, snk);
+    snk.finish(smem);
+}
+
+template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
+cudaError_t set_pass_attrs() {
+    return cudaFuncSetAttribute(k_fft_pass<L, C, SEQ_FAST, SIGN, Src, Snk>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pass_smem_bytes<L, C>());
+}
+
+template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
+cudaError_t run_pass(dim3 grid, const typename Src::Params &sp, const typename Snk::Params &kp,
+                     cudaStream_t st) {
+    k_fft_pass<L, C, SEQ_FAST, SIGN, Src, Snk>
+        <<<grid, C * (L / 32), pass_smem_bytes<L, C>(), st>>>(sp, kp);
+    return cudaGetLastError();
+}
+
+// Calls op.template run<N2, N1>() for the split of N = 2^log2N.
+template <class Op>
+cudaError_t dispatch_split(int log2N, Op &op) {
+    switch (log2N) {
+        case 10: return op.template run<32, 32>();
+        case 11: return op.template run<32, 64>();
+        case 12: return op.template run<64, 64>();
+        case 13: return op.template run<64, 128>();
+        case 14: return op.template run<128, 128>();
+        case 15: return op.template run<128, 256>();
+        case 16: return op.template run<256, 256>();
+        case 17: return op.template run<256, 512>();
+        case 18: return op.template run<512, 512>();
+        case 19: return op.template run<512, 1024>();
+        case 20: return op.template run<1024, 1024>();
+        case 21: return op.template run<1024, 2048>();
+        case 22: return op.template run<2048, 2048>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+__host__ __device__ inline int log2_n2(int log2N) { return log2N / 2; }
+
+// ---------------------------------------------------------------------------
+// Column (pass-1) sources.  Sequence seq of CTA blockIdx.x is column
+// k1 = blockIdx.x * C + seq; element n of it is spectrum entry k1 + N1 n.
+// ---------------------------------------------------------------------------
+template <int L, int C, bool HALF_ZERO>
+struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO
+    static constexpr bool kHalfZero = HALF_ZERO;
+    struct Params { const float2 *X; int log2N1; int64_t batch_stride; };
+    const Params &p;
+    __device__ ColComplexSrc(const Params &pp) : p(pp) {}
+    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
+        const float2 *X = p.X + (int64_t)blockIdx.y * p.batch_stride;
+        const int k1 = blockIdx.x * C + seq;
+        constexpr int T = L / 32;
+        constexpr int NR = HALF_ZERO ? 16 : 32;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = X[k1 + ((t + r * T) << p.log2N1)];
+    }
+};
+
+template <int L, int C>
+struct ColRealSrc {         // real samples s[n] (imaginary part zero)
+    static constexpr bool kHalfZero = false;
+    struct Params { const float *s; int log2N1; };
+    const Params &p;
+    __device__ ColRealSrc(const Params &pp) : p(pp) {}
+    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
+        const int k1 = blockIdx.x * C + seq;
+        constexpr int T = L / 32;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = make_float2(p.s[k1 + ((t + r * T) << p.log2N1)], 0.f);
+    }
+};
+
+// Column sink: multiply by the four-step twiddle exp(SIGN 2 pi i j2 k1 / N)
+// and write E[j2 * N1 + k1] (batch blockIdx.y at E + blockIdx.y * N).
+template <int L, int C, int SIGN>
+struct ExchSink {
+    struct Params { float2 *E; int log2N1; int log2N; };
+    const Params &p;
+    __device__ ExchSink(const Params &pp) : p(pp) {}
+    template <int R>
+    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
+        float2 *E = p.E + ((int64_t)blockIdx.y << p.log2N);
+        const int k1 = blockIdx.x * C + seq;
+        float2 w = unit_root<SIGN>((uint32_t)(b * k1), p.log2N);
+        const float2 step = unit_root<SIGN>((uint32_t)(stride * k1), p.log2N);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j2 = b + r * stride;
+            __stcg(&E[((int64_t)j2 << p.log2N1) + k1], cmul(v[r], w));
+            if (r + 1 < R) w = cmul(w, step);
+        }
+    }
+    __device__ __forceinline__ void finish(float2 *) const {}
+};
+
+// ---------------------------------------------------------------------------
+// Row (pass-2) source and generic sinks.  Sequence seq of CTA blockIdx.x is
+// row j2 = blockIdx.x * C + seq of E; its element k1 is E[j2 * N1 + k1].
+// ---------------------------------------------------------------------------
+template <int L, int C>
+struct RowSrc {
+    static constexpr bool kHalfZero = false;
+    struct Params { const float2 *E; int log2N1; int log2N; };
+    const Params &p;
+    __device__ RowSrc(const Params &pp) : p(pp) {}
+    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
+        const float2 *E = p.E + ((int64_t)blockIdx.y << p.log2N);
+        const int j2 = blockIdx.x * C + seq;
+        const float2 *row = E + ((int64_t)j2 << p.log2N1);
+        constexpr int T = L / 32;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = __ldcg(&row[t + r * T]);
+    }
+};
+
+// out[j2 + N2 j1] = v for indices < limit
+template <int L, int C>
+struct RowComplexOut {
+    struct Params { float2 *out; int log2N2; int64_t limit; };
+    const Params &p;
+    __device__ RowComplexOut(const Params &pp) : p(pp) {}
+    template <int R>
+    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
+        const int j2 = blockIdx.x * C + seq;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t j = j2 + ((int64_t)(b + r * stride) << p.log2N2);
+            if (j < p.limit) p.out[j] = v[r];
+        }
+    }
+    __device__ __forceinline__ void finish(float2 *) const {}
+};
+
+// s[j2 + N2 j1] = scale * Re(v)
+template <int L, int C>
+struct RowRealOut {
+    struct Params { float *s; int log2N2; float scale; };
+    const Params &p;
+    __device__ RowRealOut(const Params &pp) : p(pp) {}
+    template <int R>
+    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
+        const int j2 = blockIdx.x * C + seq;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t j = j2 + ((int64_t)(b + r * stride) << p.log2N2);
+            p.s[j] = p.scale * v[r].x;
+        }
+    }
+    __device__ __forceinline__ void finish(float2 *) const {}
+};
+
+}  // namespace mf

@@ -1,0 +1,200 @@
+// mf_prep.cu -- once-per-segment conditioning for Eq. (1) of arXiv:0906.4175:
+//   X_k = DFT(s)_k (own four-step FP32 FFT, forward sign), k = 0..N/2
+//   q_k = f_k^(-7/3) / S_k (FP64; S_k from Eq. (2) or a caller table)
+//   P_k = sum_{k' < k} q_k'  (FP64 exclusive prefix; sigma^2 of Eq. (4) for the
+//         band [k_lo, k_hi) is 4 df A^2 (P[k_hi] - P[k_lo]))
+//   W_k = alpha f_k^(-7/6) dt conj(X_k) / S_k, alpha = sqrt(4 df / P[N/2]),
+// so that raw_j = sum_band W_k e^{-i Psi_k} e^{2 pi i j k/N} gives
+// rho_j = |raw_j| sqrt(P[N/2] / (P[k_hi] - P[k_lo])) for any PSD scale.
+#include "mf_passes.cuh"
+
+namespace mf {
+
+// Eq. (2): S_n(f) = S0 [(4.49 x)^-56 + 0.16 x^-4.52 + 0.52 + 0.32 x^2], x = f/f0
+__device__ __forceinline__ double psd_eq2(double f, double f0, double S0) {
+    const double x = f / f0;
+    return S0 * (pow(4.49 * x, -56.0) + 0.16 * pow(x, -4.52) + 0.52 + 0.32 * x * x);
+}
+
+namespace {
+struct FwdOp {
+    const float *s;
+    float2 *exch, *X;
+    int log2N;
+    cudaStream_t st;
+    template <int N2, int N1>
+    cudaError_t run() {
+        constexpr int C1 = seqs_per_cta<N2>(N1);
+        constexpr int C2 = seqs_per_cta<N1>(N2);
+        const int log2N2 = log2_n2(log2N), log2N1 = log2N - log2N2;
+        typename ColRealSrc<N2, C1>::Params sp{s, log2N1};
+        typename ExchSink<N2, C1, -1>::Params kp{exch, log2N1, log2N};
+        cudaError_t e = run_pass<N2, C1, true, -1, ColRealSrc<N2, C1>, ExchSink<N2, C1, -1>>(
+            dim3(N1 / C1, 1), sp, kp, st);
+        if (e != cudaSuccess) return e;
+        typename RowSrc<N1, C2>::Params sp2{exch, log2N1, log2N};
+        typename RowComplexOut<N1, C2>::Params kp2{X, log2N2, ((int64_t)1 << (log2N - 1)) + 1};
+        return run_pass<N1, C2, false, -1, RowSrc<N1, C2>, RowComplexOut<N1, C2>>(dim3(N2 / C2, 1), sp2, kp2,
+                                                                                  st);
+    }
+};
+struct FwdAttrOp {
+    template <int N2, int N1>
+    cudaError_t run() {
+        constexpr int C1 = seqs_per_cta<N2>(N1);
+        constexpr int C2 = seqs_per_cta<N1>(N2);
+        cudaError_t e = set_pass_attrs<N2, C1, true, -1, ColRealSrc<N2, C1>, ExchSink<N2, C1, -1>>();
+        if (e != cudaSuccess) return e;
+        return set_pass_attrs<N1, C2, false, -1, RowSrc<N1, C2>, RowComplexOut<N1, C2>>();
+    }
+};
+}  // namespace
+
+static int ilog2_i64(int64_t n) {
+    int r = 0;
+    while ((int64_t)1 << (r + 1) <= n) ++r;
+    return r;
+}
+
+cudaError_t launch_forward_fft(const float *s, int64_t N, float2 *exch, float2 *X, cudaStream_t st) {
+    FwdOp op{s, exch, X, ilog2_i64(N), st};
+    return dispatch_split(op.log2N, op);
+}
+
+cudaError_t prep_kernel_attributes() {
+    for (int lg = 10; lg <= 22; ++lg) {
+        FwdAttrOp op;
+        cudaError_t e = dispatch_split(lg, op);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// q_k = f^(-7/3)/S_k for 1 <= k < N/2, q_0 = 0
+__global__ void k_psd_weights(const double *__restrict__ psd, double f0, double S0, int64_t N, double fs,
+                              double *__restrict__ q) {
+    const int64_t half = N / 2;
+    const double df = fs / (double)N;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k == 0) { q[0] = 0.0; continue; }
+        const double f = (double)k * df;
+        const double S = psd ? psd[k] : psd_eq2(f, f0, S0);
+        q[k] = pow(f, -7.0 / 3.0) / S;
+    }
+}
+
+cudaError_t launch_psd_weights(const float2 *X, const double *psd, double psd_f0, double psd_S0, int64_t N,
+                               double fs, double *q, cudaStream_t st) {
+    (void)X;
+    const int64_t half = N / 2;
+    int blocks = (int)((half + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_psd_weights<<<blocks, 256, 0, st>>>(psd, psd_f0, psd_S0, N, fs, q);
+    return cudaGetLastError();
+}
+
+// ---- deterministic FP64 exclusive prefix: P[0] = 0, P[i+1] = P[i] + q[i] ----
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 32;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+int64_t prefix_block_tmp_count(int64_t n) { return (n + kScanBlock - 1) / kScanBlock + 1; }
+
+__device__ double block_exclusive_scan_f64(double x, double *sh) {
+    // Hillis-Steele over 256 threads (fixed order -> deterministic)
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        const double y = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0.0;
+        __syncthreads();
+        sh[threadIdx.x] += y;
+        __syncthreads();
+    }
+    const double incl = sh[threadIdx.x];
+    __syncthreads();
+    return incl - x;
+}
+
+__global__ void k_scan_partials(const double *__restrict__ q, int64_t n, double *__restrict__ bsum) {
+    __shared__ double sh[kScanThreads];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanPer;
+    double s = 0.0;
+    for (int i = 0; i < kScanPer; ++i) {
+        const int64_t k = base + i;
+        if (k < n) s += q[k];
+    }
+    const double ex = block_exclusive_scan_f64(s, sh);
+    if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = ex + s;
+}
+
+__global__ void k_scan_blocksums(double *bsum, int nb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double run = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double v = bsum[b];
+        bsum[b] = run;
+        run += v;
+    }
+    bsum[nb] = run;
+}
+
+__global__ void k_scan_final(const double *__restrict__ q, int64_t n, const double *__restrict__ bsum,
+                             double *__restrict__ P) {
+    __shared__ double sh[kScanThreads];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanPer;
+    double s = 0.0;
+    for (int i = 0; i < kScanPer; ++i) {
+        const int64_t k = base + i;
+        if (k < n) s += q[k];
+    }
+    double run = bsum[blockIdx.x] + block_exclusive_scan_f64(s, sh);
+    if (blockIdx.x == 0 && threadIdx.x == 0) P[0] = 0.0;
+    for (int i = 0; i < kScanPer; ++i) {
+        const int64_t k = base + i;
+        if (k < n) {
+            run += q[k];
+            P[k + 1] = run;
+        }
+    }
+}
+
+cudaError_t launch_prefix_f64(const double *q, int64_t n, double *P, double *block_tmp, cudaStream_t st) {
+    const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
+    k_scan_partials<<<nb, kScanThreads, 0, st>>>(q, n, block_tmp);
+    k_scan_blocksums<<<1, 32, 0, st>>>(block_tmp, nb);
+    k_scan_final<<<nb, kScanThreads, 0, st>>>(q, n, block_tmp, P);
+    return cudaGetLastError();
+}
+
+// W_k = alpha f^(-7/6) dt conj(X_k)/S_k for 1 <= k < N/2, W_0 = 0
+__global__ void k_weight_data(const float2 *__restrict__ X, const double *__restrict__ psd, double f0, double S0,
+                              int64_t N, double fs, const double *__restrict__ P, SegConsts *consts,
+                              float2 *__restrict__ W) {
+    const int64_t half = N / 2;
+    const double df = fs / (double)N, dt = 1.0 / fs;
+    const double Ptot = P[half];
+    const double alpha = sqrt(4.0 * df / Ptot);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        consts->P_tot = Ptot;
+        consts->alpha = alpha;
+    }
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k == 0) { W[0] = make_float2(0.f, 0.f); continue; }
+        const double f = (double)k * df;
+        const double S = psd ? psd[k] : psd_eq2(f, f0, S0);
+        const double a = alpha * pow(f, -7.0 / 6.0) * dt / S;
+        const float2 x = X[k];
+        W[k] = make_float2((float)(a * (double)x.x), (float)(-a * (double)x.y));
+    }
+}
+
+cudaError_t launch_weight_data(const float2 *X, const double *psd, double psd_f0, double psd_S0, int64_t N,
+                               double fs, const double *P, SegConsts *consts, float2 *W, cudaStream_t st) {
+    const int64_t half = N / 2;
+    int blocks = (int)((half + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_weight_data<<<blocks, 256, 0, st>>>(X, psd, psd_f0, psd_S0, N, fs, P, consts, W);
+    return cudaGetLastError();
+}
+
+}  // namespace mf

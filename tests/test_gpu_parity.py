@@ -1,0 +1,298 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs: Eqs. (1), (3), (4) of arXiv:0906.4175 with the Sec. 1.1 templates.
+
+Every comparison uses RHO_TOL = 1e-4 on err_j = |rho_gpu - rho_ref| / max(rho_ref, 1).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from mfgb_testutil import (RHO_TOL, gpu_rho_series, oracle_rho_series, oracle_segment, peak_index_agrees,
+                           rho_err, trigger_sets_agree)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0906_4175_gb300 import build
+    build.build()
+    import paper_0906_4175_gb300 as m
+    oracle.build()
+    return m
+
+
+def _full_compare(mf, m1, m2, spec, f_low=40.0, phase_mode=0, tol=RHO_TOL):
+    s32, s64 = oracle_segment(spec, f_low)
+    import torch
+    bank = mf.Bank(m1, m2, f_low=f_low, phase_mode=phase_mode)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    rho_g, z_g, peaks = gpu_rho_series(mf, bank, seg, len(m1), spec.N)
+    ref = oracle_rho_series(m1, m2, s64, spec.fs, f_low)
+    worst = 0.0
+    for t, r in enumerate(ref):
+        e = rho_err(rho_g[t], r["rho"])
+        worst = max(worst, float(e.max()))
+        jr = int(np.argmax(r["rho"]))
+        assert peak_index_agrees(r["rho"], int(peaks["j"][t]), jr), (t, peaks["j"][t], jr)
+        assert abs(peaks["rho"][t] - r["rho"][jr]) / max(r["rho"][jr], 1) <= tol
+        # z itself (Eq. 1, amplitude A = Mc^(5/6)): relative to sigma
+        ez = np.abs(z_g[t] - r["z"]) / r["sigma"]
+        assert ez.max() <= tol, (t, ez.max())
+    assert worst <= tol, worst
+    return worst
+
+
+def test_tiny_workload_full_series(mf):
+    """16 templates, N = 2^16, fs = 2048, one injection: every rho_j."""
+    wl = workloads.tiny(0)
+    _full_compare(mf, wl.m1, wl.m2, wl.segments[0])
+
+
+@pytest.mark.parametrize("lg,fs", [(10, 4096.0), (11, 4096.0), (12, 4096.0), (13, 2048.0), (14, 4096.0),
+                                   (15, 4096.0), (17, 4096.0), (18, 4096.0)])
+def test_sizes_full_series(mf, lg, fs):
+    """Every supported FFT split from 32x32 up to 512x512 (ragged tails: the
+    heaviest templates cut at f_isco far below Nyquist)."""
+    N = 1 << lg
+    wl = workloads.small(seed=lg, N=N, fs=fs, n_templates=5, m_lo=1.2, m_hi=12.0)
+    _full_compare(mf, wl.m1, wl.m2, wl.segments[0])
+
+
+def test_largest_segments_sampled(mf):
+    """N = 2^21 and 2^22 (1024x2048, 2048x2048 splits), two templates each."""
+    import torch
+    for lg in (21, 22):
+        N = 1 << lg
+        wl = workloads.small(seed=lg, N=N, fs=4096.0, n_templates=2, m_lo=1.5, m_hi=8.0)
+        spec = wl.segments[0]
+        s32, s64 = oracle_segment(spec)
+        bank = mf.Bank(wl.m1, wl.m2)
+        seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+        peaks, trig, n = mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 16)
+        assert bank.check() == 0
+        pk = mf.peaks_to_numpy(peaks)
+        ref = oracle_rho_series(wl.m1, wl.m2, s64, spec.fs)
+        tr = mf.triggers_to_numpy(trig, n)
+        for t, r in enumerate(ref):
+            jr = int(np.argmax(r["rho"]))
+            assert peak_index_agrees(r["rho"], int(pk["j"][t]), jr)
+            assert abs(pk["rho"][t] - r["rho"][jr]) / max(1, r["rho"][jr]) <= RHO_TOL
+        gk = {(int(a), int(b)) for a, b in zip(tr["tmpl"], tr["j"])}
+        assert trigger_sets_agree(gk, {t: r["rho"] for t, r in enumerate(ref)}, 5.0) == []
+        for x in tr:
+            assert abs(x["rho"] - ref[x["tmpl"]]["rho"][x["j"]]) / max(1, x["rho"]) <= RHO_TOL
+
+
+def test_phase_fp64_mode_matches(mf):
+    wl = workloads.small(seed=3, N=1 << 14, fs=4096.0, n_templates=4)
+    _full_compare(mf, wl.m1, wl.m2, wl.segments[0], phase_mode=mf.MF_PHASE_FP64)
+
+
+def test_scale_workload_sampled(mf):
+    """The benchmark's workload (1024 templates, N = 2^20, 8 injections, thr 6)
+    in the benchmark's launch configuration; peaks and triggers of a sample of
+    templates (those nearest the injections plus random ones) against the oracle."""
+    import torch
+    wl = workloads.scale(0)
+    spec = wl.segments[0]
+    s32, s64 = oracle_segment(spec)
+    bank = mf.Bank(wl.m1, wl.m2)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    peaks, trig, n = mf.filter_bank(bank, [seg], wl.threshold, trig_cap=1 << 22)
+    assert bank.check() == 0
+    pk = mf.peaks_to_numpy(peaks)
+    tr = mf.triggers_to_numpy(trig, n)
+    assert tr.size == int(n.item())
+    # sorted by (tmpl, j)
+    key = tr["tmpl"].astype(np.int64) * spec.N + tr["j"]
+    assert np.all(np.diff(key) > 0)
+    # sample: the loudest template per injection, plus 6 random templates
+    rng = np.random.default_rng(0)
+    loud = list(np.argsort(-pk["rho"])[:4])
+    sample = sorted(set(int(x) for x in loud + list(rng.choice(wl.n_templates, 6, replace=False))))
+    ref = oracle_rho_series(wl.m1[sample], wl.m2[sample], s64, spec.fs)
+    ref_by_t = {}
+    for t, r in zip(sample, ref):
+        jr = int(np.argmax(r["rho"]))
+        assert peak_index_agrees(r["rho"], int(pk["j"][t]), jr), (t, pk["j"][t], jr)
+        assert abs(pk["rho"][t] - r["rho"][jr]) / max(1, r["rho"][jr]) <= RHO_TOL
+        ref_by_t[t] = r["rho"]
+    gk = {(int(a), int(b)) for a, b in zip(tr["tmpl"], tr["j"]) if int(a) in ref_by_t}
+    assert trigger_sets_agree(gk, ref_by_t, wl.threshold) == []
+    for x in tr:
+        if int(x["tmpl"]) in ref_by_t:
+            r = ref_by_t[int(x["tmpl"])][x["j"]]
+            assert abs(x["rho"] - r) / max(1, r) <= RHO_TOL
+    # injections at lattice masses are recovered near their SNR
+    assert pk["rho"].max() > 8.0
+
+
+def test_synth_matches_oracle(mf):
+    for N, fs, n_inj in [(1 << 12, 4096.0, 1), (1 << 16, 2048.0, 3), (1 << 20, 4096.0, 8)]:
+        wl = workloads.small(seed=N, N=N, fs=fs, n_templates=1, n_inj=n_inj)
+        spec = wl.segments[0]
+        g = spec.normals()
+        ref = oracle.synth(g, N, fs, 40.0, spec.injections)
+        got = mf.synth_segment(g, N, fs, 40.0, spec.injections).cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref).max() / np.sqrt(np.mean(ref ** 2))
+        assert err < 2e-5, (N, err)
+
+
+def test_determinism_and_order_independence(mf):
+    import torch
+    wl = workloads.small(seed=5, N=1 << 15, fs=4096.0, n_templates=12)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 18)]
+    b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 18)]
+    for x, y in zip(a, b):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    perm = np.random.default_rng(1).permutation(12)
+    bank2 = mf.Bank(wl.m1[perm], wl.m2[perm])
+    p2, t2, n2 = mf.filter_bank(bank2, [seg], 4.0, trig_cap=1 << 18)
+    pa = a[0].view(mf.PEAK_DTYPE).reshape(-1)
+    pb = mf.peaks_to_numpy(p2)
+    assert np.array_equal(pa[perm].view(np.uint8), pb.view(np.uint8))
+    assert int(n2.item()) == int(a[2][0])
+
+
+def test_mirror_masses_identical(mf):
+    import torch
+    spec = workloads.small(seed=9, N=1 << 14).segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank([1.3, 2.7], [2.7, 1.3])
+    p, _, _ = mf.filter_bank(bank, [seg], 100.0, trig_cap=0)
+    pk = mf.peaks_to_numpy(p)
+    assert pk[0].tobytes() == pk[1].tobytes()
+
+
+def test_overflow_keeps_true_count(mf):
+    import torch
+    spec = workloads.small(seed=2, N=1 << 13).segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank([1.4, 2.0, 3.0], [1.4, 1.5, 2.5])
+    _, _, n_full = mf.filter_bank(bank, [seg], 1.0, trig_cap=1 << 16)
+    assert bank.check() == 0
+    total = int(n_full.item())
+    assert total > 100
+    _, trig, n = mf.filter_bank(bank, [seg], 1.0, trig_cap=37)
+    assert bank.check() == mf._native.MF_EOVERFLOW
+    assert int(n.item()) == total
+    tr = mf.triggers_to_numpy(trig, n)
+    assert tr.size == 37
+    key = tr["tmpl"].astype(np.int64) * spec.N + tr["j"]
+    assert np.all(np.diff(key) > 0)
+    assert np.all(tr["rho"] > 1.0)
+    # nothing above an enormous threshold
+    _, _, n0 = mf.filter_bank(bank, [seg], 1e6, trig_cap=8)
+    assert bank.check() == 0 and int(n0.item()) == 0
+
+
+def test_multi_segment_call_equals_separate_calls(mf):
+    import torch
+    specs = [workloads.small(seed=s, N=N, fs=4096.0).segments[0] for s, N in ((1, 1 << 12), (2, 1 << 14))]
+    segs = [mf.Segment(torch.from_numpy(oracle_segment(sp)[0]).cuda(), sp.fs) for sp in specs]
+    m1 = np.array([1.3, 1.9, 2.4, 3.3, 1.1])
+    m2 = np.array([1.2, 1.7, 2.4, 1.5, 1.0])
+    bank = mf.Bank(m1, m2)
+    p, t, n = mf.filter_bank(bank, segs, 3.5, trig_cap=1 << 16)
+    pk = mf.peaks_to_numpy(p).reshape(5, 2)
+    tr = mf.triggers_to_numpy(t, n)
+    for si, sg in enumerate(segs):
+        p1, t1, n1 = mf.filter_bank(bank, [sg], 3.5, trig_cap=1 << 16)
+        assert np.array_equal(mf.peaks_to_numpy(p1).view(np.uint8), pk[:, si].copy().view(np.uint8))
+        t1 = mf.triggers_to_numpy(t1, n1)
+        sub = tr[tr["seg"] == si]
+        assert np.array_equal(sub[["tmpl", "j", "rho", "z_re", "z_im"]], t1[["tmpl", "j", "rho", "z_re", "z_im"]])
+
+
+def test_ragged_batches(mf, monkeypatch):
+    """A bank size that is not a multiple of the templates in flight."""
+    import torch
+    wl = workloads.small(seed=4, N=1 << 13, fs=4096.0, n_templates=13)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    ref = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 3.0, trig_cap=1 << 16)[0])
+    monkeypatch.setenv("MFGB_BATCH", "5")
+    got = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 3.0, trig_cap=1 << 16)[0])
+    assert np.array_equal(ref.view(np.uint8), got.view(np.uint8))
+
+
+def test_psd_table_and_scale(mf):
+    """A caller PSD table: with the data fixed, S_n -> 3.7 S_n scales z by 1/3.7 and
+    sigma by 1/sqrt(3.7), so rho -> rho/sqrt(3.7).  Data and PSD scaled together
+    (physical units, S0 = 9e-46) leave rho unchanged."""
+    import torch
+    spec = workloads.small(seed=8, N=1 << 14).segments[0]
+    s32, s64 = oracle_segment(spec)
+    N, fs = spec.N, spec.fs
+    bank = mf.Bank([1.5, 2.5], [1.4, 1.1])
+    base = mf.peaks_to_numpy(mf.filter_bank(bank, [mf.Segment(torch.from_numpy(s32).cuda(), fs)], 100.0, 0)[0])
+    S = oracle.psd_bins(N, fs) * 3.7
+    S[0] = 1.0
+    tab = mf.peaks_to_numpy(mf.filter_bank(bank, [mf.Segment(torch.from_numpy(s32).cuda(), fs, psd=S)], 100.0, 0)[0])
+    assert np.max(np.abs(tab["rho"] * np.sqrt(3.7) - base["rho"]) / base["rho"]) < 1e-5
+    assert np.array_equal(tab["j"], base["j"])
+    phys = s32 * np.float32(3e-23)
+    ph = mf.peaks_to_numpy(mf.filter_bank(bank, [mf.Segment(torch.from_numpy(phys).cuda(), fs, psd_S0=9e-46)],
+                                          100.0, 0)[0])
+    assert np.max(np.abs(ph["rho"] - base["rho"]) / base["rho"]) < 1e-4
+
+
+def test_refine_matches_oracle(mf):
+    """mf_refine_triggers: rho^2 and its gradient against the oracle's direct
+    sum and analytic gradient."""
+    import torch
+    N, fs = 1 << 16, 4096.0
+    spec = workloads.SegmentSpec(N, fs, 123)
+    inj = np.zeros(1, dtype=oracle.INJ_DTYPE)
+    inj[0] = (1.7, 1.3, 12.0, 5000, 0.4)
+    spec.injections = inj
+    s32, s64 = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), fs)
+    t0 = ((N - 5000) % N) / fs
+    theta = np.array([[1.7, 1.3, t0], [1.72, 1.31, t0 + 0.3 / fs], [1.65, 1.36, t0 - 1.7 / fs],
+                      [2.5, 1.2, 1.0]])
+    lo_hi = [oracle.band(N, fs, 40.0, oracle.f_isco(a, b)) for a, b, _ in theta]
+    ref_obj, ref_grad = oracle.refine(theta, s64, fs, 40.0, bands=np.array(lo_hi))
+    th = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    obj, grad = mf.refine(seg, th)
+    obj = obj.cpu().numpy()
+    grad = grad.cpu().numpy()
+    assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < 2e-4), (obj, ref_obj)
+    scale = np.abs(ref_grad).max(axis=0)
+    assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * scale), (grad, ref_grad)
+    # explicit band gives the same as the default band at the same masses
+    band = torch.tensor(np.array(lo_hi), dtype=torch.int64, device="cuda")
+    obj2, grad2 = mf.refine(seg, th, band=band)
+    assert np.array_equal(obj2.cpu().numpy(), obj)
+
+
+def test_refine_autograd_function(mf):
+    import torch
+    N, fs = 1 << 14, 4096.0
+    spec = workloads.SegmentSpec(N, fs, 7)
+    inj = np.zeros(1, dtype=oracle.INJ_DTYPE)
+    inj[0] = (1.5, 1.4, 15.0, 1000, 0.0)
+    spec.injections = inj
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), fs)
+    theta = torch.tensor([[1.52, 1.39, ((N - 1000) % N) / fs + 0.2 / fs]], dtype=torch.float64,
+                         device="cuda", requires_grad=True)
+    J = mf.RefineFn.apply(theta, seg)
+    (3.0 * J.sum()).backward()
+    _, g = mf.refine(seg, theta.detach())
+    assert torch.allclose(theta.grad, 3.0 * g)
