@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the bank filter (Eqs. 1, 3, 4 of arXiv:0906.4175) on one GB300.
+
+A step is one pass of the hot path over the 1024-template, N = 2^20 workload
+(32x32 mass lattice over [1, 3] Msun, fs = 4096 Hz, 256 s of seeded coloured
+Gaussian noise with 8 injections, threshold rho = 6): segment conditioning
+(mf_segment_upload) plus the bank filter (mf_filter_bank).  Inputs are resident
+in HBM when timing starts; L2 is flushed (256 MiB write) before every timed
+step; each step is timed with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mfgb|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on a bounded sample of the same workload.  Under torchrun (N > 1) every rank
+filters its own replica of the workload (weak scaling, no data-path
+collective); rank 0 prints the JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "templates/s filtered at N=2^20 (FP32), % HBM roofline, max ρ rel err vs FP64"
+UNIT = "templates/s"
+WORKLOAD = "1024 templates (32x32 lattice, m1,m2 in [1,3] Msun), 1 segment N=2^20 at 4096 Hz, 8 injections, thr 6"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cu", "mf_internal.h"]
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mfgb", choices=["mfgb", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _hbm_peak():
+    try:
+        with open(PEAKS_PATH) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_0906_4175_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_stage: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kernel_stage)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"]), float(e.get("templates_per_launch", 0)) or None
+    except Exception:
+        pass
+    return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="mfgb_clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def cpu_baseline(wl, cpu_seconds: float, gpu_check=None):
+    """Time the FP64 oracle as it stands on a bounded template sample of the
+    workload (its own FP64 synthesis of the same seeded segment), on all host
+    cores.  If gpu_check is given, also measure the GPU's rho error on the
+    same input and sample."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    spec = wl.segments[0]
+    s = oracle.synth(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections).astype(np.float32)
+    s64 = s.astype(np.float64)
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(wl.n_templates)
+    # calibrate with one template on all cores (OpenMP across templates -> one thread busy)
+    t0 = time.perf_counter()
+    oracle.filter_bank(wl.m1[order[:1]], wl.m2[order[:1]], s64, spec.fs, wl.f_low, wl.threshold, n_threads=1)
+    t1 = time.perf_counter() - t0
+    ncores = os.cpu_count() or 1
+    n_s = int(max(1, min(wl.n_templates, round(cpu_seconds / max(t1, 1e-3)))))
+    n_s = max(ncores, (n_s // ncores) * ncores) if n_s >= ncores else n_s
+    n_s = min(n_s, wl.n_templates)
+    sel = np.sort(order[:n_s])
+    t0 = time.perf_counter()
+    peaks, trig, ntr, used = oracle.filter_bank(wl.m1[sel], wl.m2[sel], s64, spec.fs, wl.f_low, wl.threshold)
+    dt = time.perf_counter() - t0
+    res = {"value": n_s / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+           "sample": "%d of %d templates (seeded), full N=2^20 segment, FP64 radix-2 FFT, %.1f s wall on %d threads"
+                     % (n_s, wl.n_templates, dt, used)}
+    acc = None
+    if gpu_check is not None:
+        acc = gpu_check(s, sel, peaks)
+    return res, acc
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import workloads
+    wl = workloads.scale(0)
+    import numpy as np
+    import oracle
+    oracle.build()
+    spec = wl.segments[0]
+    s64 = oracle.synth(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections).astype(np.float32).astype(np.float64)
+    ncores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.filter_bank(wl.m1[:1], wl.m2[:1], s64, spec.fs, wl.f_low, wl.threshold, n_threads=1)
+    t1 = time.perf_counter() - t0
+    # each step: a bounded sample sized so that warmup + steps end within a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    per_step = int(max(1, min(wl.n_templates, ncores * max(1, int(budget / max(t1, 1e-3))))))
+    per_step = min(per_step, wl.n_templates)
+    rng = np.random.default_rng(0)
+    times, used = [], 1
+    for k in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(wl.n_templates, per_step, replace=False))
+        t0 = time.perf_counter()
+        _, _, _, used = oracle.filter_bank(wl.m1[sel], wl.m2[sel], s64, spec.fs, wl.f_low, wl.threshold)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections)",
+            "config": {"workload": WORKLOAD, "step_sample_templates": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle",
+                             "sample": "%d random templates of 1024 per step, full N=2^20 segment" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+    from paper_0906_4175_gb300 import build as _b
+    _b.build()
+    import paper_0906_4175_gb300 as mf
+    import workloads
+
+    wl = workloads.scale(seed=rank)
+    spec = wl.segments[0]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    # inputs: seeded coloured noise + injections synthesised on the device by the library
+    s_dev = mf.synth_segment(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections)
+    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
+    cap = 1 << 22
+    outb = (torch.empty((wl.n_templates, 4), dtype=torch.float32, device=dev),
+            torch.empty((cap, 6), dtype=torch.float32, device=dev),
+            torch.zeros(1, dtype=torch.int64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    segs = []
+
+    def step():
+        seg = mf.Segment(s_dev, spec.fs)
+        mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
+        segs.append(seg)   # keep alive until the stream has drained
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert bank.check() == 0
+    segs.clear()
+    n_trig = int(outb[2].item())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    bank.profile(True)
+    l0 = mf.launch_count()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = mf.launch_count() - l0
+    clocks = sampler.stop()
+    prof = bank.profile_read()
+    bank.profile(False)
+    segs.clear()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    value = world * wl.n_templates * args.steps / (tot_ms / 1e3)
+
+    # roofline of the dominant kernel (largest share of the filter's device time)
+    stages = {k: v for k, v in prof.items() if v[2] > 0}
+    dom = max(stages, key=lambda k: stages[k][0])
+    d_ms, d_bytes, d_n = stages[dom]
+    peak, peak_kind = _hbm_peak()
+    achieved = d_bytes / (d_ms / 1e3) / 1e9
+    traffic, _ = _ncu_traffic(dom)
+    tmpl_per_launch = wl.n_templates * args.steps / max(1, d_n) if dom in ("pass1", "pass2", "anchors", "fused") else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": d_bytes / max(1, d_n), "launches": d_n,
+            "avg_launch_ms": d_ms / max(1, d_n), "templates_per_launch": tmpl_per_launch,
+            "stage_share": {k: v[0] / sum(x[0] for x in stages.values()) for k, v in stages.items()}}
+    # whole-path roofline with the per-template model B = 8 K + 16 N + 24 n_trig
+    b_total = sum(v[1] for k, v in prof.items() if k in ("pass1", "pass2", "fused")) + 24.0 * n_trig * args.steps
+    path = {"model_bytes_per_template": b_total / (wl.n_templates * args.steps),
+            "achieved_gbs": b_total / (tot_ms / 1e3) / 1e9, "frac": b_total / (tot_ms / 1e3) / 1e9 / peak}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    s_host = torch.empty(spec.N, dtype=torch.float32, pin_memory=True)
+    s_host.copy_(s_dev.cpu())
+    peaks_h = torch.empty((wl.n_templates, 4), dtype=torch.float32, pin_memory=True)
+    ntr_h = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    trig_h = torch.empty((cap, 6), dtype=torch.float32, pin_memory=True)
+    d2h = []
+    e2e_ms = []
+    for k in range(args.e2e_steps + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seg = mf.Segment(s_host.numpy(), spec.fs)
+        mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
+        peaks_h.copy_(outb[0], non_blocking=True)
+        ntr_h.copy_(outb[2], non_blocking=True)
+        torch.cuda.synchronize()
+        n = min(int(ntr_h.item()), cap)
+        trig_h[:n].copy_(outb[1][:n], non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        seg.close()
+        if k >= 2:
+            e2e_ms.append(dt * 1e3)
+            d2h.append(peaks_h.numel() * 4 + 8 + n * 24)
+    e2e_tot = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e = {"value": world * wl.n_templates * len(e2e_ms) / (e2e_tot / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)),
+           "includes": "host s -> mf_segment_upload (H2D inside), mf_filter_bank, D2H peaks + n_trig + triggers"}
+
+    cpu = None
+    acc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        def gpu_check(s32, sel, opeaks):
+            b2 = mf.Bank(wl.m1[sel], wl.m2[sel], f_low=wl.f_low)
+            sg = mf.Segment(torch.from_numpy(s32).to(dev), spec.fs)
+            p, _, _ = mf.filter_bank(b2, [sg], wl.threshold, trig_cap=1 << 16)
+            pk = mf.peaks_to_numpy(p)
+            err = np.abs(pk["rho"].astype(np.float64) - opeaks["rho"]) / np.maximum(opeaks["rho"], 1.0)
+            # full rho series of two templates (threshold 0 returns every sample)
+            b3 = mf.Bank(wl.m1[sel[:2]], wl.m2[sel[:2]], f_low=wl.f_low)
+            p3, t3, n3 = mf.filter_bank(b3, [sg], 0.0, trig_cap=2 * spec.N)
+            tr = mf.triggers_to_numpy(t3, n3)
+            import oracle
+            S = oracle.psd_bins(spec.N, spec.fs)
+            st = oracle.data_spectrum(s32.astype(np.float64), spec.fs)
+            series = 0.0
+            for i in range(2):
+                ref = oracle.filter_template(float(wl.m1[sel[i]]), float(wl.m2[sel[i]]), st, S, spec.N, spec.fs,
+                                             wl.f_low)["rho"]
+                got = tr["rho"][tr["tmpl"] == i].astype(np.float64)
+                series = max(series, float(np.max(np.abs(got - ref) / np.maximum(ref, 1.0))))
+            return {"peak_max": float(err.max()), "peak_median": float(np.median(err)),
+                    "series_max": series, "templates": int(len(sel)),
+                    "measure": "|rho_gpu - rho_fp64| / max(rho_fp64, 1)"}
+        cpu, acc = cpu_baseline(wl, args.cpu_seconds, gpu_check)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections; no LIGO data)",
+            "config": {"workload": WORKLOAD, "templates": wl.n_templates, "N": spec.N, "fs": spec.fs,
+                       "segments": 1, "threshold": wl.threshold, "n_trig_per_step": n_trig,
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "step": "mf_segment_upload (device s) + mf_filter_bank",
+                       "phase": "FP64 anchors + FP32 Taylor; FFT FP32"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "path_roofline": path,
+            "rho_err": acc, "cpu_baseline": cpu, "wall_s_timed": wall}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

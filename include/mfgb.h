@@ -169,6 +169,40 @@ int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, const doubl
                        int64_t n, const int64_t *band, double *obj, double *grad,
                        void *cuda_stream);
 
+/* ---- measurement hooks (not part of the paper's method) ------------------ */
+
+/* Total number of kernels this library has launched in this process (host
+ * counter, incremented at every launch on any stream). */
+int mf_launch_count(int64_t *n);
+
+/* Stages of mf_filter_bank timed by mf_bank_profile_read. */
+#define MF_STAGE_SETUP   0  /* per-unit band / sigma set-up */
+#define MF_STAGE_ANCHORS 1  /* FP64 phase anchors */
+#define MF_STAGE_PASS1   2  /* template generation + weighting + column IFFTs */
+#define MF_STAGE_PASS2   3  /* row IFFTs + rho epilogue */
+#define MF_STAGE_FINAL   4  /* peak reduction + trigger sort */
+#define MF_STAGE_FUSED   5  /* persistent scheduler: anchors + pass 1 + pass 2 + peaks in one launch */
+#define MF_N_STAGES      6
+
+/* mf_bank_profile -- when on != 0, later mf_filter_bank calls on this bank
+ * record a CUDA event pair around every kernel launch (on the call's stream)
+ * and the algorithmic bytes each launch moves (band reads, exchange write
+ * and read; triggers excluded).  mf_bank_profile_read synchronises the events
+ * recorded so far and returns, per stage, the summed device milliseconds,
+ * bytes and launch counts (host arrays of MF_N_STAGES), then clears them. */
+int mf_bank_profile(mf_bank bank, int on);
+
+/* mf_bank_debug_stall -- test hook for the bounded device-side waits of the
+ * persistent scheduler (segments with N >= 2^13).  With unit >= 0, later
+ * mf_filter_bank calls make the row-FFT tiles of that template wait for a
+ * completion count that is never reached; after spin_limit back-off
+ * iterations (each <= ~1 us; <= 0 restores the default of 4e6) the kernel sets
+ * its abort flag and every block returns, so mf_bank_check then reports
+ * MF_ETIMEOUT and the outputs of that call are invalid.  unit < 0 turns the
+ * hook off.  Nothing faults: the GPU context stays usable. */
+int mf_bank_debug_stall(mf_bank bank, int64_t unit, int64_t spin_limit);
+int mf_bank_profile_read(mf_bank bank, double *ms, double *bytes, int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,9 +64,27 @@ class Bank:
     def handle(self):
         return self._h
 
-    def check(self, stream=None) -> int:
-        """mf_bank_check: sync and return MF_OK / MF_EOVERFLOW (raises on timeout)."""
-        return check(_native.lib().mf_bank_check(self._h, _stream_ptr(stream)), allow=(MF_EOVERFLOW,))
+    def check(self, stream=None, allow_timeout: bool = False) -> int:
+        """mf_bank_check: sync and return MF_OK / MF_EOVERFLOW (raises on timeout unless allowed)."""
+        allow = (MF_EOVERFLOW, MF_ETIMEOUT) if allow_timeout else (MF_EOVERFLOW,)
+        return check(_native.lib().mf_bank_check(self._h, _stream_ptr(stream)), allow=allow)
+
+    def debug_stall(self, unit: int, spin_limit: int = 0):
+        """Test hook (mf_bank_debug_stall): make a unit's bounded wait run out."""
+        check(_native.lib().mf_bank_debug_stall(self._h, int(unit), int(spin_limit)))
+
+    def profile(self, on: bool = True):
+        """Record per-kernel CUDA events in later filter_bank calls (mf_bank_profile)."""
+        check(_native.lib().mf_bank_profile(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{stage: (ms, algorithmic bytes, launches)} since the last read."""
+        ns = len(_native.STAGES)
+        ms = (ctypes.c_double * ns)()
+        by = (ctypes.c_double * ns)()
+        nl = (ctypes.c_int64 * ns)()
+        check(_native.lib().mf_bank_profile_read(self._h, ms, by, nl))
+        return {name: (ms[i], by[i], nl[i]) for i, name in enumerate(_native.STAGES)}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -78,6 +96,13 @@ class Bank:
             self.close()
         except Exception:
             pass
+
+
+def launch_count() -> int:
+    """Kernels launched by libmfgb in this process so far."""
+    n = ctypes.c_int64()
+    check(_native.lib().mf_launch_count(ctypes.byref(n)))
+    return int(n.value)
 
 
 class Segment:

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +19,7 @@ cudaError_t filter_kernel_attributes();
 cudaError_t prep_kernel_attributes();
 cudaError_t synth_kernel_attributes();
 cudaError_t refine_kernel_attributes();
+cudaError_t persist_kernel_attributes();
 }  // namespace mf
 
 using namespace mf;
@@ -48,6 +50,14 @@ static int set_err(int code, const char *fmt, ...) {
     } while (0)
 
 extern "C" const char *mf_last_error(void) { return g_err; }
+
+static std::atomic<int64_t> g_launches{0};
+static void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" int mf_launch_count(int64_t *n) {
+    if (!n) return set_err(MF_EINVAL, "NULL argument");
+    *n = g_launches.load();
+    return MF_OK;
+}
 extern "C" const char *mf_version(void) { return "mfgb 0.1 (sm_103a)"; }
 
 // One-time per-device kernel attribute set-up (dynamic shared memory > 48 KB).
@@ -60,6 +70,7 @@ static int ensure_device_init() {
     if (std::find(done.begin(), done.end(), dev) != done.end()) return MF_OK;
     MF_CUDA(filter_kernel_attributes());
     MF_CUDA(prep_kernel_attributes());
+    MF_CUDA(persist_kernel_attributes());
     MF_CUDA(synth_kernel_attributes());
     MF_CUDA(refine_kernel_attributes());
     done.push_back(dev);
@@ -105,28 +116,61 @@ struct Workspace {
     UnitInfo *units = nullptr;
     float2 *exch = nullptr;
     float4 *anchors = nullptr;
+    float *anchors4 = nullptr;
     float4 *partials = nullptr;
     mf_trigger *staged = nullptr;
     uint64_t *keys = nullptr, *keys_tmp = nullptr;
     uint32_t *idx_a = nullptr, *idx_b = nullptr;
     unsigned long long *counter = nullptr;
     int *status = nullptr;
+    unsigned *ctl = nullptr;      // persistent scheduler: [0] head, [1] abort, then doneA, done1, done2 per unit
+    int2 *items = nullptr;        // persistent scheduler work queue
+    int64_t items_cap = 0;
+    int64_t items_key[4] = {-1, -1, -1, -1};   // (units, nA, n1, n2) the device queue was built for
+    int64_t items_n = 0;
     void release() {
-        cudaFree(units); cudaFree(exch); cudaFree(anchors); cudaFree(partials);
+        cudaFree(units); cudaFree(exch); cudaFree(anchors); cudaFree(anchors4); cudaFree(partials);
         cudaFree(staged); cudaFree(keys); cudaFree(keys_tmp); cudaFree(idx_a); cudaFree(idx_b);
-        cudaFree(counter); cudaFree(status);
+        cudaFree(counter); cudaFree(status); cudaFree(ctl); cudaFree(items);
         *this = Workspace();
     }
+};
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+    double bytes;
 };
 
 struct mf_bank_s {
     int64_t n = 0;
     mf_bank_params params{};
     double *d_tmpl = nullptr;
-    double B1 = 0.0, B4 = 0.0, fisco_min = 0.0;
+    std::vector<double> fisco;   // host copy of f_isco per template (profiling byte counts)
+    double B1 = 0.0, B5 = 0.0, fisco_min = 0.0;
     int device = 0;
     Workspace ws;
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    int64_t stall_unit = -1;          // test hook (mf_bank_debug_stall)
+    long long spin_limit = 4000000;   // bounded-wait iterations, back-off <= ~1 us each
 };
+
+// Records an event before a launch when profiling; returns the record index or -1.
+static int prof_begin(mf_bank_s *b, int stage, double bytes, cudaStream_t st) {
+    if (!b->prof_on) return -1;
+    ProfRec r;
+    r.stage = stage;
+    r.bytes = bytes;
+    if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&r.b) != cudaSuccess) { cudaEventDestroy(r.a); return -1; }
+    cudaEventRecord(r.a, st);
+    b->prof.push_back(r);
+    return (int)b->prof.size() - 1;
+}
+static void prof_end(mf_bank_s *b, int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(b->prof[idx].b, st);
+}
 
 struct mf_segment_s {
     int64_t N = 0;
@@ -169,14 +213,14 @@ extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, con
     int r0 = ensure_device_init();
     if (r0) return r0;
     std::vector<double> rec((size_t)n * kTmplStride);
-    double B1 = 0.0, B4 = 0.0, fmin = INFINITY;
+    double B1 = 0.0, B5 = 0.0, fmin = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         if (!(m1[i] > 0.0) || !(m2[i] > 0.0) || !isfinite(m1[i]) || !isfinite(m2[i]))
             return set_err(MF_EINVAL, "template %lld: masses must be finite and > 0", (long long)i);
         double *r = &rec[(size_t)i * kTmplStride];
         template_constants(m1[i], m2[i], r);
         B1 = std::max(B1, psi_deriv_bound(r, p.f_low, 1));
-        B4 = std::max(B4, psi_deriv_bound(r, p.f_low, 4));
+        B5 = std::max(B5, psi_deriv_bound(r, p.f_low, 5));
         fmin = std::min(fmin, r[TF_FISCO]);
     }
     mf_bank b = new (std::nothrow) mf_bank_s();
@@ -184,8 +228,10 @@ extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, con
     b->n = n;
     b->params = p;
     b->B1 = B1;
-    b->B4 = B4;
+    b->B5 = B5;
     b->fisco_min = fmin;
+    b->fisco.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) b->fisco[(size_t)i] = rec[(size_t)i * kTmplStride + TF_FISCO];
     cudaGetDevice(&b->device);
     cudaError_t e = cudaMalloc(&b->d_tmpl, sizeof(double) * rec.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tmpl, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice);
@@ -201,6 +247,7 @@ extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, con
 
 extern "C" int mf_bank_destroy(mf_bank b) {
     if (!b) return MF_OK;
+    for (auto &r : b->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     b->ws.release();
     cudaFree(b->d_tmpl);
     delete b;
@@ -260,6 +307,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     if (e == cudaSuccess) e = launch_psd_weights(X, psd_dev, psd_f0, psd_S0, N, fs, q, st);
     if (e == cudaSuccess) e = launch_prefix_f64(q, half, g->P, btmp, st);
     if (e == cudaSuccess) e = launch_weight_data(X, psd_dev, psd_f0, psd_S0, N, fs, g->P, g->consts, g->W, st);
+    if (e == cudaSuccess) count_launches(7);   // 2 FFT passes, weights, 3 scan kernels, weighting
     if (s_dev) cudaFreeAsync(s_dev, st);
     if (psd_dev) cudaFreeAsync(psd_dev, st);
     if (exch) cudaFreeAsync(exch, st);
@@ -309,9 +357,10 @@ static SegDev seg_dev(const mf_segment_s *g) {
 }
 
 // Anchor spacing D = 2^log2D for a (bank, segment): the largest power of two
-// (<= 256) for which the cubic-Taylor remainder max|psi''''| (D/2)^4/24 stays
-// below 5e-7 turns and |psi'| D/2 below 8 turns (FP32 magnitude), both bounded
-// at f_low over the whole bank.
+// (<= 256) for which the quartic-Taylor remainder max|d^5 psi/dk^5| (D/2)^5/120
+// stays below 5e-7 turns and |d psi/dk| D/2 below 16 turns (FP32 magnitude of
+// the Taylor sum), both bounded at f_low over the whole bank (k-derivatives are
+// f-derivatives times df^n).
 static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
     if (b->params.phase_mode == MF_PHASE_FP64) return 0;
     const double df = g->fs / (double)g->N;
@@ -319,9 +368,9 @@ static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
     while (lg < 8) {
         const double D2 = (double)(1 << (lg + 1));
         const double h = D2 / 2.0;
-        const double taylor = b->B4 * pow(df, 4) * h * h * h * h / 24.0;
+        const double taylor = b->B5 * pow(df, 5) * h * h * h * h * h / 120.0;
         const double mag = b->B1 * df * h;
-        if (taylor > 5e-7 || mag > 8.0) break;
+        if (taylor > 5e-7 || mag > 16.0) break;
         ++lg;
     }
     return lg;
@@ -350,6 +399,7 @@ static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch,
     MF_CUDA(cudaMalloc(&w.units, sizeof(UnitInfo) * b->n));
     MF_CUDA(cudaMalloc(&w.exch, sizeof(float2) * nN * nb));
     MF_CUDA(cudaMalloc(&w.anchors, sizeof(float4) * na * nb));
+    MF_CUDA(cudaMalloc(&w.anchors4, sizeof(float) * na * nb));
     MF_CUDA(cudaMalloc(&w.partials, sizeof(float4) * nbl * b->n));
     MF_CUDA(cudaMalloc(&w.staged, sizeof(mf_trigger) * ncap));
     MF_CUDA(cudaMalloc(&w.keys, sizeof(uint64_t) * ncap));
@@ -359,8 +409,68 @@ static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch,
     MF_CUDA(cudaMalloc(&w.counter, sizeof(unsigned long long)));
     MF_CUDA(cudaMalloc(&w.status, sizeof(int)));
     MF_CUDA(cudaMemset(w.status, 0, sizeof(int)));
+    MF_CUDA(cudaMalloc(&w.ctl, sizeof(unsigned) * (2 + 3 * b->n)));
     w.N = nN; w.n_t = b->n; w.cap = ncap; w.batch = nb; w.max_anc = na; w.nblk = nbl;
     return MF_OK;
+}
+
+// Persistent scheduler geometry: anchors LA rounds ahead of their pass 1, pass
+// 2 of a unit D2 rounds after its pass 1, exchange ring S > D2 slots, anchor
+// ring SA > LA slots (every wait then points to an earlier queue item).
+constexpr int kLA = 2, kD2 = 3, kS = kD2 + 3, kSA = kLA + 3;
+
+static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
+    if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32) return false;
+    const char *e = getenv("MFGB_SCHED");
+    return !(e && strcmp(e, "batch") == 0);
+}
+
+// Work queue in rounds r: A(r + LA) chunks, P1(r) tiles, P2(r - D2) tiles.
+static void build_queue(int64_t U, int nA, int n1, int n2, std::vector<int2> &q) {
+    q.clear();
+    q.reserve((size_t)(U * (nA + n1 + n2)));
+    auto push = [&](int64_t u, int phase, int tile) { q.push_back(make_int2((int)u, (phase << 16) | tile)); };
+    for (int64_t u = 0; u < std::min<int64_t>(kLA, U); ++u)
+        for (int c = 0; c < nA; ++c) push(u, 0, c);
+    for (int64_t r = 0; r < U + kD2; ++r) {
+        if (r + kLA < U)
+            for (int c = 0; c < nA; ++c) push(r + kLA, 0, c);
+        if (r < U)
+            for (int i = 0; i < n1; ++i) push(r, 1, i);
+        if (r >= kD2 && r - kD2 < U)
+            for (int i = 0; i < n2; ++i) push(r - kD2, 2, i);
+    }
+}
+
+static int ensure_queue(mf_bank_s *b, int64_t U, int nA, int n1, int n2, cudaStream_t st) {
+    Workspace &w = b->ws;
+    if (w.items && w.items_key[0] == U && w.items_key[1] == nA && w.items_key[2] == n1 && w.items_key[3] == n2)
+        return MF_OK;
+    std::vector<int2> q;
+    build_queue(U, nA, n1, n2, q);
+    if ((int64_t)q.size() > w.items_cap) {
+        MF_CUDA(cudaStreamSynchronize(st));
+        cudaFree(w.items);
+        w.items = nullptr;
+        MF_CUDA(cudaMalloc(&w.items, sizeof(int2) * q.size()));
+        w.items_cap = (int64_t)q.size();
+    }
+    MF_CUDA(cudaMemcpyAsync(w.items, q.data(), sizeof(int2) * q.size(), cudaMemcpyHostToDevice, st));
+    MF_CUDA(cudaStreamSynchronize(st));   // q is a host temporary
+    w.items_n = (int64_t)q.size();
+    w.items_key[0] = U; w.items_key[1] = nA; w.items_key[2] = n1; w.items_key[3] = n2;
+    return MF_OK;
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
 }
 
 extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, float threshold, mf_peak *peaks,
@@ -396,7 +506,9 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     if (key_bits > 64) return set_err(MF_EINVAL, "trigger key needs %d bits", key_bits);
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int64_t batch = choose_batch(maxN, b->n);
+    int64_t batch = choose_batch(maxN, b->n);
+    for (int s = 0; s < n_seg; ++s)
+        if (use_persistent(b, segs[s])) batch = std::max<int64_t>(batch, std::max(kS, kSA));
     int64_t max_anc = 0, nblk = 0;
     for (int s = 0; s < n_seg; ++s) {
         const int lgD = choose_log2D(b, segs[s]);
@@ -414,20 +526,135 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const int lgD = choose_log2D(b, segs[s]);
         const int man = (int)(((segs[s]->N / 2) >> lgD) + 2);
         const int nbk = pass2_blocks(sd.log2N);
+        const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
+        // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
+        std::vector<double> band_bytes, anc_bytes;
+        if (b->prof_on) {
+            band_bytes.resize((size_t)n_t);
+            anc_bytes.resize((size_t)n_t);
+            for (int t = 0; t < n_t; ++t) {
+                const double fc = std::min(b->fisco[(size_t)t], 0.5 * sd.fs);
+                int64_t lo = std::max((int64_t)1, (int64_t)ceil(b->params.f_low * (double)sd.N / sd.fs));
+                int64_t hi = std::min((int64_t)floor(fc * (double)sd.N / sd.fs) + 1, sd.N / 2);
+                if (hi < lo) hi = lo;
+                band_bytes[(size_t)t] = 8.0 * (double)(hi - lo);
+                anc_bytes[(size_t)t] = anchors ? 16.0 * (double)(((hi - 1) >> lgD) - (lo >> lgD) + 1) : 0.0;
+            }
+        }
+        int pi = prof_begin(b, MF_STAGE_SETUP, 48.0 * n_t, st);
         MF_CUDA(launch_units(sd, b->d_tmpl, n_t, b->params.f_low, threshold, lgD, w.units, st));
+        prof_end(b, pi, st);
+        count_launches(1);
+        if (use_persistent(b, segs[s])) {
+            int n1 = 0, n2 = 0;
+            persist_tiles(sd.log2N, &n1, &n2);
+            const int nA = (man + 1023) / 1024;
+            int rq = ensure_queue(b, n_t, nA, n1, n2, st);
+            if (rq) return rq;
+            MF_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(unsigned) * (2 + 3 * (size_t)n_t), st));
+            PersistParams P;
+            P.seg = sd;
+            P.tmpl = b->d_tmpl;
+            P.units = w.units;
+            P.items = w.items;
+            P.n_items = (int)w.items_n;
+            P.log2D = lgD;
+            P.max_anc = man;
+            P.nA = nA;
+            P.S = kS;
+            P.SA = kSA;
+            P.anchors = w.anchors;
+            P.anchors4 = w.anchors4;
+            P.exch = w.exch;
+            P.ctl = w.ctl;
+            P.doneA = w.ctl + 2;
+            P.done1 = w.ctl + 2 + n_t;
+            P.done2 = w.ctl + 2 + 2 * (size_t)n_t;
+            P.status = w.status;
+            P.partials = w.partials;
+            P.staged = w.staged;
+            P.keys = w.keys;
+            P.counter = w.counter;
+            P.cap = std::max<int64_t>(trig_cap, 0);
+            P.seg_idx = s;
+            P.n_seg = n_seg;
+            P.kl = kl;
+            P.peaks = peaks;
+            P.spin_limit = b->spin_limit;
+            P.stall_unit = (int)b->stall_unit;
+            double by = 16.0 * (double)sd.N * n_t;
+            if (b->prof_on)
+                for (int t = 0; t < n_t; ++t) by += band_bytes[(size_t)t] + anc_bytes[(size_t)t];
+            const int grid = std::max(1, persist_blocks_per_sm(sd.log2N)) * sm_count();
+            pi = prof_begin(b, MF_STAGE_FUSED, by, st);
+            MF_CUDA(launch_persistent(P, std::min<int64_t>(grid, w.items_n), st));
+            prof_end(b, pi, st);
+            count_launches(1);
+            continue;
+        }
         for (int u0 = 0; u0 < n_t; u0 += (int)batch) {
             const int nb = (int)std::min<int64_t>(batch, n_t - u0);
-            if (b->params.phase_mode != MF_PHASE_FP32)
-                MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, u0, nb, lgD, man, w.anchors, st));
-            MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors, w.exch, b->params.phase_mode,
-                                 b->d_tmpl, st));
+            double by_band = 0.0, by_anc = 0.0;
+            if (b->prof_on)
+                for (int t = u0; t < u0 + nb; ++t) { by_band += band_bytes[(size_t)t]; by_anc += anc_bytes[(size_t)t]; }
+            const double exch_bytes = 8.0 * (double)sd.N * nb;
+            if (anchors) {
+                pi = prof_begin(b, MF_STAGE_ANCHORS, by_anc, st);
+                MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, u0, nb, lgD, man, w.anchors, w.anchors4, st));
+                prof_end(b, pi, st);
+                count_launches(1);
+            }
+            pi = prof_begin(b, MF_STAGE_PASS1, by_band + by_anc + exch_bytes, st);
+            MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors, w.anchors4, w.exch,
+                                 b->params.phase_mode, b->d_tmpl, st));
+            prof_end(b, pi, st);
+            pi = prof_begin(b, MF_STAGE_PASS2, exch_bytes, st);
             MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                  std::max<int64_t>(trig_cap, 0), st));
+            prof_end(b, pi, st);
+            count_launches(2);
         }
+        pi = prof_begin(b, MF_STAGE_FINAL, 16.0 * nbk * n_t, st);
         MF_CUDA(launch_reduce_peaks(sd, w.units, n_t, w.partials, nbk, s, n_seg, peaks, st));
+        prof_end(b, pi, st);
+        count_launches(1);
     }
+    int pf = prof_begin(b, MF_STAGE_FINAL, 0.0, st);
     MF_CUDA(launch_sort_triggers(w.counter, trig_cap, key_bits, w.staged, w.keys, w.keys_tmp, w.idx_a, w.idx_b,
                                  trig, n_trig, w.status, st));
+    prof_end(b, pf, st);
+    count_launches(1);
+    return MF_OK;
+}
+
+extern "C" int mf_bank_debug_stall(mf_bank b, int64_t unit, int64_t spin_limit) {
+    if (!b) return set_err(MF_EINVAL, "NULL bank");
+    if (unit >= b->n) return set_err(MF_EINVAL, "unit out of range");
+    b->stall_unit = unit < 0 ? -1 : unit;
+    b->spin_limit = spin_limit > 0 ? spin_limit : 4000000;
+    return MF_OK;
+}
+
+extern "C" int mf_bank_profile(mf_bank b, int on) {
+    if (!b) return set_err(MF_EINVAL, "NULL bank");
+    b->prof_on = on != 0;
+    return MF_OK;
+}
+
+extern "C" int mf_bank_profile_read(mf_bank b, double *ms, double *bytes, int64_t *launches) {
+    if (!b || !ms || !bytes || !launches) return set_err(MF_EINVAL, "NULL argument");
+    for (int i = 0; i < MF_N_STAGES; ++i) { ms[i] = 0.0; bytes[i] = 0.0; launches[i] = 0; }
+    for (auto &r : b->prof) {
+        MF_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        MF_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.stage] += t;
+        bytes[r.stage] += r.bytes;
+        launches[r.stage] += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    b->prof.clear();
     return MF_OK;
 }
 
@@ -497,6 +724,7 @@ extern "C" int mf_synth_segment(const double *g, int64_t N, double fs, double f_
     if (e == cudaSuccess)
         e = launch_synth_spectrum(g, N, fs, f_low, psd_dev, psd_f0, psd_S0, inj_dev, n_inj, P, noise_scale, Y, st);
     if (e == cudaSuccess) e = launch_inverse_real_fft(Y, N, 2.0 * fs / (double)N, exch, s_out, st);
+    if (e == cudaSuccess) count_launches(7);   // weights, 3 scan kernels, spectrum, 2 FFT passes
     if (inj_dev) cudaFreeAsync(inj_dev, st);
     if (q) cudaFreeAsync(q, st);
     if (P) cudaFreeAsync(P, st);
@@ -530,6 +758,7 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
     double *partial = nullptr;
     cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * 8 * bpr * n, st);
     if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, st);
+    if (e == cudaSuccess) count_launches(2);
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers: %s",

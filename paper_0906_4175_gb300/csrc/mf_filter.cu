@@ -3,9 +3,9 @@
 //   k_units    band [k_lo, k_hi) (Sec. 1.1 band rule), sigma from the FP64
 //              prefix table, rho and z scale factors, anchor range;
 //   k_anchors  the 2PN phase Psi/(2 pi) in FP64 at anchor bins, reduced mod 1,
-//              plus its first three k-derivatives (FP32 Taylor coefficients);
+//              plus its first four k-derivatives (FP32 Taylor coefficients);
 //   pass 1     template generation h~_k = e^{-i Psi_k} in registers (FP32
-//              cubic Taylor from the nearest anchor, __sincosf of the reduced
+//              quartic Taylor from the nearest anchor, __sincosf of the reduced
 //              phase), weighting by W_k = f^(-7/6) conj(s~_k)/S_k, column IFFTs,
 //              four-step twiddle, one complex64 exchange write;
 //   pass 2     row IFFTs and the rho epilogue: |z|^2 threshold test, argmax with
@@ -13,7 +13,7 @@
 //   k_reduce_peaks / k_sort_triggers   deterministic peaks and (tmpl, seg, j)
 //              ordered triggers.
 // Neither h~(f) nor z(t) is written to memory.
-#include "mf_passes.cuh"
+#include "mf_filter.cuh"
 
 namespace mf {
 
@@ -48,211 +48,23 @@ __global__ void k_units(SegDev seg, const double *__restrict__ tmpl, int n_t, do
     units[t] = u;
 }
 
-// ---------------------------------------------------------------------------
-// FP64 anchors.  psi(k) = C0 + sum_p c_p u^p, u = (k df)^(-1/3); with
-// w_p = c_p u^p:  dpsi/dk = -sum p w_p / (3k),
-// d2psi/dk2 = sum p(p+3) w_p / (9 k^2),  d3psi/dk3 = -sum p(p+3)(p+6) w_p / (27 k^3).
-// Record: (psi mod 1, psi', psi''/2, psi'''/6) at the anchor centre
-// k_a = g D + D/2, in turns and bins.
-// ---------------------------------------------------------------------------
 __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const UnitInfo *__restrict__ units,
-                          int unit0, int log2D, int max_anc, float4 *__restrict__ anchors) {
+                          int unit0, int log2D, int max_anc, float4 *__restrict__ anchors,
+                          float *__restrict__ anchors4) {
     const int b = blockIdx.y;
     const UnitInfo u = units[unit0 + b];
     const double *T = tmpl + (int64_t)u.tmpl * kTmplStride;
     const double c1 = T[TF_C1], c2 = T[TF_C2], c3 = T[TF_C3], c5 = T[TF_C5];
     float4 *out = anchors + (int64_t)b * max_anc;
+    float *out4 = anchors4 + (int64_t)b * max_anc;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < u.n_anc; i += gridDim.x * blockDim.x) {
-        const int64_t g = (int64_t)u.g_lo + i;
-        const int64_t ka = (g << log2D) + ((1 << log2D) >> 1);
-        const double f = (double)ka * seg.df;
-        const double uu = rcbrt(f);
-        const double u2 = uu * uu, u3 = u2 * uu, u5 = u3 * u2;
-        const double w1 = c1 * uu, w2 = c2 * u2, w3 = c3 * u3, w5 = c5 * u5;
-        const double psi = -0.125 + w1 + w2 + w3 + w5;
-        const double r0 = psi - rint(psi);
-        const double S1 = w1 + 2.0 * w2 + 3.0 * w3 + 5.0 * w5;
-        const double S2 = 4.0 * w1 + 10.0 * w2 + 18.0 * w3 + 40.0 * w5;
-        const double S3 = 28.0 * w1 + 80.0 * w2 + 162.0 * w3 + 440.0 * w5;
-        const double ik = seg.df * u3;   // 1 / k_a
-        out[i] = make_float4((float)r0, (float)(-S1 * ik / 3.0), (float)(S2 * ik * ik / 18.0),
-                             (float)(-S3 * ik * ik * ik / 162.0));
+        float4 r;
+        float r4;
+        anchor_record(c1, c2, c3, c5, (int64_t)u.g_lo + i, log2D, seg.df, r, r4);
+        out[i] = r;
+        out4[i] = r4;
     }
 }
-
-// ---------------------------------------------------------------------------
-// pass-1 source: X_k = W_k e^{-i Psi_k} on the band, 0 elsewhere; k >= N/2 is
-// always outside (one-sided spectrum), so the upper half of every column is 0.
-// ---------------------------------------------------------------------------
-template <int L, int C>
-struct TemplateSrc {
-    static constexpr bool kHalfZero = true;
-    struct Params {
-        const float2 *W;
-        const UnitInfo *units;
-        const float4 *anchors;
-        int unit0, anc_stride, log2N1, log2D;
-    };
-    const Params &p;
-    __device__ TemplateSrc(const Params &pp) : p(pp) {}
-    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
-        constexpr int T = L / 32;
-        const int b = blockIdx.y;
-        const UnitInfo u = p.units[p.unit0 + b];
-        const float4 *anc = p.anchors + (int64_t)b * p.anc_stride - u.g_lo;
-        const int k1 = blockIdx.x * C + seq;
-        const int half = (1 << p.log2D) >> 1;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int k = k1 + ((t + r * T) << p.log2N1);
-            const bool in = (k >= u.k_lo) && (k < u.k_hi);
-            const int kk = in ? k : u.k_lo;
-            const float2 w = __ldg(&p.W[kk]);
-            const int g = kk >> p.log2D;
-            const float4 a = __ldg(&anc[g]);
-            const float d = (float)(kk - ((g << p.log2D) + half));
-            float ph = fmaf(fmaf(fmaf(a.w, d, a.z), d, a.y), d, a.x);
-            ph -= rintf(ph);
-            float s, c;
-            __sincosf(6.283185307179586f * ph, &s, &c);
-            // W * e^{-i 2 pi ph}
-            const float2 x = make_float2(fmaf(w.x, c, w.y * s), fmaf(w.y, c, -w.x * s));
-            v[r] = in ? x : czero();
-        }
-    }
-};
-
-// FP32-only phase (precision-sweep reference): psi evaluated directly in FP32.
-template <int L, int C>
-struct TemplateSrcF32 {
-    static constexpr bool kHalfZero = true;
-    struct Params {
-        const float2 *W;
-        const UnitInfo *units;
-        const double *tmpl;
-        int unit0, log2N1;
-        float df;
-    };
-    const Params &p;
-    __device__ TemplateSrcF32(const Params &pp) : p(pp) {}
-    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
-        constexpr int T = L / 32;
-        const UnitInfo u = p.units[p.unit0 + blockIdx.y];
-        const double *Tm = p.tmpl + (int64_t)u.tmpl * kTmplStride;
-        const float c1 = (float)Tm[TF_C1], c2 = (float)Tm[TF_C2], c3 = (float)Tm[TF_C3], c5 = (float)Tm[TF_C5];
-        const int k1 = blockIdx.x * C + seq;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int k = k1 + ((t + r * T) << p.log2N1);
-            const bool in = (k >= u.k_lo) && (k < u.k_hi);
-            const int kk = in ? k : u.k_lo;
-            const float2 w = __ldg(&p.W[kk]);
-            const float uu = rcbrtf((float)kk * p.df);
-            const float u2 = uu * uu;
-            float ph = -0.125f + uu * (c1 + uu * (c2 + uu * (c3 + u2 * c5)));
-            ph -= rintf(ph);
-            float s, c;
-            __sincosf(6.283185307179586f * ph, &s, &c);
-            const float2 x = make_float2(fmaf(w.x, c, w.y * s), fmaf(w.y, c, -w.x * s));
-            v[r] = in ? x : czero();
-        }
-    }
-};
-
-// ---------------------------------------------------------------------------
-// pass-2 sink: rho epilogue.  raw_j = row FFT output at j = j2 + N2 j1;
-// rho_j = |raw_j| rho_scale.  Tracks the argmax (lowest j on ties) and
-// appends every j with |raw_j|^2 > thr2.
-// ---------------------------------------------------------------------------
-template <int L, int C>
-struct RhoSink {
-    struct Params {
-        const UnitInfo *units;
-        float4 *partials;
-        mf_trigger *staged;
-        uint64_t *keys;
-        unsigned long long *counter;
-        int64_t cap;
-        int unit0, log2N2, nblk, seg_idx;
-        KeyLayout kl;
-    };
-    const Params &p;
-    UnitInfo u;
-    float bp;
-    int bj;
-    float2 bz;
-    __device__ RhoSink(const Params &pp) : p(pp), bp(-1.f), bj(0x7fffffff), bz(make_float2(0.f, 0.f)) {
-        u = p.units[p.unit0 + blockIdx.y];
-    }
-    template <int R>
-    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) {
-        const int j2 = blockIdx.x * C + seq;
-        bool any = false;
-        float pw[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
-            const int j = j2 + ((b + r * stride) << p.log2N2);
-            if (pw[r] > bp || (pw[r] == bp && j < bj)) { bp = pw[r]; bj = j; bz = v[r]; }
-            any |= pw[r] > u.thr2;
-        }
-        if (__any_sync(0xffffffffu, any)) {
-            const int lane = threadIdx.x & 31;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const bool pred = pw[r] > u.thr2;
-                const unsigned m = __ballot_sync(0xffffffffu, pred);
-                if (m == 0u) continue;   // warp-uniform
-                const int leader = __ffs(m) - 1;
-                unsigned long long base = 0ull;
-                if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (pred) {
-                    const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-                    if (slot < (unsigned long long)p.cap) {
-                        const int j = j2 + ((b + r * stride) << p.log2N2);
-                        mf_trigger tr;
-                        tr.tmpl = u.tmpl;
-                        tr.seg = p.seg_idx;
-                        tr.j = j;
-                        tr.rho = sqrtf(pw[r]) * u.rho_scale;
-                        tr.z_re = v[r].x * u.z_scale;
-                        tr.z_im = v[r].y * u.z_scale;
-                        p.staged[slot] = tr;
-                        p.keys[slot] = ((uint64_t)u.tmpl << (p.kl.seg_bits + p.kl.j_bits)) |
-                                       ((uint64_t)p.seg_idx << p.kl.j_bits) | (uint64_t)j;
-                    }
-                }
-            }
-        }
-    }
-    // CTA argmax -> partials[(unit0 + blockIdx.y) * nblk + blockIdx.x]
-    __device__ __forceinline__ void finish(float2 *smem) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float op = __shfl_xor_sync(0xffffffffu, bp, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            const float ox = __shfl_xor_sync(0xffffffffu, bz.x, o);
-            const float oy = __shfl_xor_sync(0xffffffffu, bz.y, o);
-            if (op > bp || (op == bp && oj < bj)) { bp = op; bj = oj; bz = make_float2(ox, oy); }
-        }
-        __syncthreads();   // the last FFT stage may still be reading shared memory
-        float4 *red = reinterpret_cast<float4 *>(smem);
-        if (lane == 0) red[warp] = make_float4(bp, __int_as_float(bj), bz.x, bz.y);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int nw = blockDim.x >> 5;
-            float4 best = red[0];
-            for (int w = 1; w < nw; ++w) {
-                const float4 c = red[w];
-                const int cj = __float_as_int(c.y), bjj = __float_as_int(best.y);
-                if (c.x > best.x || (c.x == best.x && cj < bjj)) best = c;
-            }
-            p.partials[(int64_t)(p.unit0 + blockIdx.y) * p.nblk + blockIdx.x] = best;
-        }
-    }
-};
 
 // ---------------------------------------------------------------------------
 // launches
@@ -264,11 +76,11 @@ cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double 
 }
 
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0, int n_units,
-                           int log2D, int max_anc, float4 *anchors, cudaStream_t st) {
+                           int log2D, int max_anc, float4 *anchors, float *anchors4, cudaStream_t st) {
     const int per = 256;
     int gx = (max_anc + per - 1) / per;
     if (gx > 64) gx = 64;
-    k_anchors<<<dim3(gx, n_units), per, 0, st>>>(seg, tmpl, units, unit0, log2D, max_anc, anchors);
+    k_anchors<<<dim3(gx, n_units), per, 0, st>>>(seg, tmpl, units, unit0, log2D, max_anc, anchors, anchors4);
     return cudaGetLastError();
 }
 
@@ -278,6 +90,7 @@ struct Pass1Op {
     const UnitInfo *units;
     int unit0, n_units, log2D, max_anc, phase_mode;
     const float4 *anchors;
+    const float *anchors4;
     float2 *exch;
     const double *tmpl;
     cudaStream_t st;
@@ -287,11 +100,11 @@ struct Pass1Op {
         typename ExchSink<N2, C, +1>::Params kp{exch, seg.log2N1, seg.log2N};
         const dim3 grid(N1 / C, n_units);
         if (phase_mode == MF_PHASE_FP32) {
-            typename TemplateSrcF32<N2, C>::Params sp{seg.W, units, tmpl, unit0, seg.log2N1, (float)seg.df};
-            return run_pass<N2, C, true, +1, TemplateSrcF32<N2, C>, ExchSink<N2, C, +1>>(grid, sp, kp, st);
+            typename TemplateSrcF32<N2, C>::Params sp{seg.W, units, tmpl, seg.log2N1, (float)seg.df};
+            return run_pass<N2, C, true, +1, TemplateSrcF32<N2, C>, ExchSink<N2, C, +1>>(grid, sp, kp, st, unit0);
         }
-        typename TemplateSrc<N2, C>::Params sp{seg.W, units, anchors, unit0, max_anc, seg.log2N1, log2D};
-        return run_pass<N2, C, true, +1, TemplateSrc<N2, C>, ExchSink<N2, C, +1>>(grid, sp, kp, st);
+        typename TemplateSrc<N2, C>::Params sp{seg.W, units, anchors, anchors4, max_anc, seg.log2N1, log2D};
+        return run_pass<N2, C, true, +1, TemplateSrc<N2, C>, ExchSink<N2, C, +1>>(grid, sp, kp, st, unit0);
     }
 };
 
@@ -314,8 +127,8 @@ struct Pass2Op {
         const int nblk = N2 / C;
         typename RowSrc<N1, C>::Params sp{exch, seg.log2N1, seg.log2N};
         typename RhoSink<N1, C>::Params kp{units, partials, staged, keys, counter, cap,
-                                           unit0, seg.log2N2, nblk, seg_idx, kl};
-        return run_pass<N1, C, false, +1, RowSrc<N1, C>, RhoSink<N1, C>>(dim3(nblk, n_units), sp, kp, st);
+                                           seg.log2N2, nblk, seg_idx, kl};
+        return run_pass<N1, C, false, +1, RowSrc<N1, C>, RhoSink<N1, C>>(dim3(nblk, n_units), sp, kp, st, unit0);
     }
 };
 
@@ -342,9 +155,9 @@ struct AttrOp {
 }  // namespace
 
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D, int max_anc,
-                         const float4 *anchors, float2 *exch, int phase_mode, const double *tmpl,
-                         cudaStream_t st) {
-    Pass1Op op{seg, units, unit0, n_units, log2D, max_anc, phase_mode, anchors, exch, tmpl, st};
+                         const float4 *anchors, const float *anchors4, float2 *exch, int phase_mode,
+                         const double *tmpl, cudaStream_t st) {
+    Pass1Op op{seg, units, unit0, n_units, log2D, max_anc, phase_mode, anchors, anchors4, exch, tmpl, st};
     return dispatch_split(seg.log2N, op);
 }
 

@@ -1,0 +1,223 @@
+// mf_filter.cuh -- the fused sources and sinks of the bank filter, shared by
+// the per-batch kernels (mf_filter.cu) and the persistent scheduler
+// (mf_persist.cu).
+#pragma once
+#include "mf_passes.cuh"
+
+namespace mf {
+
+// ---------------------------------------------------------------------------
+// FP64 anchors.  psi(k) = C0 + sum_p c_p u^p, u = (k df)^(-1/3), in turns.  With
+// w_p = c_p u^p the k-derivatives are
+//   d^n psi/dk^n = (-1)^n sum_p [p (p+3) ... (p+3(n-1)) / 3^n] w_p / k^n,
+// so the Taylor coefficients at the anchor centre k_a = g D + D/2 are
+//   q1 = -sum p w_p / (3k),  q2 = sum p(p+3) w_p / (18 k^2),
+//   q3 = -sum p(p+3)(p+6) w_p / (162 k^3),  q4 = sum p(p+3)(p+6)(p+9) w_p / (1944 k^4).
+// psi mod 1 and q1 (which multiplies offsets up to D/2) are formed in FP64 --
+// u from an FP32 seed and one FP64 Newton step u <- u (4 - f u^3) / 3 -- and
+// q2..q4 in FP32.  Record: float4 (psi mod 1, q1, q2, q3) and float q4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void anchor_record(double c1, double c2, double c3, double c5, int64_t g, int log2D,
+                                              double df, float4 &rec, float &rec4) {
+    const int64_t ka = (g << log2D) + ((1 << log2D) >> 1);
+    const double f = (double)ka * df;
+    double uu = (double)rcbrtf((float)f);
+    uu = uu * (4.0 - f * uu * uu * uu) * (1.0 / 3.0);
+    const double u2 = uu * uu;
+    const double psi = -0.125 + uu * (c1 + uu * (c2 + uu * (c3 + u2 * c5)));
+    const double S1 = uu * (c1 + uu * (2.0 * c2 + uu * (3.0 * c3 + u2 * (5.0 * c5))));
+    const double ik = df * u2 * uu;   // 1 / k_a
+    const double r0 = psi - rint(psi);
+    const float uf = (float)uu, ikf = (float)ik;
+    const float w1 = (float)c1 * uf, w2 = (float)c2 * uf * uf, w3 = (float)c3 * uf * uf * uf;
+    const float w5 = (float)c5 * (uf * uf) * (uf * uf * uf);
+    const float S2 = 4.f * w1 + 10.f * w2 + 18.f * w3 + 40.f * w5;
+    const float S3 = 28.f * w1 + 80.f * w2 + 162.f * w3 + 440.f * w5;
+    const float S4 = 280.f * w1 + 880.f * w2 + 1944.f * w3 + 6160.f * w5;
+    const float ik2 = ikf * ikf;
+    rec = make_float4((float)r0, (float)(-S1 * ik * (1.0 / 3.0)), S2 * ik2 * (1.f / 18.f),
+                      -S3 * ik2 * ikf * (1.f / 162.f));
+    rec4 = S4 * ik2 * ik2 * (1.f / 1944.f);
+}
+
+// ---------------------------------------------------------------------------
+// pass-1 source: X_k = W_k e^{-i Psi_k} on the band, 0 elsewhere; k >= N/2 is
+// always outside (one-sided spectrum), so the upper half of every column is 0.
+// ---------------------------------------------------------------------------
+template <int L, int C>
+struct TemplateSrc {
+    static constexpr bool kHalfZero = true;
+    struct Params {
+        const float2 *W;
+        const UnitInfo *units;
+        const float4 *anchors;
+        const float *anchors4;
+        int anc_stride, log2N1, log2D;
+    };
+    const Params &p;
+    const int tile, unit, slot;
+    __device__ TemplateSrc(const Params &pp, int tl, int un, int sl) : p(pp), tile(tl), unit(un), slot(sl) {}
+    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
+        constexpr int T = L / 32;
+        const UnitInfo u = p.units[unit];
+        const float4 *anc = p.anchors + (int64_t)slot * p.anc_stride - u.g_lo;
+        const float *anc4 = p.anchors4 + (int64_t)slot * p.anc_stride - u.g_lo;
+        const int k1 = tile * C + seq;
+        const int half = (1 << p.log2D) >> 1;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int k = k1 + ((t + r * T) << p.log2N1);
+            const bool in = (k >= u.k_lo) && (k < u.k_hi);
+            const int kk = in ? k : u.k_lo;
+            const float2 w = __ldg(&p.W[kk]);
+            const int g = kk >> p.log2D;
+            const float4 a = __ldcg(&anc[g]);   // anchors may be rewritten in the same launch (ring)
+            const float a4 = __ldcg(&anc4[g]);
+            const float d = (float)(kk - ((g << p.log2D) + half));
+            float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
+            ph -= rintf(ph);
+            float s, c;
+            __sincosf(6.283185307179586f * ph, &s, &c);
+            // W * e^{-i 2 pi ph}
+            const float2 x = make_float2(fmaf(w.x, c, w.y * s), fmaf(w.y, c, -w.x * s));
+            v[r] = in ? x : czero();
+        }
+    }
+};
+
+// FP32-only phase (precision-sweep reference): psi evaluated directly in FP32.
+template <int L, int C>
+struct TemplateSrcF32 {
+    static constexpr bool kHalfZero = true;
+    struct Params {
+        const float2 *W;
+        const UnitInfo *units;
+        const double *tmpl;
+        int log2N1;
+        float df;
+    };
+    const Params &p;
+    const int tile, unit;
+    __device__ TemplateSrcF32(const Params &pp, int tl, int un, int) : p(pp), tile(tl), unit(un) {}
+    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
+        constexpr int T = L / 32;
+        const UnitInfo u = p.units[unit];
+        const double *Tm = p.tmpl + (int64_t)u.tmpl * kTmplStride;
+        const float c1 = (float)Tm[TF_C1], c2 = (float)Tm[TF_C2], c3 = (float)Tm[TF_C3], c5 = (float)Tm[TF_C5];
+        const int k1 = tile * C + seq;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int k = k1 + ((t + r * T) << p.log2N1);
+            const bool in = (k >= u.k_lo) && (k < u.k_hi);
+            const int kk = in ? k : u.k_lo;
+            const float2 w = __ldg(&p.W[kk]);
+            const float uu = rcbrtf((float)kk * p.df);
+            const float u2 = uu * uu;
+            float ph = -0.125f + uu * (c1 + uu * (c2 + uu * (c3 + u2 * c5)));
+            ph -= rintf(ph);
+            float s, c;
+            __sincosf(6.283185307179586f * ph, &s, &c);
+            const float2 x = make_float2(fmaf(w.x, c, w.y * s), fmaf(w.y, c, -w.x * s));
+            v[r] = in ? x : czero();
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// pass-2 sink: rho epilogue.  raw_j = row FFT output at j = j2 + N2 j1;
+// rho_j = |raw_j| rho_scale.  Tracks the argmax (lowest j on ties) and
+// appends every j with |raw_j|^2 > thr2.
+// ---------------------------------------------------------------------------
+template <int L, int C>
+struct RhoSink {
+    struct Params {
+        const UnitInfo *units;
+        float4 *partials;
+        mf_trigger *staged;
+        uint64_t *keys;
+        unsigned long long *counter;
+        int64_t cap;
+        int log2N2, nblk, seg_idx;
+        KeyLayout kl;
+    };
+    const Params &p;
+    const int tile, unit;
+    UnitInfo u;
+    float bp;
+    int bj;
+    float2 bz;
+    __device__ RhoSink(const Params &pp, int tl, int un, int)
+        : p(pp), tile(tl), unit(un), bp(-1.f), bj(0x7fffffff), bz(make_float2(0.f, 0.f)) {
+        u = p.units[un];
+    }
+    template <int R>
+    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) {
+        const int j2 = tile * C + seq;
+        bool any = false;
+        float pw[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+            const int j = j2 + ((b + r * stride) << p.log2N2);
+            if (pw[r] > bp || (pw[r] == bp && j < bj)) { bp = pw[r]; bj = j; bz = v[r]; }
+            any |= pw[r] > u.thr2;
+        }
+        if (__any_sync(0xffffffffu, any)) {
+            const int lane = threadIdx.x & 31;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bool pred = pw[r] > u.thr2;
+                const unsigned m = __ballot_sync(0xffffffffu, pred);
+                if (m == 0u) continue;   // warp-uniform
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0ull;
+                if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (pred) {
+                    const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+                    if (slot < (unsigned long long)p.cap) {
+                        const int j = j2 + ((b + r * stride) << p.log2N2);
+                        mf_trigger tr;
+                        tr.tmpl = u.tmpl;
+                        tr.seg = p.seg_idx;
+                        tr.j = j;
+                        tr.rho = sqrtf(pw[r]) * u.rho_scale;
+                        tr.z_re = v[r].x * u.z_scale;
+                        tr.z_im = v[r].y * u.z_scale;
+                        p.staged[slot] = tr;
+                        p.keys[slot] = ((uint64_t)u.tmpl << (p.kl.seg_bits + p.kl.j_bits)) |
+                                       ((uint64_t)p.seg_idx << p.kl.j_bits) | (uint64_t)j;
+                    }
+                }
+            }
+        }
+    }
+    // CTA argmax -> partials[unit * nblk + tile]
+    __device__ __forceinline__ void finish(float2 *smem) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float op = __shfl_xor_sync(0xffffffffu, bp, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            const float ox = __shfl_xor_sync(0xffffffffu, bz.x, o);
+            const float oy = __shfl_xor_sync(0xffffffffu, bz.y, o);
+            if (op > bp || (op == bp && oj < bj)) { bp = op; bj = oj; bz = make_float2(ox, oy); }
+        }
+        __syncthreads();   // the last FFT stage may still be reading shared memory
+        float4 *red = reinterpret_cast<float4 *>(smem);
+        if (lane == 0) red[warp] = make_float4(bp, __int_as_float(bj), bz.x, bz.y);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nw = blockDim.x >> 5;
+            float4 best = red[0];
+            for (int w = 1; w < nw; ++w) {
+                const float4 c = red[w];
+                const int cj = __float_as_int(c.y), bjj = __float_as_int(best.y);
+                if (c.x > best.x || (c.x == best.x && cj < bjj)) best = c;
+            }
+            p.partials[(int64_t)unit * p.nblk + tile] = best;
+        }
+    }
+};
+
+}  // namespace mf

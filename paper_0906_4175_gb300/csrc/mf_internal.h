@@ -48,6 +48,32 @@ struct KeyLayout {
     int j_bits, seg_bits, tmpl_bits;
 };
 
+// Everything the persistent bank scheduler (mf_persist.cu) needs for one segment.
+struct PersistParams {
+    SegDev seg;
+    const double *tmpl;
+    const UnitInfo *units;
+    const int2 *items;          // work queue: {unit, phase << 16 | tile}, phase 0 = A, 1 = P1, 2 = P2
+    int n_items;
+    int log2D, max_anc, nA, S, SA;
+    float4 *anchors;            // SA slots of max_anc records
+    float *anchors4;
+    float2 *exch;               // S slots of N complex64
+    unsigned *ctl;              // [0] queue head, [1] abort flag (zeroed before launch)
+    unsigned *doneA, *done1, *done2;   // per-unit completed item counts (zeroed before launch)
+    int *status;                // bit 1: a bounded wait expired
+    float4 *partials;           // [units][pass-2 tiles]
+    mf_trigger *staged;
+    uint64_t *keys;
+    unsigned long long *counter;
+    int64_t cap;
+    int seg_idx, n_seg;
+    KeyLayout kl;
+    mf_peak *peaks;
+    long long spin_limit;       // bounded-wait iterations (back-off <= ~1 us each)
+    int stall_unit;             // test hook: this unit's pass 2 waits for a count never reached (-1: off)
+};
+
 // ---- launch wrappers (defined in the .cu files; return cudaError_t) -----
 
 // segment preparation (mf_prep.cu)
@@ -71,10 +97,11 @@ cudaError_t launch_inverse_real_fft(const float2 *Y, int64_t N, double scale, fl
 cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double f_low, float thr,
                          int log2D, UnitInfo *units, cudaStream_t st);
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0,
-                           int n_units, int log2D, int max_anc, float4 *anchors, cudaStream_t st);
+                           int n_units, int log2D, int max_anc, float4 *anchors, float *anchors4,
+                           cudaStream_t st);
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
-                         int max_anc, const float4 *anchors, float2 *exch, int phase_mode,
-                         const double *tmpl, cudaStream_t st);
+                         int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
+                         int phase_mode, const double *tmpl, cudaStream_t st);
 cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units,
                          const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
                          mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
@@ -92,6 +119,9 @@ cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const
                           const int64_t *band, double *obj, double *grad, double *partial, cudaStream_t st);
 int refine_blocks_per_row();
 
-cudaError_t init_kernel_attributes();
+// persistent scheduler (mf_persist.cu): segments with N >= 2^13
+cudaError_t launch_persistent(const PersistParams &P, int grid, cudaStream_t st);
+int persist_blocks_per_sm(int log2N);
+void persist_tiles(int log2N, int *n1, int *n2);
 
 }  // namespace mf

@@ -20,13 +20,17 @@ __host__ __device__ constexpr size_t pass_smem_bytes() {
     return (size_t)C * FftShape<L>::STRIDE * sizeof(float2);
 }
 
-// Generic pass kernel: grid.x = N_other / C tiles, grid.y = batch.
+// Every source and sink is constructed with (params, tile, unit, slot): tile
+// = which group of C sequences, unit = (template, segment) unit index, slot =
+// which batch entry of the ring buffers it reads or writes.
+// Generic pass kernel: grid.x = N_other / C tiles, grid.y = batch
+// (unit = unit0 + blockIdx.y, slot = blockIdx.y).
 template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
 __global__ void __launch_bounds__(C *(L / 32), (C * (L / 32) >= 256) ? 2 : 1)
-    k_fft_pass(typename Src::Params sp, typename Snk::Params kp) {
+    k_fft_pass(typename Src::Params sp, typename Snk::Params kp, int unit0) {
     extern __shared__ float2 smem[];
-    Src src(sp);
-    Snk snk(kp);
+    Src src(sp, blockIdx.x, unit0 + blockIdx.y, blockIdx.y);
+    Snk snk(kp, blockIdx.x, unit0 + blockIdx.y, blockIdx.y);
     cta_fft<L, C, SEQ_FAST, SIGN>(smem, src, snk);
     snk.finish(smem);
 }
@@ -40,9 +44,9 @@ cudaError_t set_pass_attrs() {
 
 template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
 cudaError_t run_pass(dim3 grid, const typename Src::Params &sp, const typename Snk::Params &kp,
-                     cudaStream_t st) {
+                     cudaStream_t st, int unit0 = 0) {
     k_fft_pass<L, C, SEQ_FAST, SIGN, Src, Snk>
-        <<<grid, C * (L / 32), pass_smem_bytes<L, C>(), st>>>(sp, kp);
+        <<<grid, C * (L / 32), pass_smem_bytes<L, C>(), st>>>(sp, kp, unit0);
     return cudaGetLastError();
 }
 
@@ -78,10 +82,11 @@ struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO
     static constexpr bool kHalfZero = HALF_ZERO;
     struct Params { const float2 *X; int log2N1; int64_t batch_stride; };
     const Params &p;
-    __device__ ColComplexSrc(const Params &pp) : p(pp) {}
+    const int tile, slot;
+    __device__ ColComplexSrc(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
-        const float2 *X = p.X + (int64_t)blockIdx.y * p.batch_stride;
-        const int k1 = blockIdx.x * C + seq;
+        const float2 *X = p.X + (int64_t)slot * p.batch_stride;
+        const int k1 = tile * C + seq;
         constexpr int T = L / 32;
         constexpr int NR = HALF_ZERO ? 16 : 32;
 #pragma unroll
@@ -94,9 +99,10 @@ struct ColRealSrc {         // real samples s[n] (imaginary part zero)
     static constexpr bool kHalfZero = false;
     struct Params { const float *s; int log2N1; };
     const Params &p;
-    __device__ ColRealSrc(const Params &pp) : p(pp) {}
+    const int tile;
+    __device__ ColRealSrc(const Params &pp, int tl, int, int) : p(pp), tile(tl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
-        const int k1 = blockIdx.x * C + seq;
+        const int k1 = tile * C + seq;
         constexpr int T = L / 32;
 #pragma unroll
         for (int r = 0; r < 32; ++r) v[r] = make_float2(p.s[k1 + ((t + r * T) << p.log2N1)], 0.f);
@@ -109,11 +115,12 @@ template <int L, int C, int SIGN>
 struct ExchSink {
     struct Params { float2 *E; int log2N1; int log2N; };
     const Params &p;
-    __device__ ExchSink(const Params &pp) : p(pp) {}
+    const int tile, slot;
+    __device__ ExchSink(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
     template <int R>
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
-        float2 *E = p.E + ((int64_t)blockIdx.y << p.log2N);
-        const int k1 = blockIdx.x * C + seq;
+        float2 *E = p.E + ((int64_t)slot << p.log2N);
+        const int k1 = tile * C + seq;
         float2 w = unit_root<SIGN>((uint32_t)(b * k1), p.log2N);
         const float2 step = unit_root<SIGN>((uint32_t)(stride * k1), p.log2N);
 #pragma unroll
@@ -135,10 +142,11 @@ struct RowSrc {
     static constexpr bool kHalfZero = false;
     struct Params { const float2 *E; int log2N1; int log2N; };
     const Params &p;
-    __device__ RowSrc(const Params &pp) : p(pp) {}
+    const int tile, slot;
+    __device__ RowSrc(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
-        const float2 *E = p.E + ((int64_t)blockIdx.y << p.log2N);
-        const int j2 = blockIdx.x * C + seq;
+        const float2 *E = p.E + ((int64_t)slot << p.log2N);
+        const int j2 = tile * C + seq;
         const float2 *row = E + ((int64_t)j2 << p.log2N1);
         constexpr int T = L / 32;
 #pragma unroll
@@ -151,10 +159,11 @@ template <int L, int C>
 struct RowComplexOut {
     struct Params { float2 *out; int log2N2; int64_t limit; };
     const Params &p;
-    __device__ RowComplexOut(const Params &pp) : p(pp) {}
+    const int tile;
+    __device__ RowComplexOut(const Params &pp, int tl, int, int) : p(pp), tile(tl) {}
     template <int R>
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
-        const int j2 = blockIdx.x * C + seq;
+        const int j2 = tile * C + seq;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int64_t j = j2 + ((int64_t)(b + r * stride) << p.log2N2);
@@ -169,10 +178,11 @@ template <int L, int C>
 struct RowRealOut {
     struct Params { float *s; int log2N2; float scale; };
     const Params &p;
-    __device__ RowRealOut(const Params &pp) : p(pp) {}
+    const int tile;
+    __device__ RowRealOut(const Params &pp, int tl, int, int) : p(pp), tile(tl) {}
     template <int R>
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
-        const int j2 = blockIdx.x * C + seq;
+        const int j2 = tile * C + seq;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int64_t j = j2 + ((int64_t)(b + r * stride) << p.log2N2);

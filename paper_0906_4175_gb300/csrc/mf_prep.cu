@@ -1,6 +1,7 @@
 // mf_prep.cu -- once-per-segment conditioning for Eq. (1) of arXiv:0906.4175:
 //   X_k = DFT(s)_k (own four-step FP32 FFT, forward sign), k = 0..N/2
-//   q_k = f_k^(-7/3) / S_k (FP64; S_k from Eq. (2) or a caller table)
+//   q_k = f_k^(-7/3) / S_k (FP32 powers of f and Eq. (2) bracket, FP64 result;
+//         S_k = S0 [(4.49 x)^-56 + 0.16 x^-4.52 + 0.52 + 0.32 x^2], x = f/f0, or a caller table)
 //   P_k = sum_{k' < k} q_k'  (FP64 exclusive prefix; sigma^2 of Eq. (4) for the
 //         band [k_lo, k_hi) is 4 df A^2 (P[k_hi] - P[k_lo]))
 //   W_k = alpha f_k^(-7/6) dt conj(X_k) / S_k, alpha = sqrt(4 df / P[N/2]),
@@ -9,12 +10,6 @@
 #include "mf_passes.cuh"
 
 namespace mf {
-
-// Eq. (2): S_n(f) = S0 [(4.49 x)^-56 + 0.16 x^-4.52 + 0.52 + 0.32 x^2], x = f/f0
-__device__ __forceinline__ double psd_eq2(double f, double f0, double S0) {
-    const double x = f / f0;
-    return S0 * (pow(4.49 * x, -56.0) + 0.16 * pow(x, -4.52) + 0.52 + 0.32 * x * x);
-}
 
 namespace {
 struct FwdOp {
@@ -70,16 +65,25 @@ cudaError_t prep_kernel_attributes() {
     return cudaSuccess;
 }
 
-// q_k = f^(-7/3)/S_k for 1 <= k < N/2, q_0 = 0
+// q_k = f^(-7/3)/S_k for 1 <= k < N/2, q_0 = 0.  Eq. (2) is evaluated as
+// S0 * B(f) with the bracket B and the powers of f in FP32 (powf), the
+// quotient scaled by 1/S0 in FP64; a caller table is used in FP64.
+__device__ __forceinline__ float psd_eq2_bracket(float f, float f0) {
+    const float x = f / f0;
+    return powf(4.49f * x, -56.0f) + 0.16f * powf(x, -4.52f) + 0.52f + 0.32f * x * x;
+}
+
 __global__ void k_psd_weights(const double *__restrict__ psd, double f0, double S0, int64_t N, double fs,
                               double *__restrict__ q) {
     const int64_t half = N / 2;
     const double df = fs / (double)N;
+    const double inv_S0 = 1.0 / S0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half; k += (int64_t)gridDim.x * blockDim.x) {
         if (k == 0) { q[0] = 0.0; continue; }
         const double f = (double)k * df;
-        const double S = psd ? psd[k] : psd_eq2(f, f0, S0);
-        q[k] = pow(f, -7.0 / 3.0) / S;
+        const float p73 = powf((float)f, -7.0f / 3.0f);
+        if (psd) q[k] = (double)p73 / psd[k];
+        else q[k] = (double)(p73 / psd_eq2_bracket((float)f, (float)f0)) * inv_S0;
     }
 }
 
@@ -178,13 +182,14 @@ __global__ void k_weight_data(const float2 *__restrict__ X, const double *__rest
         consts->P_tot = Ptot;
         consts->alpha = alpha;
     }
+    const float a_eq2 = (float)(alpha * dt / S0);
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half; k += (int64_t)gridDim.x * blockDim.x) {
         if (k == 0) { W[0] = make_float2(0.f, 0.f); continue; }
-        const double f = (double)k * df;
-        const double S = psd ? psd[k] : psd_eq2(f, f0, S0);
-        const double a = alpha * pow(f, -7.0 / 6.0) * dt / S;
+        const float f = (float)((double)k * df);
+        const float p76 = powf(f, -7.0f / 6.0f);
+        const float a = psd ? (float)(alpha * dt / psd[k]) * p76 : a_eq2 * (p76 / psd_eq2_bracket(f, (float)f0));
         const float2 x = X[k];
-        W[k] = make_float2((float)(a * (double)x.x), (float)(-a * (double)x.y));
+        W[k] = make_float2(a * x.x, -a * x.y);
     }
 }
 

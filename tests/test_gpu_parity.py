@@ -296,3 +296,42 @@ def test_refine_autograd_function(mf):
     (3.0 * J.sum()).backward()
     _, g = mf.refine(seg, theta.detach())
     assert torch.allclose(theta.grad, 3.0 * g)
+
+
+def test_persistent_and_batch_schedulers_agree(mf, monkeypatch):
+    """The persistent scheduler (one launch, ordered work queue) and the
+    per-batch launches give bit-identical peaks and triggers."""
+    import torch
+    wl = workloads.small(seed=12, N=1 << 16, fs=4096.0, n_templates=21, m_lo=1.1, m_hi=9.0)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 18)]
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 18)]
+    assert int(a[2][0]) == int(b[2][0]) > 0
+    n = int(a[2][0])
+    assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8))
+    assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
+
+
+def test_bounded_wait_timeout_reports_and_recovers(mf):
+    """A wait that can never be satisfied (test hook) runs out after its
+    iteration limit: the call reports MF_ETIMEOUT, nothing faults, and the next
+    call on the same bank is correct again."""
+    import torch
+    wl = workloads.small(seed=13, N=1 << 14, fs=4096.0, n_templates=6)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    ref = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)[0])
+    assert bank.check() == 0
+    bank.debug_stall(3, spin_limit=2000)
+    mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)
+    assert bank.check(allow_timeout=True) == mf._native.MF_ETIMEOUT
+    bank.debug_stall(-1)
+    got = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)[0])
+    assert bank.check() == 0
+    assert np.array_equal(ref.view(np.uint8), got.view(np.uint8))
