@@ -169,6 +169,24 @@ int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, const doubl
                        int64_t n, const int64_t *band, double *obj, double *grad,
                        void *cuda_stream);
 
+/* mf_refine_triggers_static -- the same computation as mf_refine_triggers
+ * (same arguments, same results) for callers that cannot allocate device
+ * memory while they refine: the call makes no cudaMalloc, cudaMallocAsync,
+ * cudaFree or other allocating call.  The paper has no counterpart; it exists
+ * for ascent loops that run while another component owns the device
+ * allocator.  Its per-block partial sums live in one fixed 4 MiB array in
+ * device global memory that every device which loads the library holds until
+ * the process exits; hence n <= 4096 rows per call (larger n returns
+ * MF_EINVAL with a message).  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture on that device.  All calls share the array: two calls whose
+ * work overlaps on the GPU (different streams, or different host threads
+ * without ordering) race and give wrong results; calls on one stream are
+ * ordered and safe.  Nothing in the array needs clearing between calls. */
+int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *params, const double *theta,
+                              int64_t n, const int64_t *band, double *obj, double *grad,
+                              void *cuda_stream);
+
 /* ---- measurement hooks (not part of the paper's method) ------------------ */
 
 /* Total number of kernels this library has launched in this process (host

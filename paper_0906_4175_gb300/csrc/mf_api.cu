@@ -765,3 +765,60 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
                        cudaGetErrorString(e));
     return MF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free refinement.  Some callers cannot allocate device memory at
+// the point where they refine triggers: an ascent loop that runs while another
+// component owns the device allocator, or code that must never trigger an
+// allocator call inside its hot loop.  This variant keeps the per-block
+// partial sums in a fixed array in device global memory instead of the stream
+// allocation that mf_refine_triggers makes.
+// ---------------------------------------------------------------------------
+static constexpr int64_t kRefineStaticRows = 4096;   // at most this many theta rows per call
+static constexpr int kRefineStaticBpr = 16;           // blocks per row (== refine_blocks_per_row())
+// 4096 rows x 16 blocks x 8 partial sums x 8 bytes = 4 MiB on every device that loads the library
+static __device__ __align__(256) double g_refine_scratch[kRefineStaticRows * kRefineStaticBpr * 8];
+
+// Device address of g_refine_scratch per device ordinal.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device, with that device current.
+static int refine_scratch_ptr(double **out) {
+    static std::mutex mu;
+    static std::vector<double *> ptrs;
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)ptrs.size() <= dev) ptrs.resize((size_t)dev + 1, nullptr);
+    if (!ptrs[(size_t)dev]) {
+        void *p = nullptr;
+        MF_CUDA(cudaGetSymbolAddress(&p, g_refine_scratch));
+        ptrs[(size_t)dev] = (double *)p;
+    }
+    *out = ptrs[(size_t)dev];
+    return MF_OK;
+}
+
+extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *params, const double *theta, int64_t n,
+                                         const int64_t *band, double *obj, double *grad, void *cuda_stream) {
+    if (!seg || !theta || !obj || !grad) return set_err(MF_EINVAL, "NULL argument");
+    if (n < 0) return set_err(MF_EINVAL, "n < 0");
+    if (n > kRefineStaticRows)
+        return set_err(MF_EINVAL, "n = %lld exceeds the fixed scratch of %lld rows of mf_refine_triggers_static",
+                       (long long)n, (long long)kRefineStaticRows);
+    if (refine_blocks_per_row() != kRefineStaticBpr) return set_err(MF_ENOTSUP, "scratch layout mismatch");
+    if (n == 0) return MF_OK;
+    mf_bank_params p = params ? *params : default_params();
+    int rc = check_params(p);
+    if (rc) return rc;
+    rc = ensure_device_init();
+    if (rc) return rc;
+    double *scratch = nullptr;
+    rc = refine_scratch_ptr(&scratch);
+    if (rc) return rc;
+    // every partial sum the final kernel reads is written by the first kernel of
+    // the same call, so nothing in the scratch needs clearing
+    const SegDev sd = seg_dev(seg);
+    MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, (cudaStream_t)cuda_stream));
+    count_launches(2);
+    return MF_OK;
+}
