@@ -36,7 +36,7 @@ UNIT = "templates/s"
 WORKLOAD = "1024 templates (32x32 lattice, m1,m2 in [1,3] Msun), 1 segment N=2^20 at 4096 Hz, 8 injections, thr 6"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cu", "mf_internal.h"]
+KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu", "mf_internal.h"]
 
 
 def _args():
@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--templates", type=int, default=0,
+                    help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     return ap.parse_args()
 
 
@@ -236,6 +238,8 @@ def main():
     import workloads
 
     wl = workloads.scale(seed=rank)
+    if args.templates > 0:
+        wl.m1, wl.m2 = wl.m1[:args.templates], wl.m2[:args.templates]
     spec = wl.segments[0]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -316,7 +320,7 @@ def main():
     trig_h = torch.empty((cap, 6), dtype=torch.float32, pin_memory=True)
     d2h = []
     e2e_ms = []
-    for k in range(args.e2e_steps + 2):
+    for k in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         seg = mf.Segment(s_host.numpy(), spec.fs)
@@ -332,13 +336,13 @@ def main():
         if k >= 2:
             e2e_ms.append(dt * 1e3)
             d2h.append(peaks_h.numel() * 4 + 8 + n * 24)
-    e2e_tot = sum(e2e_ms)
+    e2e_tot = sum(e2e_ms) if e2e_ms else float("nan")
     if dist:
         t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_tot = float(t.item())
-    e2e = {"value": world * wl.n_templates * len(e2e_ms) / (e2e_tot / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)),
+    e2e = {"value": world * wl.n_templates * len(e2e_ms) / (e2e_tot / 1e3) if e2e_ms else None, "unit": UNIT,
+           "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)) if d2h else 0,
            "includes": "host s -> mf_segment_upload (H2D inside), mf_filter_bank, D2H peaks + n_trig + triggers"}
 
     cpu = None

@@ -123,15 +123,11 @@ struct Workspace {
     uint32_t *idx_a = nullptr, *idx_b = nullptr;
     unsigned long long *counter = nullptr;
     int *status = nullptr;
-    unsigned *ctl = nullptr;      // persistent scheduler: [0] head, [1] abort, then doneA, done1, done2 per unit
-    int2 *items = nullptr;        // persistent scheduler work queue
-    int64_t items_cap = 0;
-    int64_t items_key[4] = {-1, -1, -1, -1};   // (units, nA, n1, n2) the device queue was built for
-    int64_t items_n = 0;
+    unsigned *ctl = nullptr;      // persistent scheduler: [1] abort, then doneA, done1, done2 per unit
     void release() {
         cudaFree(units); cudaFree(exch); cudaFree(anchors); cudaFree(anchors4); cudaFree(partials);
         cudaFree(staged); cudaFree(keys); cudaFree(keys_tmp); cudaFree(idx_a); cudaFree(idx_b);
-        cudaFree(counter); cudaFree(status); cudaFree(ctl); cudaFree(items);
+        cudaFree(counter); cudaFree(status); cudaFree(ctl);
         *this = Workspace();
     }
 };
@@ -417,7 +413,7 @@ static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch,
 // Persistent scheduler geometry: anchors LA rounds ahead of their pass 1, pass
 // 2 of a unit D2 rounds after its pass 1, exchange ring S > D2 slots, anchor
 // ring SA > LA slots (every wait then points to an earlier queue item).
-constexpr int kLA = 2, kD2 = 3, kS = kD2 + 3, kSA = kLA + 3;
+constexpr int kLA = 4, kD2 = 4, kS = kD2 + 4, kSA = kLA + 4;
 
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
     if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32) return false;
@@ -425,41 +421,43 @@ static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
     return !(e && strcmp(e, "batch") == 0);
 }
 
-// Work queue in rounds r: A(r + LA) chunks, P1(r) tiles, P2(r - D2) tiles.
-static void build_queue(int64_t U, int nA, int n1, int n2, std::vector<int2> &q) {
-    q.clear();
-    q.reserve((size_t)(U * (nA + n1 + n2)));
-    auto push = [&](int64_t u, int phase, int tile) { q.push_back(make_int2((int)u, (phase << 16) | tile)); };
-    for (int64_t u = 0; u < std::min<int64_t>(kLA, U); ++u)
-        for (int c = 0; c < nA; ++c) push(u, 0, c);
-    for (int64_t r = 0; r < U + kD2; ++r) {
-        if (r + kLA < U)
-            for (int c = 0; c < nA; ++c) push(r + kLA, 0, c);
-        if (r < U)
-            for (int i = 0; i < n1; ++i) push(r, 1, i);
-        if (r >= kD2 && r - kD2 < U)
-            for (int i = 0; i < n2; ++i) push(r - kD2, 2, i);
+// Rounds rho = -LA .. U + D2 - 1; round rho holds the anchor chunks of unit
+// rho + LA, the pass-1 tiles of unit rho and the pass-2 tiles of unit rho - D2
+// (those units that exist).  Consecutive rounds with the same membership form
+// one regime.  Returns false if the queue would not fit an int index.
+static bool build_regimes(int64_t U, int nA, int n1, int n2, PersistParams &P) {
+    auto flags = [&](int64_t rho) {
+        int f = 0;
+        if (rho + kLA >= 0 && rho + kLA < U) f |= 1;
+        if (rho >= 0 && rho < U) f |= 2;
+        if (rho - kD2 >= 0 && rho - kD2 < U) f |= 4;
+        return f;
+    };
+    int64_t q = 0;
+    int nr = 0;
+    for (int64_t rho = -kLA; rho < U + kD2;) {
+        const int f = flags(rho);
+        int64_t end = rho + 1;
+        while (end < U + kD2 && flags(end) == f) ++end;
+        const int64_t size = ((f & 1) ? nA : 0) + ((f & 2) ? n1 : 0) + ((f & 4) ? n2 : 0);
+        if (size > 0) {
+            if (nr >= kMaxRegimes) return false;
+            P.reg[nr].rho0 = (int)rho;
+            P.reg[nr].first = (int)q;
+            P.reg[nr].size = (int)size;
+            P.reg[nr].rounds = (int)(end - rho);
+            P.reg[nr].flags = f;
+            ++nr;
+            q += size * (end - rho);
+            if (q >= ((int64_t)1 << 31) - 1) return false;
+        }
+        rho = end;
     }
-}
-
-static int ensure_queue(mf_bank_s *b, int64_t U, int nA, int n1, int n2, cudaStream_t st) {
-    Workspace &w = b->ws;
-    if (w.items && w.items_key[0] == U && w.items_key[1] == nA && w.items_key[2] == n1 && w.items_key[3] == n2)
-        return MF_OK;
-    std::vector<int2> q;
-    build_queue(U, nA, n1, n2, q);
-    if ((int64_t)q.size() > w.items_cap) {
-        MF_CUDA(cudaStreamSynchronize(st));
-        cudaFree(w.items);
-        w.items = nullptr;
-        MF_CUDA(cudaMalloc(&w.items, sizeof(int2) * q.size()));
-        w.items_cap = (int64_t)q.size();
-    }
-    MF_CUDA(cudaMemcpyAsync(w.items, q.data(), sizeof(int2) * q.size(), cudaMemcpyHostToDevice, st));
-    MF_CUDA(cudaStreamSynchronize(st));   // q is a host temporary
-    w.items_n = (int64_t)q.size();
-    w.items_key[0] = U; w.items_key[1] = nA; w.items_key[2] = n1; w.items_key[3] = n2;
-    return MF_OK;
+    P.n_reg = nr;
+    P.n_items = (int)q;
+    P.LA = kLA;
+    P.D2 = kD2;
+    return true;
 }
 
 static int sm_count() {
@@ -545,19 +543,19 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         MF_CUDA(launch_units(sd, b->d_tmpl, n_t, b->params.f_low, threshold, lgD, w.units, st));
         prof_end(b, pi, st);
         count_launches(1);
-        if (use_persistent(b, segs[s])) {
-            int n1 = 0, n2 = 0;
+        PersistParams P;
+        int n1 = 0, n2 = 0, nA = 0;
+        bool persist = use_persistent(b, segs[s]);
+        if (persist) {
             persist_tiles(sd.log2N, &n1, &n2);
-            const int nA = (man + 1023) / 1024;
-            int rq = ensure_queue(b, n_t, nA, n1, n2, st);
-            if (rq) return rq;
-            MF_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(unsigned) * (2 + 3 * (size_t)n_t), st));
-            PersistParams P;
+            nA = (man + 1023) / 1024;
+            persist = build_regimes(n_t, nA, n1, n2, P);
+        }
+        if (persist) {
+            MF_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(unsigned) * (2 + 3 * (size_t)n_t), st));   // head, abort, counters
             P.seg = sd;
             P.tmpl = b->d_tmpl;
             P.units = w.units;
-            P.items = w.items;
-            P.n_items = (int)w.items_n;
             P.log2D = lgD;
             P.max_anc = man;
             P.nA = nA;
@@ -582,14 +580,30 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             P.peaks = peaks;
             P.spin_limit = b->spin_limit;
             P.stall_unit = (int)b->stall_unit;
+            P.stats = nullptr;
+            const bool want_stats = getenv("MFGB_SCHED_STATS") != nullptr;
+            if (want_stats) {
+                MF_CUDA(cudaMallocAsync(&P.stats, sizeof(unsigned long long) * 12, st));
+                MF_CUDA(cudaMemsetAsync(P.stats, 0, sizeof(unsigned long long) * 12, st));
+            }
             double by = 16.0 * (double)sd.N * n_t;
             if (b->prof_on)
                 for (int t = 0; t < n_t; ++t) by += band_bytes[(size_t)t] + anc_bytes[(size_t)t];
             const int grid = std::max(1, persist_blocks_per_sm(sd.log2N)) * sm_count();
             pi = prof_begin(b, MF_STAGE_FUSED, by, st);
-            MF_CUDA(launch_persistent(P, std::min<int64_t>(grid, w.items_n), st));
+            MF_CUDA(launch_persistent(P, std::min<int64_t>(grid, P.n_items), st));
             prof_end(b, pi, st);
             count_launches(1);
+            if (want_stats) {   // diagnostics only: synchronises
+                unsigned long long h[12];
+                MF_CUDA(cudaMemcpyAsync(h, P.stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+                MF_CUDA(cudaStreamSynchronize(st));
+                cudaFreeAsync(P.stats, st);
+                const char *nm[3] = {"anchors", "pass1", "pass2"};
+                for (int ph = 0; ph < 3; ++ph)
+                    fprintf(stderr, "mfgb sched %-7s items %8llu waited %8llu  wait %.3e cyc\n", nm[ph],
+                            h[4 * ph + 2], h[4 * ph + 3], (double)h[4 * ph + 1]);
+            }
             continue;
         }
         for (int u0 = 0; u0 < n_t; u0 += (int)batch) {

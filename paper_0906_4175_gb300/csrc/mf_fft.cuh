@@ -93,13 +93,40 @@ __device__ __forceinline__ float2 tw_const(float2 x) {
 // In-register DFT of length R (natural order in and out), radix-2 DIT
 // recursion with compile-time twiddles:  X_q = sum_r v_r exp(SIGN 2 pi i r q / R)
 // ----------------------------------------------------------------------------
+__host__ __device__ constexpr double cx_abs(double x) { return x < 0 ? -x : x; }
+
+// Radix-2 combine  v[Q] = e[Q] + w o[Q],  v[Q + R/2] = e[Q] - w o[Q],
+// w = exp(SIGN 2 pi i Q / R).  A general w = c + i s is applied in the
+// multiply-add form of Linzer & Feig (1993): w o = c (o (1 + i s/c)) when
+// |c| >= |s|, else s (o (c/s + i)); the inner product takes 2 FMAs and the
+// scaled add/subtract 4, i.e. 6 instead of 8 instructions.
 template <int R, int SIGN, int Q>
 struct Combine {
     static __device__ __forceinline__ void run(float2 *v, const float2 *e, const float2 *o) {
         if constexpr (Q < R / 2) {
-            float2 t = tw_const<Q, R, SIGN>(o[Q]);
-            v[Q] = cadd(e[Q], t);
-            v[Q + R / 2] = csub(e[Q], t);
+            constexpr long long g = Q % R;
+            if constexpr (g == 0 || 4 * g == R) {
+                const float2 t = tw_const<Q, R, SIGN>(o[Q]);
+                v[Q] = cadd(e[Q], t);
+                v[Q + R / 2] = csub(e[Q], t);
+            } else {
+                constexpr CxCS w = cx_sincos_turn(SIGN * g, R);
+                float2 b;
+                float k;
+                if constexpr (cx_abs(w.c) >= cx_abs(w.s)) {
+                    constexpr float tt = (float)(w.s / w.c);
+                    constexpr float kc = (float)w.c;
+                    b = make_float2(fmaf(-tt, o[Q].y, o[Q].x), fmaf(tt, o[Q].x, o[Q].y));
+                    k = kc;
+                } else {
+                    constexpr float ct = (float)(w.c / w.s);
+                    constexpr float ks = (float)w.s;
+                    b = make_float2(fmaf(ct, o[Q].x, -o[Q].y), fmaf(ct, o[Q].y, o[Q].x));
+                    k = ks;
+                }
+                v[Q] = make_float2(fmaf(k, b.x, e[Q].x), fmaf(k, b.y, e[Q].y));
+                v[Q + R / 2] = make_float2(fmaf(-k, b.x, e[Q].x), fmaf(-k, b.y, e[Q].y));
+            }
             Combine<R, SIGN, Q + 1>::run(v, e, o);
         }
     }
@@ -188,10 +215,42 @@ struct FftShape {
 
 __device__ __forceinline__ int spad(int m) { return m + (m >> 5); }
 
+// Twiddle tables of the Stockham stages after stage 0, in shared memory:
+// for a stage (Ns, R) the entries w[r * Ns + k] = exp(+2 pi i r k / (Ns R)),
+// r < R, k < Ns (k fastest, so a warp reading one r hits consecutive words).
+// Stage 1 has Ns = 32; stage 2 (L > 1024) has Ns = 1024.
+template <int L>
+struct TwTable {
+    static constexpr int S1 = 32 * FftShape<L>::R1;                        // stage-1 entries
+    static constexpr int S2 = (FftShape<L>::NST == 3) ? 1024 * FftShape<L>::R2 : 0;
+    static constexpr int SIZE = (FftShape<L>::NST == 1) ? 0 : S1 + S2;
+};
+
+// Fill the table of an L-point FFT (all threads of the block; callers
+// synchronise before first use).
+template <int L>
+__device__ __forceinline__ void fill_twiddles(float2 *tw) {
+    using S = FftShape<L>;
+    if constexpr (S::NST >= 2) {
+        constexpr int LG1 = cx_ilog2(32 * S::R1);
+        for (int m = threadIdx.x; m < TwTable<L>::S1; m += blockDim.x) {
+            const int r = m >> 5, k = m & 31;
+            tw[m] = unit_root<+1>((uint32_t)(r * k), LG1);
+        }
+    }
+    if constexpr (S::NST == 3) {
+        constexpr int LG2 = cx_ilog2(L);
+        for (int m = threadIdx.x; m < TwTable<L>::S2; m += blockDim.x) {
+            const int r = m >> 10, k = m & 1023;
+            tw[TwTable<L>::S1 + m] = unit_root<+1>((uint32_t)(r * k), LG2);
+        }
+    }
+}
+
 // One Stockham stage reading from and (unless LAST) writing to shared memory.
 // Ns = product of earlier radices; each thread runs 32/R butterflies b = t + i*T.
 template <int L, int R, int Ns, int SIGN, bool LAST, class Snk>
-__device__ __forceinline__ void stockham_stage(float2 *sq, int seq, int t, Snk &snk) {
+__device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int seq, int t, Snk &snk) {
     constexpr int T = L / 32;
     constexpr int NB = 32 / R;
     constexpr int SPAN = L / R;
@@ -208,8 +267,12 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, int seq, int t, Snk &
         const int b = t + i * T;
         const int k = b & (Ns - 1);
         if constexpr (Ns > 1) {
-            constexpr int LG = cx_ilog2(Ns * R);
-            twiddle_powers<R>(v + i * R, unit_root<SIGN>((uint32_t)k, LG));
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * Ns + k];
+                if (SIGN < 0) w.y = -w.y;
+                v[i * R + r] = cmul(v[i * R + r], w);
+            }
         }
         Dft<R, SIGN>::run(v + i * R);
         if constexpr (LAST) {
@@ -223,14 +286,17 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, int seq, int t, Snk &
     if constexpr (!LAST) __syncthreads();
 }
 
-// Full CTA FFT.  Src::load(seq, t, v) fills v[r] = x[t + r*T], r < 32
+// Full CTA FFT.  tw: the TwTable<L> twiddles in shared memory, filled and
+// made visible before the call (or filled before it with no intervening
+// shared-memory write, the first stage barrier publishes them).
+// Src::load(seq, t, v) fills v[r] = x[t + r*T], r < 32
 // (Src::kHalfZero: v[16..31] are zero and are not read).
 // Snk::store<R>(seq, b, stride, v) receives outputs b + r*stride, r < R.
 // The last stage does not synchronise: a sink that reuses shared memory
 // afterwards must __syncthreads() first.
 // smem: C * FftShape<L>::STRIDE float2.  Must be called by all C*T threads.
 template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
-__device__ __forceinline__ void cta_fft(float2 *smem, Src &src, Snk &snk) {
+__device__ __forceinline__ void cta_fft(float2 *smem, const float2 *tw, Src &src, Snk &snk) {
     using S = FftShape<L>;
     constexpr int T = S::T;
     const int tid = threadIdx.x;
@@ -253,10 +319,10 @@ __device__ __forceinline__ void cta_fft(float2 *smem, Src &src, Snk &snk) {
     }
     __syncthreads();
     if constexpr (S::NST == 2) {
-        stockham_stage<L, S::R1, 32, SIGN, true>(sq, seq, t, snk);
+        stockham_stage<L, S::R1, 32, SIGN, true>(sq, tw, seq, t, snk);
     } else if constexpr (S::NST == 3) {
-        stockham_stage<L, S::R1, 32, SIGN, false>(sq, seq, t, snk);
-        stockham_stage<L, S::R2, 32 * S::R1, SIGN, true>(sq, seq, t, snk);
+        stockham_stage<L, S::R1, 32, SIGN, false>(sq, tw, seq, t, snk);
+        stockham_stage<L, S::R2, 32 * S::R1, SIGN, true>(sq, tw + TwTable<L>::S1, seq, t, snk);
     }
 }
 

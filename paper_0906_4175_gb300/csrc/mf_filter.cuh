@@ -47,6 +47,8 @@ __device__ __forceinline__ void anchor_record(double c1, double c2, double c3, d
 template <int L, int C>
 struct TemplateSrc {
     static constexpr bool kHalfZero = true;
+    // one anchor record (float4 + float) per non-zero column row, staged per tile
+    static constexpr size_t kScratchBytes = (size_t)(L / 2) * (sizeof(float4) + sizeof(float));
     struct Params {
         const float2 *W;
         const UnitInfo *units;
@@ -56,31 +58,76 @@ struct TemplateSrc {
     };
     const Params &p;
     const int tile, unit, slot;
-    __device__ TemplateSrc(const Params &pp, int tl, int un, int sl) : p(pp), tile(tl), unit(un), slot(sl) {}
+    float4 *sa;
+    float *sa4;
+    __device__ TemplateSrc(const Params &pp, int tl, int un, int sl, void *scratch)
+        : p(pp), tile(tl), unit(un), slot(sl), sa((float4 *)scratch), sa4((float *)((float4 *)scratch + L / 2)) {}
+    // All threads of the block call load() (it contains a block barrier).
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         constexpr int T = L / 32;
         const UnitInfo u = p.units[unit];
-        const float4 *anc = p.anchors + (int64_t)slot * p.anc_stride - u.g_lo;
-        const float *anc4 = p.anchors4 + (int64_t)slot * p.anc_stride - u.g_lo;
+        const float4 *anc0 = p.anchors + (int64_t)slot * p.anc_stride;   // index: anchor - g_lo
+        const float *anc40 = p.anchors4 + (int64_t)slot * p.anc_stride;
         const int k1 = tile * C + seq;
-        const int half = (1 << p.log2D) >> 1;
+        const int D = 1 << p.log2D;
+        float2 w[16];
+        bool in[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int k = k1 + ((t + r * T) << p.log2N1);
-            const bool in = (k >= u.k_lo) && (k < u.k_hi);
-            const int kk = in ? k : u.k_lo;
-            const float2 w = __ldg(&p.W[kk]);
-            const int g = kk >> p.log2D;
-            const float4 a = __ldcg(&anc[g]);   // anchors may be rewritten in the same launch (ring)
-            const float a4 = __ldcg(&anc4[g]);
-            const float d = (float)(kk - ((g << p.log2D) + half));
-            float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
-            ph -= rintf(ph);
-            float s, c;
-            __sincosf(6.283185307179586f * ph, &s, &c);
-            // W * e^{-i 2 pi ph}
-            const float2 x = make_float2(fmaf(w.x, c, w.y * s), fmaf(w.y, c, -w.x * s));
-            v[r] = in ? x : czero();
+            in[r] = (k >= u.k_lo) && (k < u.k_hi);
+            w[r] = __ldg(&p.W[in[r] ? k : u.k_lo]);
+        }
+        if (D >= C && p.log2D <= p.log2N1) {
+            // Every column of this tile falls in the same anchor group on a
+            // given row n, so the tile needs one anchor per row:
+            // g(n) = (tile C >> log2D) + n (N1 >> log2D), staged once in shared memory.
+            const int gstep = 1 << (p.log2N1 - p.log2D);
+            const int gbase = ((tile * C) >> p.log2D) - u.g_lo;
+            for (int n = threadIdx.x; n < L / 2; n += blockDim.x) {
+                const int a = gbase + n * gstep;
+                if (a >= 0 && a < u.n_anc) {
+                    sa[n] = __ldcg(&anc0[a]);   // anchors may be rewritten in the same launch (ring)
+                    sa4[n] = __ldcg(&anc40[a]);
+                }
+            }
+            __syncthreads();
+            // offset from the anchor centre is the same on every row (D divides N1)
+            const float d = (float)((k1 & (D - 1)) - (D >> 1));
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int n = t + r * T;
+                float2 x = czero();
+                if (in[r]) {
+                    const float4 a = sa[n];
+                    const float a4 = sa4[n];
+                    float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
+                    ph -= rintf(ph);
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * ph, &sn, &cs);
+                    x = make_float2(fmaf(w[r].x, cs, w[r].y * sn), fmaf(w[r].y, cs, -w[r].x * sn));  // W e^{-i 2 pi ph}
+                }
+                v[r] = x;
+            }
+        } else {
+            const float4 *anc = anc0 - u.g_lo;
+            const float *anc4 = anc40 - u.g_lo;
+            const int half = D >> 1;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int k = k1 + ((t + r * T) << p.log2N1);
+                const int kk = in[r] ? k : u.k_lo;
+                const int g = kk >> p.log2D;
+                const float4 a = __ldcg(&anc[g]);
+                const float a4 = __ldcg(&anc4[g]);
+                const float d = (float)(kk - ((g << p.log2D) + half));
+                float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
+                ph -= rintf(ph);
+                float sn, cs;
+                __sincosf(6.283185307179586f * ph, &sn, &cs);
+                const float2 x = make_float2(fmaf(w[r].x, cs, w[r].y * sn), fmaf(w[r].y, cs, -w[r].x * sn));
+                v[r] = in[r] ? x : czero();
+            }
         }
     }
 };
@@ -96,9 +143,10 @@ struct TemplateSrcF32 {
         int log2N1;
         float df;
     };
+    static constexpr size_t kScratchBytes = 0;
     const Params &p;
     const int tile, unit;
-    __device__ TemplateSrcF32(const Params &pp, int tl, int un, int) : p(pp), tile(tl), unit(un) {}
+    __device__ TemplateSrcF32(const Params &pp, int tl, int un, int, void *) : p(pp), tile(tl), unit(un) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         constexpr int T = L / 32;
         const UnitInfo u = p.units[unit];
@@ -153,28 +201,42 @@ struct RhoSink {
     template <int R>
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) {
         const int j2 = tile * C + seq;
-        bool any = false;
         float pw[R];
+        float m = 0.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
-            const int j = j2 + ((b + r * stride) << p.log2N2);
-            if (pw[r] > bp || (pw[r] == bp && j < bj)) { bp = pw[r]; bj = j; bz = v[r]; }
-            any |= pw[r] > u.thr2;
+            m = fmaxf(m, pw[r]);
         }
-        if (__any_sync(0xffffffffu, any)) {
+        // The butterfly's outputs j2 + N2 (b + r stride) increase with r, so its
+        // argmax with the lowest-j tie rule is the first r with pw[r] == m.
+        if (m >= bp) {
+            int rs = R - 1;
+#pragma unroll
+            for (int r = R - 2; r >= 0; --r) rs = (pw[r] == m) ? r : rs;
+            const int j = j2 + ((b + rs * stride) << p.log2N2);
+            if (m > bp || j < bj) {
+                float2 z = v[R - 1];
+#pragma unroll
+                for (int r = R - 2; r >= 0; --r) z = (r == rs) ? v[r] : z;
+                bp = m;
+                bj = j;
+                bz = z;
+            }
+        }
+        if (__any_sync(0xffffffffu, m > u.thr2)) {
             const int lane = threadIdx.x & 31;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const bool pred = pw[r] > u.thr2;
-                const unsigned m = __ballot_sync(0xffffffffu, pred);
-                if (m == 0u) continue;   // warp-uniform
-                const int leader = __ffs(m) - 1;
+                const unsigned msk = __ballot_sync(0xffffffffu, pred);
+                if (msk == 0u) continue;   // warp-uniform
+                const int leader = __ffs(msk) - 1;
                 unsigned long long base = 0ull;
-                if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(m));
+                if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(msk));
                 base = __shfl_sync(0xffffffffu, base, leader);
                 if (pred) {
-                    const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+                    const unsigned long long slot = base + (unsigned long long)__popc(msk & ((1u << lane) - 1u));
                     if (slot < (unsigned long long)p.cap) {
                         const int j = j2 + ((b + r * stride) << p.log2N2);
                         mf_trigger tr;

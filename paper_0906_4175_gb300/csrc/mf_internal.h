@@ -48,13 +48,28 @@ struct KeyLayout {
     int j_bits, seg_bits, tmpl_bits;
 };
 
+// The persistent scheduler's work queue is a sequence of rounds rho; round
+// rho holds, in order, the anchor chunks of unit rho + LA, the pass-1 tiles of
+// unit rho and the pass-2 tiles of unit rho - D2 (each only if that unit
+// exists).  Rounds with the same membership form a regime of equal size.
+struct QueueRegime {
+    int rho0;      // first round of the regime
+    int first;     // queue index of its first item
+    int size;      // items per round
+    int rounds;    // number of rounds
+    int flags;     // 1: anchors, 2: pass 1, 4: pass 2
+};
+constexpr int kMaxRegimes = 8;
+
 // Everything the persistent bank scheduler (mf_persist.cu) needs for one segment.
 struct PersistParams {
     SegDev seg;
     const double *tmpl;
     const UnitInfo *units;
-    const int2 *items;          // work queue: {unit, phase << 16 | tile}, phase 0 = A, 1 = P1, 2 = P2
+    QueueRegime reg[kMaxRegimes];
+    int n_reg;
     int n_items;
+    int LA, D2;
     int log2D, max_anc, nA, S, SA;
     float4 *anchors;            // SA slots of max_anc records
     float *anchors4;
@@ -72,6 +87,7 @@ struct PersistParams {
     mf_peak *peaks;
     long long spin_limit;       // bounded-wait iterations (back-off <= ~1 us each)
     int stall_unit;             // test hook: this unit's pass 2 waits for a count never reached (-1: off)
+    unsigned long long *stats;  // diagnostics (nullable): per phase [work cycles, wait cycles, items, waited items]
 };
 
 // ---- launch wrappers (defined in the .cu files; return cudaError_t) -----

@@ -16,22 +16,30 @@ __host__ __device__ constexpr int seqs_per_cta(int other) {
 }
 
 template <int L, int C>
-__host__ __device__ constexpr size_t pass_smem_bytes() {
+__host__ __device__ constexpr size_t pass_data_bytes() {
     return (size_t)C * FftShape<L>::STRIDE * sizeof(float2);
+}
+// data area, then the twiddle table, then the source's scratch
+template <int L, int C, class Src>
+__host__ __device__ constexpr size_t pass_smem_bytes() {
+    return pass_data_bytes<L, C>() + (size_t)TwTable<L>::SIZE * sizeof(float2) + Src::kScratchBytes;
 }
 
 // Every source and sink is constructed with (params, tile, unit, slot): tile
 // = which group of C sequences, unit = (template, segment) unit index, slot =
-// which batch entry of the ring buffers it reads or writes.
+// which batch entry of the ring buffers it reads or writes; a source also gets
+// Src::kScratchBytes of shared memory of its own.
 // Generic pass kernel: grid.x = N_other / C tiles, grid.y = batch
 // (unit = unit0 + blockIdx.y, slot = blockIdx.y).
 template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
 __global__ void __launch_bounds__(C *(L / 32), (C * (L / 32) >= 256) ? 2 : 1)
     k_fft_pass(typename Src::Params sp, typename Snk::Params kp, int unit0) {
     extern __shared__ float2 smem[];
-    Src src(sp, blockIdx.x, unit0 + blockIdx.y, blockIdx.y);
+    float2 *tw = smem + pass_data_bytes<L, C>() / sizeof(float2);
+    fill_twiddles<L>(tw);
+    Src src(sp, blockIdx.x, unit0 + blockIdx.y, blockIdx.y, tw + TwTable<L>::SIZE);
     Snk snk(kp, blockIdx.x, unit0 + blockIdx.y, blockIdx.y);
-    cta_fft<L, C, SEQ_FAST, SIGN>(smem, src, snk);
+    cta_fft<L, C, SEQ_FAST, SIGN>(smem, tw, src, snk);
     snk.finish(smem);
 }
 
@@ -39,14 +47,14 @@ template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
 cudaError_t set_pass_attrs() {
     return cudaFuncSetAttribute(k_fft_pass<L, C, SEQ_FAST, SIGN, Src, Snk>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pass_smem_bytes<L, C>());
+                                (int)pass_smem_bytes<L, C, Src>());
 }
 
 template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
 cudaError_t run_pass(dim3 grid, const typename Src::Params &sp, const typename Snk::Params &kp,
                      cudaStream_t st, int unit0 = 0) {
     k_fft_pass<L, C, SEQ_FAST, SIGN, Src, Snk>
-        <<<grid, C * (L / 32), pass_smem_bytes<L, C>(), st>>>(sp, kp, unit0);
+        <<<grid, C * (L / 32), pass_smem_bytes<L, C, Src>(), st>>>(sp, kp, unit0);
     return cudaGetLastError();
 }
 
@@ -80,10 +88,11 @@ __host__ __device__ inline int log2_n2(int log2N) { return log2N / 2; }
 template <int L, int C, bool HALF_ZERO>
 struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO
     static constexpr bool kHalfZero = HALF_ZERO;
+    static constexpr size_t kScratchBytes = 0;
     struct Params { const float2 *X; int log2N1; int64_t batch_stride; };
     const Params &p;
     const int tile, slot;
-    __device__ ColComplexSrc(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
+    __device__ ColComplexSrc(const Params &pp, int tl, int, int sl, void *) : p(pp), tile(tl), slot(sl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         const float2 *X = p.X + (int64_t)slot * p.batch_stride;
         const int k1 = tile * C + seq;
@@ -97,10 +106,11 @@ struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO
 template <int L, int C>
 struct ColRealSrc {         // real samples s[n] (imaginary part zero)
     static constexpr bool kHalfZero = false;
+    static constexpr size_t kScratchBytes = 0;
     struct Params { const float *s; int log2N1; };
     const Params &p;
     const int tile;
-    __device__ ColRealSrc(const Params &pp, int tl, int, int) : p(pp), tile(tl) {}
+    __device__ ColRealSrc(const Params &pp, int tl, int, int, void *) : p(pp), tile(tl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         const int k1 = tile * C + seq;
         constexpr int T = L / 32;
@@ -140,10 +150,11 @@ struct ExchSink {
 template <int L, int C>
 struct RowSrc {
     static constexpr bool kHalfZero = false;
+    static constexpr size_t kScratchBytes = 0;
     struct Params { const float2 *E; int log2N1; int log2N; };
     const Params &p;
     const int tile, slot;
-    __device__ RowSrc(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
+    __device__ RowSrc(const Params &pp, int tl, int, int sl, void *) : p(pp), tile(tl), slot(sl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         const float2 *E = p.E + ((int64_t)slot << p.log2N);
         const int j2 = tile * C + seq;
