@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--templates", type=int, default=0,
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     return ap.parse_args()
 
 
@@ -258,6 +259,15 @@ def main():
         mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
         segs.append(seg)   # keep alive until the stream has drained
 
+    schedule = {"scheduler": "default"}
+    if not args.no_autotune:
+        seg0 = mf.Segment(s_dev, spec.fs)
+        cache = os.path.join(tempfile.gettempdir(), "mfgb_autotune_%d.json" % rank)
+        mf.autotune(bank, [seg0], wl.threshold, repeats=2, cache_path=cache)
+        with open(cache) as fh:
+            schedule = json.load(fh)
+        os.unlink(cache)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -380,6 +390,7 @@ def main():
                        "segments": 1, "threshold": wl.threshold, "n_trig_per_step": n_trig,
                        "l2": "flushed before every timed step (256 MiB write)",
                        "step": "mf_segment_upload (device s) + mf_filter_bank",
+                       "schedule": schedule,
                        "phase": "FP64 anchors + FP32 Taylor; FFT FP32"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "path_roofline": path,
             "rho_err": acc, "cpu_baseline": cpu, "wall_s_timed": wall}

@@ -141,6 +141,19 @@ int mf_filter_bank(mf_bank bank, const mf_segment *segs, int n_seg, float thresh
  * MF_ETIMEOUT (a bounded device-side wait of that call expired). */
 int mf_bank_check(mf_bank bank, void *cuda_stream);
 
+/* mf_autotune -- times the candidate schedules of mf_filter_bank for this
+ * bank on these segments (the persistent scheduler with 55/60/65% of the SMs
+ * starting on template generation + column FFTs, and per-batch launches of
+ * 16..128 templates) and keeps the fastest in the bank for later calls.  It
+ * runs each candidate 1 + repeats times on cuda_stream and synchronises; it
+ * allocates temporary outputs and may grow the bank's workspace.  threshold
+ * should be the one the search will use (it sets the trigger traffic).  If
+ * cache_path is not NULL the choice is written there as one JSON line.
+ * Results of mf_filter_bank do not depend on the schedule (bit-identical).
+ * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold, int repeats,
+                const char *cache_path, void *cuda_stream);
+
 /* mf_synth_segment -- seeded synthetic data: stationary Gaussian noise
  * coloured by S_n (Eq. 2, or psd) plus frequency-domain injections, the
  * stand-in for the paper's coloured-noise test data (Sec. 3).

@@ -18,7 +18,7 @@ from . import _native
 from ._native import (INJ_DTYPE, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
                       MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
 
-__all__ = ["Bank", "Segment", "filter_bank", "synth_segment", "refine", "RefineFn", "MFError",
+__all__ = ["Bank", "Segment", "filter_bank", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
            "PEAK_DTYPE", "TRIG_DTYPE", "INJ_DTYPE", "MF_PHASE_ANCHOR", "MF_PHASE_FP64", "MF_PHASE_FP32",
            "peaks_to_numpy", "triggers_to_numpy", "version"]
 
@@ -168,6 +168,14 @@ def filter_bank(bank: Bank, segments, threshold: float, trig_cap: int = 1 << 20,
                                        trig.data_ptr(), int(trig_cap), n_trig.data_ptr(),
                                        _stream_ptr(stream)))
     return peaks, trig, n_trig
+
+
+def autotune(bank: Bank, segments, threshold: float, repeats: int = 2, cache_path: str = None, stream=None):
+    """mf_autotune: time the candidate schedules on this bank and keep the fastest."""
+    segs = list(segments) if isinstance(segments, (list, tuple)) else [segments]
+    arr = (ctypes.c_void_p * len(segs))(*[s.handle.value for s in segs])
+    check(_native.lib().mf_autotune(bank.handle, arr, len(segs), float(threshold), int(repeats),
+                                    cache_path.encode() if cache_path else None, _stream_ptr(stream)))
 
 
 def peaks_to_numpy(peaks) -> np.ndarray:

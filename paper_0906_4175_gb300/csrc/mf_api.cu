@@ -150,6 +150,12 @@ struct mf_bank_s {
     std::vector<ProfRec> prof;
     int64_t stall_unit = -1;          // test hook (mf_bank_debug_stall)
     long long spin_limit = 4000000;   // bounded-wait iterations, back-off <= ~1 us each
+    // schedule (defaults until mf_autotune measures this bank): 0 = persistent
+    // scheduler, 1 = per-batch launches; templates per batch (0 = by L2 size);
+    // fraction of SMs that start on queue 1
+    int sched = 0;
+    int64_t tuned_batch = 0;
+    double split = 0.60;
 };
 
 // Records an event before a launch when profiling; returns the record index or -1.
@@ -373,8 +379,8 @@ static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
 }
 
 // templates in flight per batch (exchange ring of batch * N complex64)
-static int64_t choose_batch(int64_t N, int64_t n_t) {
-    int64_t b = ((int64_t)64 << 20) / (8 * N);
+static int64_t choose_batch(int64_t N, int64_t n_t, int64_t tuned) {
+    int64_t b = tuned > 0 ? tuned : ((int64_t)64 << 20) / (8 * N);
     if (const char *env = getenv("MFGB_BATCH")) b = atoll(env);
     if (b < 1) b = 1;
     if (b > 65535) b = 65535;
@@ -405,41 +411,43 @@ static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch,
     MF_CUDA(cudaMalloc(&w.counter, sizeof(unsigned long long)));
     MF_CUDA(cudaMalloc(&w.status, sizeof(int)));
     MF_CUDA(cudaMemset(w.status, 0, sizeof(int)));
-    MF_CUDA(cudaMalloc(&w.ctl, sizeof(unsigned) * (2 + 3 * b->n)));
+    MF_CUDA(cudaMalloc(&w.ctl, sizeof(unsigned) * (4 + 3 * b->n)));
     w.N = nN; w.n_t = b->n; w.cap = ncap; w.batch = nb; w.max_anc = na; w.nblk = nbl;
     return MF_OK;
 }
 
-// Persistent scheduler geometry: anchors LA rounds ahead of their pass 1, pass
-// 2 of a unit D2 rounds after its pass 1, exchange ring S > D2 slots, anchor
-// ring SA > LA slots (every wait then points to an earlier queue item).
-constexpr int kLA = 4, kD2 = 4, kS = kD2 + 4, kSA = kLA + 4;
+// Persistent scheduler geometry: anchor chunks LA rounds ahead of their pass
+// 1 in queue 1, anchor ring SA > LA slots, exchange ring S slots (pass 1 may
+// run up to S - 1 units ahead of pass 2).  The first kSplit of the SMs start
+// on queue 1 (anchors + pass 1, about 60% of the work), the rest on queue 2.
+constexpr int kLA = 4, kS = 8, kSA = kLA + 4;
+constexpr double kSplit = 0.60;
 
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
     if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32) return false;
-    const char *e = getenv("MFGB_SCHED");
-    return !(e && strcmp(e, "batch") == 0);
+    if (const char *e = getenv("MFGB_SCHED")) return strcmp(e, "batch") != 0;
+    return b->sched == 0;
 }
 
-// Rounds rho = -LA .. U + D2 - 1; round rho holds the anchor chunks of unit
-// rho + LA, the pass-1 tiles of unit rho and the pass-2 tiles of unit rho - D2
-// (those units that exist).  Consecutive rounds with the same membership form
-// one regime.  Returns false if the queue would not fit an int index.
-static bool build_regimes(int64_t U, int nA, int n1, int n2, PersistParams &P) {
+// Queue 1: rounds rho = -LA .. U - 1; round rho holds the anchor chunks of
+// unit rho + LA and the pass-1 tiles of unit rho (those units that exist);
+// consecutive rounds with the same membership form one regime.  Queue 2 holds
+// the pass-2 tiles of units 0 .. U - 1 in order.  Returns false if a queue
+// would not fit an int index.
+static bool build_queues(int64_t U, int nA, int n1, int n2, PersistParams &P) {
     auto flags = [&](int64_t rho) {
         int f = 0;
         if (rho + kLA >= 0 && rho + kLA < U) f |= 1;
         if (rho >= 0 && rho < U) f |= 2;
-        if (rho - kD2 >= 0 && rho - kD2 < U) f |= 4;
         return f;
     };
     int64_t q = 0;
     int nr = 0;
-    for (int64_t rho = -kLA; rho < U + kD2;) {
+    for (int64_t rho = -kLA; rho < U;) {
         const int f = flags(rho);
         int64_t end = rho + 1;
-        while (end < U + kD2 && flags(end) == f) ++end;
-        const int64_t size = ((f & 1) ? nA : 0) + ((f & 2) ? n1 : 0) + ((f & 4) ? n2 : 0);
+        while (end < U && flags(end) == f) ++end;
+        const int64_t size = ((f & 1) ? nA : 0) + ((f & 2) ? n1 : 0);
         if (size > 0) {
             if (nr >= kMaxRegimes) return false;
             P.reg[nr].rho0 = (int)rho;
@@ -453,10 +461,11 @@ static bool build_regimes(int64_t U, int nA, int n1, int n2, PersistParams &P) {
         }
         rho = end;
     }
+    if (U * (int64_t)n2 >= ((int64_t)1 << 31) - 1) return false;
     P.n_reg = nr;
-    P.n_items = (int)q;
+    P.n_items1 = (int)q;
+    P.n_items2 = (int)(U * n2);
     P.LA = kLA;
-    P.D2 = kD2;
     return true;
 }
 
@@ -504,7 +513,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     if (key_bits > 64) return set_err(MF_EINVAL, "trigger key needs %d bits", key_bits);
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    int64_t batch = choose_batch(maxN, b->n);
+    int64_t batch = choose_batch(maxN, b->n, b->tuned_batch);
     for (int s = 0; s < n_seg; ++s)
         if (use_persistent(b, segs[s])) batch = std::max<int64_t>(batch, std::max(kS, kSA));
     int64_t max_anc = 0, nblk = 0;
@@ -549,10 +558,11 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         if (persist) {
             persist_tiles(sd.log2N, &n1, &n2);
             nA = (man + 1023) / 1024;
-            persist = build_regimes(n_t, nA, n1, n2, P);
+            persist = build_queues(n_t, nA, n1, n2, P);
         }
         if (persist) {
-            MF_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(unsigned) * (2 + 3 * (size_t)n_t), st));   // head, abort, counters
+            // heads, abort flag, per-unit counters
+            MF_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(unsigned) * (4 + 3 * (size_t)n_t), st));
             P.seg = sd;
             P.tmpl = b->d_tmpl;
             P.units = w.units;
@@ -565,9 +575,13 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             P.anchors4 = w.anchors4;
             P.exch = w.exch;
             P.ctl = w.ctl;
-            P.doneA = w.ctl + 2;
-            P.done1 = w.ctl + 2 + n_t;
-            P.done2 = w.ctl + 2 + 2 * (size_t)n_t;
+            P.doneA = w.ctl + 4;
+            P.done1 = w.ctl + 4 + n_t;
+            P.done2 = w.ctl + 4 + 2 * (size_t)n_t;
+            P.n_sm = sm_count();
+            double split = b->split > 0.0 ? b->split : kSplit;
+            if (const char *e = getenv("MFGB_SPLIT")) split = atof(e);
+            P.split = std::min(P.n_sm - 1, std::max(1, (int)lround(split * P.n_sm)));
             P.status = w.status;
             P.partials = w.partials;
             P.staged = w.staged;
@@ -591,7 +605,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
                 for (int t = 0; t < n_t; ++t) by += band_bytes[(size_t)t] + anc_bytes[(size_t)t];
             const int grid = std::max(1, persist_blocks_per_sm(sd.log2N)) * sm_count();
             pi = prof_begin(b, MF_STAGE_FUSED, by, st);
-            MF_CUDA(launch_persistent(P, std::min<int64_t>(grid, P.n_items), st));
+            MF_CUDA(launch_persistent(P, grid, st));
             prof_end(b, pi, st);
             count_launches(1);
             if (want_stats) {   // diagnostics only: synchronises
@@ -604,6 +618,10 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
                     fprintf(stderr, "mfgb sched %-7s items %8llu waited %8llu  wait %.3e cyc\n", nm[ph],
                             h[4 * ph + 2], h[4 * ph + 3], (double)h[4 * ph + 1]);
             }
+            pi = prof_begin(b, MF_STAGE_FINAL, 16.0 * nbk * n_t, st);
+            MF_CUDA(launch_reduce_peaks(sd, w.units, n_t, w.partials, nbk, s, n_seg, peaks, st));
+            prof_end(b, pi, st);
+            count_launches(1);
             continue;
         }
         for (int u0 = 0; u0 < n_t; u0 += (int)batch) {
@@ -680,6 +698,74 @@ extern "C" int mf_bank_check(mf_bank b, void *cuda_stream) {
     MF_CUDA(cudaMemcpy(&st, b->ws.status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st & 2) return set_err(MF_ETIMEOUT, "a bounded device wait expired in the last mf_filter_bank");
     if (st & 1) return set_err(MF_EOVERFLOW, "more triggers than trig_cap in the last mf_filter_bank");
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate schedules of mf_filter_bank on this bank and these
+// segments and keep the fastest
+// ---------------------------------------------------------------------------
+extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float threshold, int repeats,
+                           const char *cache_path, void *cuda_stream) {
+    if (!b || !segs || n_seg < 1) return set_err(MF_EINVAL, "need a bank and n_seg >= 1 segments");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (repeats < 1) repeats = 2;
+    struct Cand { int sched; int64_t batch; double split; };
+    std::vector<Cand> cands;
+    for (double sp : {0.55, 0.60, 0.65}) cands.push_back({0, 0, sp});
+    int64_t maxN = 0;
+    for (int s = 0; s < n_seg; ++s) maxN = std::max(maxN, segs[s]->N);
+    for (int64_t bt : {16, 32, 64, 128})
+        if (bt * maxN * 8 <= ((int64_t)2 << 30)) cands.push_back({1, bt, 0.60});
+    const int64_t cap = 1 << 16;
+    mf_peak *pk = nullptr;
+    mf_trigger *tr = nullptr;
+    int64_t *nt = nullptr;
+    MF_CUDA(cudaMalloc(&pk, sizeof(mf_peak) * b->n * n_seg));
+    MF_CUDA(cudaMalloc(&tr, sizeof(mf_trigger) * cap));
+    MF_CUDA(cudaMalloc(&nt, sizeof(int64_t)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_sched = b->sched;
+    const int64_t saved_batch = b->tuned_batch;
+    const double saved_split = b->split;
+    float best_ms = 1e30f;
+    Cand best = {saved_sched, saved_batch, saved_split};
+    int rc = MF_OK;
+    for (const Cand &c : cands) {
+        b->sched = c.sched;
+        b->tuned_batch = c.batch;
+        b->split = c.split;
+        rc = mf_filter_bank(b, segs, n_seg, threshold, pk, tr, cap, nt, cuda_stream);   // warm-up, sizes workspace
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < repeats && !rc; ++r) rc = mf_filter_bank(b, segs, n_seg, threshold, pk, tr, cap, nt, cuda_stream);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_err(MF_ECUDA, "autotune timing"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(pk);
+    cudaFree(tr);
+    cudaFree(nt);
+    b->sched = best.sched;
+    b->tuned_batch = best.batch;
+    b->split = best.split;
+    if (rc) return rc;
+    if (cache_path && cache_path[0]) {
+        FILE *f = fopen(cache_path, "w");
+        if (!f) return set_err(MF_EINVAL, "cannot write %s", cache_path);
+        fprintf(f, "{\"N\": %lld, \"templates\": %lld, \"segments\": %d, \"scheduler\": \"%s\", \"batch\": %lld, "
+                   "\"split\": %.3f, \"ms_per_call\": %.4f}\n",
+                (long long)maxN, (long long)b->n, n_seg, best.sched == 0 ? "persistent" : "batch",
+                (long long)best.batch, best.split, best_ms / repeats);
+        fclose(f);
+    }
     return MF_OK;
 }
 

@@ -60,6 +60,7 @@ struct TemplateSrc {
     const int tile, unit, slot;
     float4 *sa;
     float *sa4;
+    unsigned *rel = nullptr;   // deferred release (persistent scheduler), done by thread 0 once loads are in flight
     __device__ TemplateSrc(const Params &pp, int tl, int un, int sl, void *scratch)
         : p(pp), tile(tl), unit(un), slot(sl), sa((float4 *)scratch), sa4((float *)((float4 *)scratch + L / 2)) {}
     // All threads of the block call load() (it contains a block barrier).
@@ -91,6 +92,7 @@ struct TemplateSrc {
                     sa4[n] = __ldcg(&anc40[a]);
                 }
             }
+            release_hook(rel);
             __syncthreads();
             // offset from the anchor centre is the same on every row (D divides N1)
             const float d = (float)((k1 & (D - 1)) - (D >> 1));
@@ -110,6 +112,7 @@ struct TemplateSrc {
                 v[r] = x;
             }
         } else {
+            release_hook(rel);
             const float4 *anc = anc0 - u.g_lo;
             const float *anc4 = anc40 - u.g_lo;
             const int half = D >> 1;

@@ -48,16 +48,16 @@ struct KeyLayout {
     int j_bits, seg_bits, tmpl_bits;
 };
 
-// The persistent scheduler's work queue is a sequence of rounds rho; round
-// rho holds, in order, the anchor chunks of unit rho + LA, the pass-1 tiles of
-// unit rho and the pass-2 tiles of unit rho - D2 (each only if that unit
-// exists).  Rounds with the same membership form a regime of equal size.
+// The persistent scheduler's first queue is a sequence of rounds rho; round
+// rho holds, in order, the anchor chunks of unit rho + LA and the pass-1 tiles
+// of unit rho (each only if that unit exists).  Rounds with the same
+// membership form a regime of equal size.
 struct QueueRegime {
     int rho0;      // first round of the regime
     int first;     // queue index of its first item
     int size;      // items per round
     int rounds;    // number of rounds
-    int flags;     // 1: anchors, 2: pass 1, 4: pass 2
+    int flags;     // 1: anchors, 2: pass 1
 };
 constexpr int kMaxRegimes = 8;
 
@@ -66,15 +66,16 @@ struct PersistParams {
     SegDev seg;
     const double *tmpl;
     const UnitInfo *units;
-    QueueRegime reg[kMaxRegimes];
+    QueueRegime reg[kMaxRegimes];   // queue 1: anchor chunks and pass-1 tiles in rounds
     int n_reg;
-    int n_items;
-    int LA, D2;
+    int n_items1, n_items2;         // queue 2: pass-2 tiles, unit by unit
+    int n_sm, split;                // CTAs with blockIdx mod n_sm < split start on queue 1
+    int LA;
     int log2D, max_anc, nA, S, SA;
     float4 *anchors;            // SA slots of max_anc records
     float *anchors4;
     float2 *exch;               // S slots of N complex64
-    unsigned *ctl;              // [0] queue head, [1] abort flag (zeroed before launch)
+    unsigned *ctl;              // [0] queue-1 head, [1] abort flag, [2] queue-2 head (zeroed before launch)
     unsigned *doneA, *done1, *done2;   // per-unit completed item counts (zeroed before launch)
     int *status;                // bit 1: a bounded wait expired
     float4 *partials;           // [units][pass-2 tiles]

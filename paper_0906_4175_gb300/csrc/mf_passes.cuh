@@ -81,6 +81,18 @@ cudaError_t dispatch_split(int log2N, Op &op) {
 
 __host__ __device__ inline int log2_n2(int log2N) { return log2N / 2; }
 
+// Deferred release of a work counter by thread 0 (persistent scheduler): the
+// device-scope fence orders the block's writes of the previous item, which
+// thread 0 observed through the block barrier that ended that item, before
+// the increment.  Called right after the next item's loads are issued, so the
+// fence's wait overlaps the load latency thread 0 has to wait for anyway.
+__device__ __forceinline__ void release_hook(unsigned *ctr) {
+    if (ctr != nullptr && threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Column (pass-1) sources.  Sequence seq of CTA blockIdx.x is column
 // k1 = blockIdx.x * C + seq; element n of it is spectrum entry k1 + N1 n.
@@ -154,6 +166,7 @@ struct RowSrc {
     struct Params { const float2 *E; int log2N1; int log2N; };
     const Params &p;
     const int tile, slot;
+    unsigned *rel = nullptr;   // deferred release (persistent scheduler)
     __device__ RowSrc(const Params &pp, int tl, int, int sl, void *) : p(pp), tile(tl), slot(sl) {}
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         const float2 *E = p.E + ((int64_t)slot << p.log2N);
@@ -162,6 +175,7 @@ struct RowSrc {
         constexpr int T = L / 32;
 #pragma unroll
         for (int r = 0; r < 32; ++r) v[r] = __ldcg(&row[t + r * T]);
+        release_hook(rel);
     }
 };
 

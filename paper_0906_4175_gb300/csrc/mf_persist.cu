@@ -1,28 +1,26 @@
 // mf_persist.cu -- persistent bank scheduler (one launch per segment).
 //
-// A grid of resident CTAs takes work items from an ordered queue (one atomic
-// counter; each CTA reserves its next item while it works on the current
-// one).  For unit u (a template on this segment) the items are
-//   A(u, c)   anchors chunk c (FP64 phase anchors, 1024 per chunk)
-//   P1(u, i)  pass-1 tile i: template generation + weighting + column IFFTs
-//   P2(u, i)  pass-2 tile i: row IFFTs + rho epilogue
-// interleaved in rounds r = 0, 1, ...:  A(r + LA), P1(r), P2(r - D2), so that
-// anchor work (FP64), column FFTs and row FFTs of different templates run side
-// by side.  Exchange buffers form a ring of S slots and anchor tables a ring
-// of SA slots.  Every dependency points to an item earlier in the queue and
-// items are handed out in queue order to running CTAs only, so the earliest
-// unfinished item can always run and every wait ends as long as the GPU makes
+// A grid of resident CTAs (two per SM) works through two ordered queues:
+//   queue 1, in rounds r = -LA, ..., U-1:  A(r + LA, c) anchor chunks (FP64
+//            phase anchors, 1024 per chunk) then P1(r, i) pass-1 tiles
+//            (template generation + weighting + column IFFTs);
+//   queue 2: P2(u, i) pass-2 tiles (row IFFTs + rho epilogue), unit by unit.
+// A CTA starts on queue 1 if (blockIdx mod n_sm) < split, else on queue 2, so
+// the two CTAs of an SM usually run the same code; a CTA whose queue is empty
+// moves to the other queue.  Items of a queue are handed out in order (one
+// atomic head per queue) to running CTAs only.  Dependencies:
+//   A(u) needs P1(u - SA) complete (its anchor slot is free),
+//   P1(u) needs A(u) complete and P2(u - S) complete (its exchange slot is free),
+//   P2(u) needs P1(u) complete.
+// Each points to a smaller unit or to an earlier item of the same queue and
+// both queues have CTAs from the start, so every wait ends while the GPU makes
 // progress; each wait is still bounded (spin limit with __nanosleep back-off),
 // after which the kernel raises the abort flag, sets status bit 1
-// (MF_ETIMEOUT) and every CTA returns.  Items are decoded arithmetically from
-// the round structure, and thread 0 reads the next item's dependency counters
-// before the current item's release barrier, so a satisfied dependency costs
-// no memory round trip on the critical path.
-//   P1(u) waits for A(u) complete and for P2(u - S) complete (slot free);
-//   A(u) waits for P1(u - SA) complete (anchor slot free);
-//   P2(u) waits for P1(u) complete.
-// The last P2 tile of a unit reduces the unit's per-tile partial argmaxes into
-// its peak record.
+// (MF_ETIMEOUT) and every CTA returns.  Thread 0 decodes the next item and
+// reads its counters while the current item runs, and releases each finished
+// item during the next one, right after that item's loads are issued, so
+// neither the dependency check nor the release fence sits on the critical
+// path.  Per-unit peaks are reduced afterwards from the per-tile partials.
 #include "mf_filter.cuh"
 
 namespace mf {
@@ -74,9 +72,11 @@ template <int N2, int N1>
 __device__ __forceinline__ void persist_p1(float2 *smem, const float2 *tw, void *scratch,
                                         const typename TemplateSrc<N2, seqs_per_cta<N2>(N1)>::Params &sp,
                                         const typename ExchSink<N2, seqs_per_cta<N2>(N1), +1>::Params &kp, int u,
-                                        int tile, int S, int SA) {
+                                        int tile, int S, int SA, unsigned *&pending) {
     constexpr int C1 = seqs_per_cta<N2>(N1);
     TemplateSrc<N2, C1> src(sp, tile, u, u % SA, scratch);
+    src.rel = pending;
+    pending = nullptr;
     ExchSink<N2, C1, +1> snk(kp, tile, u, u % S);
     cta_fft<N2, C1, true, +1>(smem, tw, src, snk);
 }
@@ -86,9 +86,11 @@ template <int N2, int N1>
 __device__ __forceinline__ void persist_p2(float2 *smem, const float2 *tw,
                                         const typename RowSrc<N1, seqs_per_cta<N1>(N2)>::Params &sp,
                                         const typename RhoSink<N1, seqs_per_cta<N1>(N2)>::Params &kp, int u, int tile,
-                                        int S) {
+                                        int S, unsigned *&pending) {
     constexpr int C2 = seqs_per_cta<N1>(N2);
     RowSrc<N1, C2> src(sp, tile, u, u % S, nullptr);
+    src.rel = pending;
+    pending = nullptr;
     RhoSink<N1, C2> snk(kp, tile, u, 0);
     cta_fft<N1, C2, false, +1>(smem, tw, src, snk);
     snk.finish(smem);
@@ -111,45 +113,12 @@ __device__ __noinline__ void persist_anchors(const PersistParams &P, int u, int 
     }
 }
 
-// The last pass-2 tile of unit u reduces the unit's partial argmaxes (warp 0).
-template <int N2, int N1>
-__device__ __noinline__ void persist_peak(const PersistParams &P, int u) {
-    constexpr int n2 = N2 / seqs_per_cta<N1>(N2);
-    __threadfence();   // the other tiles' partials were released before their increments
-    const int lane = threadIdx.x;
-    float bp = -1.f, bx = 0.f, by = 0.f;
-    int bj = 0x7fffffff;
-    const float4 *pp = P.partials + (int64_t)u * n2;
-    for (int i = lane; i < n2; i += 32) {
-        const float4 c = __ldcg(&pp[i]);
-        const int cj = __float_as_int(c.y);
-        if (c.x > bp || (c.x == bp && cj < bj)) { bp = c.x; bj = cj; bx = c.z; by = c.w; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float op = __shfl_xor_sync(0xffffffffu, bp, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        const float ox = __shfl_xor_sync(0xffffffffu, bx, o);
-        const float oy = __shfl_xor_sync(0xffffffffu, by, o);
-        if (op > bp || (op == bp && oj < bj)) { bp = op; bj = oj; bx = ox; by = oy; }
-    }
-    if (lane == 0) {
-        const UnitInfo ui = P.units[u];
-        mf_peak pk;
-        pk.rho = sqrtf(bp) * ui.rho_scale;
-        pk.j = bj;
-        pk.z_re = bx * ui.z_scale;
-        pk.z_im = by * ui.z_scale;
-        P.peaks[(int64_t)ui.tmpl * P.n_seg + P.seg_idx] = pk;
-    }
-}
-
 struct ItemDesc {
     int u, phase, tile;
 };
 
-__device__ __forceinline__ ItemDesc decode_item(const PersistParams &P, int q, int n1) {
-    ItemDesc d{0, 2, 0};
+__device__ __forceinline__ ItemDesc decode_item(const PersistParams &P, int qid, int q, int n1, int n2) {
+    if (qid == 2) return ItemDesc{q / n2, 2, q % n2};
     for (int i = 0; i < P.n_reg; ++i) {
         const QueueRegime &g = P.reg[i];
         const int end = g.first + g.size * g.rounds;
@@ -162,13 +131,9 @@ __device__ __forceinline__ ItemDesc decode_item(const PersistParams &P, int q, i
             if (pos < P.nA) return ItemDesc{rho + P.LA, kItemA, pos};
             pos -= P.nA;
         }
-        if (g.flags & 2) {
-            if (pos < n1) return ItemDesc{rho, kItemP1, pos};
-            pos -= n1;
-        }
-        return ItemDesc{rho - P.D2, 2, pos};
+        return ItemDesc{rho, kItemP1, pos};
     }
-    return d;
+    return ItemDesc{0, kItemP1, 0};
 }
 
 // Counters (address, target) that must be reached before item d may run.
@@ -192,6 +157,19 @@ __device__ __forceinline__ Deps item_deps(const PersistParams &P, const ItemDesc
     return r;
 }
 
+__device__ __forceinline__ unsigned *item_counter(const PersistParams &P, int phase, int u) {
+    return (phase == kItemA ? P.doneA : (phase == kItemP1 ? P.done1 : P.done2)) + u;
+}
+
+// thread 0: release a deferred counter now (see release_hook)
+__device__ __forceinline__ void flush_release(unsigned *&pending) {
+    if (pending) {
+        __threadfence();
+        atomicAdd(pending, 1u);
+        pending = nullptr;
+    }
+}
+
 template <int N2, int N1>
 __global__ void __launch_bounds__(256, 2)
     k_filter_persistent(PersistParams P, typename TemplateSrc<N2, seqs_per_cta<N2>(N1)>::Params sp1,
@@ -204,113 +182,116 @@ __global__ void __launch_bounds__(256, 2)
     constexpr int n1 = N1 / C1;
     constexpr int n2 = N2 / C2;
     extern __shared__ float2 smem[];
-    unsigned *abort_flag = P.ctl + 1;   // P.ctl[0] is the queue head
+    unsigned *abort_flag = P.ctl + 1;
     constexpr size_t d1 = pass_data_bytes<N2, C1>(), d2 = pass_data_bytes<N1, C2>();
     float2 *tw1 = smem + (d1 > d2 ? d1 : d2) / sizeof(float2);
     float2 *tw2 = tw1 + TwTable<N2>::SIZE;
     void *scratch1 = tw2 + TwTable<N1>::SIZE;
     fill_twiddles<N2>(tw1);
     fill_twiddles<N1>(tw2);
-    unsigned *head = P.ctl;
-    // Item pipeline.  s_desc[par] is the item this block runs now; while it
-    // runs, thread 0 decodes the next item (index qn, reserved one item
-    // earlier) and reads its dependency counters, and reserves the index after
-    // it.  At the end thread 0 publishes the next descriptor, one barrier
-    // follows, and only then does thread 0 release the finished item, so the
-    // other warps start the next item while the release (which waits for this
-    // item's stores) is in flight.  If the counters read ahead do not yet show
-    // the next item's dependencies (rare), the descriptor is published as
-    // "pending": thread 0 releases first (the dependency may be this block's
-    // own item), then waits, then a second barrier publishes the outcome.
+    // Item pipeline (per queue).  s_desc[par] is the item this block runs now;
+    // while it runs, thread 0 decodes the next item (index qn, reserved one
+    // item earlier), reads its counters and reserves the index after it.  At
+    // the end thread 0 publishes the next descriptor and one barrier follows.
+    // If the counters read ahead do not show the next item's dependencies
+    // (rare) it is published as pending (state 2): thread 0 then releases its
+    // deferred counter (the dependency may be this block's own item), waits,
+    // and a second barrier publishes the outcome.
     __shared__ int4 s_desc[2];   // {unit, phase, tile, state}: state 0 stop, 1 run, 2 pending
     __shared__ int4 s_nd;        // thread 0's decoded next item
     __shared__ Deps s_dep;       // and its dependencies
     __shared__ int s_next_ok;
-    int qn = 0;
-    if (threadIdx.x == 0) {
-        const int q0 = (int)atomicAdd(head, 1u);
-        int4 d = make_int4(0, 0, 0, 0);
-        if (q0 < P.n_items) {
-            const ItemDesc it0 = decode_item(P, q0, n1);
-            const Deps dp = item_deps(P, it0, n1, n2);
-            bool ok = true;
-            if (dp.c0) ok = wait_geq(dp.c0, dp.t0, abort_flag, P.status, P.spin_limit);
-            if (ok && dp.c1) ok = wait_geq(dp.c1, dp.t1, abort_flag, P.status, P.spin_limit);
-            d = make_int4(it0.u, it0.phase, it0.tile, ok ? 1 : 0);
-        }
-        s_desc[0] = d;
-        qn = (int)atomicAdd(head, 1u);
-    }
-    __syncthreads();
-    int par = 0;
-    for (;;) {
-        const int4 d = s_desc[par];
-        if (d.w == 0) break;
-        const int u = d.x, phase = d.y, tile = d.z;
-        // look-ahead (thread 0): decode the next item into shared memory, read
-        // its counters (the values stay in registers), reserve the index after it
-        unsigned nv0 = 0u, nv1 = 0u, nab = 0u;
-        int qn2 = 0;
+    unsigned *pending = nullptr;   // thread 0: finished item whose counter is not yet released
+    bool aborted = false;
+    const int role = ((int)(blockIdx.x % (unsigned)P.n_sm) < P.split) ? 1 : 2;
+    for (int pass = 0; pass < 2 && !aborted; ++pass) {
+        const int qid = pass == 0 ? role : 3 - role;
+        unsigned *head = qid == 1 ? P.ctl : P.ctl + 2;
+        const int nq = qid == 1 ? P.n_items1 : P.n_items2;
+        int qn = 0;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            s_next_ok = qn < P.n_items;
-            if (s_next_ok) {
-                const ItemDesc nd = decode_item(P, qn, n1);
-                const Deps dp = item_deps(P, nd, n1, n2);
-                s_nd = make_int4(nd.u, nd.phase, nd.tile, 0);
-                s_dep = dp;
-                nv0 = dp.c0 ? ld_acquire(dp.c0) : 0u;
-                nv1 = dp.c1 ? ld_acquire(dp.c1) : 0u;
-            }
-            nab = *(volatile unsigned *)abort_flag;
-            qn2 = (int)atomicAdd(head, 1u);
-        }
-        unsigned *done_ctr;
-        if (phase == kItemA) {
-            persist_anchors(P, u, tile);
-            done_ctr = P.doneA + u;
-        } else if (phase == kItemP1) {
-            persist_p1<N2, N1>(smem, tw1, scratch1, sp1, kp1, u, tile, P.S, P.SA);
-            done_ctr = P.done1 + u;
-        } else {
-            persist_p2<N2, N1>(smem, tw2, sp2, kp2, u, tile, P.S);
-            done_ctr = P.done2 + u;
-        }
-        if (threadIdx.x == 0) {
-            int4 e = make_int4(0, 0, 0, 0);
-            if (s_next_ok && !nab) {
-                const Deps dp = s_dep;
-                const bool sat = (!dp.c0 || nv0 >= dp.t0) && (!dp.c1 || nv1 >= dp.t1);
-                e = s_nd;
-                e.w = sat ? 1 : 2;
-                if (P.stats) {
-                    atomicAdd(P.stats + 4 * e.y + 2, 1ull);
-                    if (!sat) atomicAdd(P.stats + 4 * e.y + 3, 1ull);
-                }
-            }
-            s_desc[par ^ 1] = e;
-            qn = qn2;
-        }
-        __syncthreads();   // publishes the next descriptor; this item's writes are issued
-        unsigned old = 0u;
-        if (threadIdx.x == 0) old = add_release(done_ctr, 1u);
-        if (phase != kItemA && phase != kItemP1 && threadIdx.x < 32) {
-            old = __shfl_sync(0xffffffffu, old, 0);
-            if (old == (unsigned)(n2 - 1)) persist_peak<N2, N1>(P, u);
-        }
-        par ^= 1;
-        if (s_desc[par].w == 2) {
-            if (threadIdx.x == 0) {
-                const long long t0 = clock64();
-                const Deps dp = s_dep;
+            const int q0 = (int)atomicAdd(head, 1u);
+            int4 d = make_int4(0, 0, 0, 0);
+            if (q0 < nq && !*(volatile unsigned *)abort_flag) {
+                const ItemDesc it0 = decode_item(P, qid, q0, n1, n2);
+                const Deps dp = item_deps(P, it0, n1, n2);
+                flush_release(pending);
                 bool ok = true;
-                if (dp.c0 && nv0 < dp.t0) ok = wait_geq(dp.c0, dp.t0, abort_flag, P.status, P.spin_limit);
-                if (ok && dp.c1 && nv1 < dp.t1) ok = wait_geq(dp.c1, dp.t1, abort_flag, P.status, P.spin_limit);
-                if (P.stats) atomicAdd(P.stats + 4 * s_desc[par].y + 1, (unsigned long long)(clock64() - t0));
-                s_desc[par].w = ok ? 1 : 0;
+                if (dp.c0) ok = wait_geq(dp.c0, dp.t0, abort_flag, P.status, P.spin_limit);
+                if (ok && dp.c1) ok = wait_geq(dp.c1, dp.t1, abort_flag, P.status, P.spin_limit);
+                d = make_int4(it0.u, it0.phase, it0.tile, ok ? 1 : 0);
             }
-            __syncthreads();
+            s_desc[0] = d;
+            qn = (int)atomicAdd(head, 1u);
+        }
+        __syncthreads();
+        int par = 0;
+        for (;;) {
+            const int4 d = s_desc[par];
+            if (d.w == 0) {
+                aborted = *(volatile unsigned *)abort_flag != 0u;
+                break;
+            }
+            const int u = d.x, phase = d.y, tile = d.z;
+            // look-ahead (thread 0)
+            unsigned nv0 = 0u, nv1 = 0u, nab = 0u;
+            int qn2 = 0;
+            if (threadIdx.x == 0) {
+                s_next_ok = qn < nq;
+                if (s_next_ok) {
+                    const ItemDesc nd = decode_item(P, qid, qn, n1, n2);
+                    const Deps dp = item_deps(P, nd, n1, n2);
+                    s_nd = make_int4(nd.u, nd.phase, nd.tile, 0);
+                    s_dep = dp;
+                    nv0 = dp.c0 ? ld_acquire(dp.c0) : 0u;
+                    nv1 = dp.c1 ? ld_acquire(dp.c1) : 0u;
+                }
+                nab = *(volatile unsigned *)abort_flag;
+                qn2 = (int)atomicAdd(head, 1u);
+            }
+            if (phase == kItemA) {
+                if (threadIdx.x == 0) flush_release(pending);
+                persist_anchors(P, u, tile);
+            } else if (phase == kItemP1) {
+                persist_p1<N2, N1>(smem, tw1, scratch1, sp1, kp1, u, tile, P.S, P.SA, pending);
+            } else {
+                persist_p2<N2, N1>(smem, tw2, sp2, kp2, u, tile, P.S, pending);
+            }
+            if (threadIdx.x == 0) {
+                pending = item_counter(P, phase, u);   // released during the next item
+                int4 e = make_int4(0, 0, 0, 0);
+                if (s_next_ok && !nab) {
+                    const Deps dp = s_dep;
+                    const bool sat = (!dp.c0 || nv0 >= dp.t0) && (!dp.c1 || nv1 >= dp.t1);
+                    e = s_nd;
+                    e.w = sat ? 1 : 2;
+                    if (P.stats) {
+                        atomicAdd(P.stats + 4 * e.y + 2, 1ull);
+                        if (!sat) atomicAdd(P.stats + 4 * e.y + 3, 1ull);
+                    }
+                }
+                s_desc[par ^ 1] = e;
+                qn = qn2;
+            }
+            __syncthreads();   // publishes the next descriptor; this item's writes are issued
+            par ^= 1;
+            if (s_desc[par].w == 2) {
+                if (threadIdx.x == 0) {
+                    const long long t0 = clock64();
+                    flush_release(pending);
+                    const Deps dp = s_dep;
+                    bool ok = true;
+                    if (dp.c0 && nv0 < dp.t0) ok = wait_geq(dp.c0, dp.t0, abort_flag, P.status, P.spin_limit);
+                    if (ok && dp.c1 && nv1 < dp.t1) ok = wait_geq(dp.c1, dp.t1, abort_flag, P.status, P.spin_limit);
+                    if (P.stats) atomicAdd(P.stats + 4 * s_desc[par].y + 1, (unsigned long long)(clock64() - t0));
+                    s_desc[par].w = ok ? 1 : 0;
+                }
+                __syncthreads();
+            }
         }
     }
+    if (threadIdx.x == 0) flush_release(pending);
     (void)C2;
 }
 

@@ -335,3 +335,25 @@ def test_bounded_wait_timeout_reports_and_recovers(mf):
     got = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)[0])
     assert bank.check() == 0
     assert np.array_equal(ref.view(np.uint8), got.view(np.uint8))
+
+
+def test_autotune_keeps_results(mf, tmp_path):
+    """mf_autotune only changes the schedule: results stay bit-identical and
+    the choice is written to the cache file."""
+    import json
+    import torch
+    wl = workloads.small(seed=14, N=1 << 15, fs=4096.0, n_templates=9, m_lo=1.1, m_hi=6.0)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)]
+    cache = tmp_path / "tune.json"
+    mf.autotune(bank, [seg], 4.0, repeats=1, cache_path=str(cache))
+    rec = json.loads(cache.read_text())
+    assert rec["scheduler"] in ("persistent", "batch") and rec["templates"] == 9
+    b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)]
+    n = int(a[2][0])
+    assert int(b[2][0]) == n
+    assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8))
+    assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
