@@ -97,14 +97,14 @@ struct Pass1Op {
     template <int N2, int N1>
     cudaError_t run() {
         constexpr int C = seqs_per_cta<N2>(N1);
-        typename ExchSink<N2, C, +1>::Params kp{exch, seg.log2N1, seg.log2N};
+        typename ExchSink<N2, C, +1, cx_ilog2(N1)>::Params kp{exch, seg.log2N1, seg.log2N};
         const dim3 grid(N1 / C, n_units);
         if (phase_mode == MF_PHASE_FP32) {
-            typename TemplateSrcF32<N2, C>::Params sp{seg.W, units, tmpl, seg.log2N1, (float)seg.df};
-            return run_pass<N2, C, true, +1, TemplateSrcF32<N2, C>, ExchSink<N2, C, +1>>(grid, sp, kp, st, unit0);
+            typename TemplateSrcF32<N2, C, cx_ilog2(N1)>::Params sp{seg.W, units, tmpl, (float)seg.df};
+            return run_pass<N2, C, true, +1, TemplateSrcF32<N2, C, cx_ilog2(N1)>, ExchSink<N2, C, +1, cx_ilog2(N1)>>(grid, sp, kp, st, unit0);
         }
-        typename TemplateSrc<N2, C>::Params sp{seg.W, units, anchors, anchors4, max_anc, seg.log2N1, log2D};
-        return run_pass<N2, C, true, +1, TemplateSrc<N2, C>, ExchSink<N2, C, +1>>(grid, sp, kp, st, unit0);
+        typename TemplateSrc<N2, C, cx_ilog2(N1)>::Params sp{seg.W, units, anchors, anchors4, max_anc, log2D};
+        return run_pass<N2, C, true, +1, TemplateSrc<N2, C, cx_ilog2(N1)>, ExchSink<N2, C, +1, cx_ilog2(N1)>>(grid, sp, kp, st, unit0);
     }
 };
 
@@ -147,8 +147,8 @@ struct AttrOp {
         constexpr int C1 = seqs_per_cta<N2>(N1);
         constexpr int C2 = seqs_per_cta<N1>(N2);
         cudaError_t e;
-        if ((e = set_pass_attrs<N2, C1, true, +1, TemplateSrc<N2, C1>, ExchSink<N2, C1, +1>>())) return e;
-        if ((e = set_pass_attrs<N2, C1, true, +1, TemplateSrcF32<N2, C1>, ExchSink<N2, C1, +1>>())) return e;
+        if ((e = set_pass_attrs<N2, C1, true, +1, TemplateSrc<N2, C1, cx_ilog2(N1)>, ExchSink<N2, C1, +1, cx_ilog2(N1)>>())) return e;
+        if ((e = set_pass_attrs<N2, C1, true, +1, TemplateSrcF32<N2, C1, cx_ilog2(N1)>, ExchSink<N2, C1, +1, cx_ilog2(N1)>>())) return e;
         return set_pass_attrs<N1, C2, false, +1, RowSrc<N1, C2>, RhoSink<N1, C2>>();
     }
 };

@@ -44,7 +44,7 @@ __device__ __forceinline__ void anchor_record(double c1, double c2, double c3, d
 // pass-1 source: X_k = W_k e^{-i Psi_k} on the band, 0 elsewhere; k >= N/2 is
 // always outside (one-sided spectrum), so the upper half of every column is 0.
 // ---------------------------------------------------------------------------
-template <int L, int C>
+template <int L, int C, int LG1>
 struct TemplateSrc {
     static constexpr bool kHalfZero = true;
     // one anchor record (float4 + float) per non-zero column row, staged per tile
@@ -54,7 +54,7 @@ struct TemplateSrc {
         const UnitInfo *units;
         const float4 *anchors;
         const float *anchors4;
-        int anc_stride, log2N1, log2D;
+        int anc_stride, log2D;
     };
     const Params &p;
     const int tile, unit, slot;
@@ -73,17 +73,18 @@ struct TemplateSrc {
         const int D = 1 << p.log2D;
         float2 w[16];
         bool in[16];
+        const int k0 = k1 + (t << LG1);
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            const int k = k1 + ((t + r * T) << p.log2N1);
+            const int k = k0 + ((r * T) << LG1);
             in[r] = (k >= u.k_lo) && (k < u.k_hi);
             w[r] = __ldg(&p.W[in[r] ? k : u.k_lo]);
         }
-        if (D >= C && p.log2D <= p.log2N1) {
+        if (D >= C && p.log2D <= LG1) {
             // Every column of this tile falls in the same anchor group on a
             // given row n, so the tile needs one anchor per row:
             // g(n) = (tile C >> log2D) + n (N1 >> log2D), staged once in shared memory.
-            const int gstep = 1 << (p.log2N1 - p.log2D);
+            const int gstep = 1 << (LG1 - p.log2D);
             const int gbase = ((tile * C) >> p.log2D) - u.g_lo;
             for (int n = threadIdx.x; n < L / 2; n += blockDim.x) {
                 const int a = gbase + n * gstep;
@@ -118,7 +119,7 @@ struct TemplateSrc {
             const int half = D >> 1;
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
-                const int k = k1 + ((t + r * T) << p.log2N1);
+                const int k = k0 + ((r * T) << LG1);
                 const int kk = in[r] ? k : u.k_lo;
                 const int g = kk >> p.log2D;
                 const float4 a = __ldcg(&anc[g]);
@@ -136,14 +137,13 @@ struct TemplateSrc {
 };
 
 // FP32-only phase (precision-sweep reference): psi evaluated directly in FP32.
-template <int L, int C>
+template <int L, int C, int LG1>
 struct TemplateSrcF32 {
     static constexpr bool kHalfZero = true;
     struct Params {
         const float2 *W;
         const UnitInfo *units;
         const double *tmpl;
-        int log2N1;
         float df;
     };
     static constexpr size_t kScratchBytes = 0;
@@ -158,7 +158,7 @@ struct TemplateSrcF32 {
         const int k1 = tile * C + seq;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            const int k = k1 + ((t + r * T) << p.log2N1);
+            const int k = k1 + ((t + r * T) << LG1);
             const bool in = (k >= u.k_lo) && (k < u.k_hi);
             const int kk = in ? k : u.k_lo;
             const float2 w = __ldg(&p.W[kk]);

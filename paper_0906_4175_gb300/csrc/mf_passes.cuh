@@ -97,8 +97,8 @@ __device__ __forceinline__ void release_hook(unsigned *ctr) {
 // Column (pass-1) sources.  Sequence seq of CTA blockIdx.x is column
 // k1 = blockIdx.x * C + seq; element n of it is spectrum entry k1 + N1 n.
 // ---------------------------------------------------------------------------
-template <int L, int C, bool HALF_ZERO>
-struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO
+template <int L, int C, bool HALF_ZERO, int LG1>
+struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO; LG1 = log2 N1
     static constexpr bool kHalfZero = HALF_ZERO;
     static constexpr size_t kScratchBytes = 0;
     struct Params { const float2 *X; int log2N1; int64_t batch_stride; };
@@ -110,12 +110,13 @@ struct ColComplexSrc {      // X[k], zero for k >= N/2 when HALF_ZERO
         const int k1 = tile * C + seq;
         constexpr int T = L / 32;
         constexpr int NR = HALF_ZERO ? 16 : 32;
+        const float2 *col = X + k1 + ((int64_t)t << LG1);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = X[k1 + ((t + r * T) << p.log2N1)];
+        for (int r = 0; r < NR; ++r) v[r] = col[(int64_t)r * T << LG1];
     }
 };
 
-template <int L, int C>
+template <int L, int C, int LG1>
 struct ColRealSrc {         // real samples s[n] (imaginary part zero)
     static constexpr bool kHalfZero = false;
     static constexpr size_t kScratchBytes = 0;
@@ -127,13 +128,13 @@ struct ColRealSrc {         // real samples s[n] (imaginary part zero)
         const int k1 = tile * C + seq;
         constexpr int T = L / 32;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] = make_float2(p.s[k1 + ((t + r * T) << p.log2N1)], 0.f);
+        for (int r = 0; r < 32; ++r) v[r] = make_float2(p.s[k1 + ((t + r * T) << LG1)], 0.f);
     }
 };
 
 // Column sink: multiply by the four-step twiddle exp(SIGN 2 pi i j2 k1 / N)
 // and write E[j2 * N1 + k1] (batch blockIdx.y at E + blockIdx.y * N).
-template <int L, int C, int SIGN>
+template <int L, int C, int SIGN, int LG1>
 struct ExchSink {
     struct Params { float2 *E; int log2N1; int log2N; };
     const Params &p;
@@ -141,14 +142,13 @@ struct ExchSink {
     __device__ ExchSink(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
     template <int R>
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
-        float2 *E = p.E + ((int64_t)slot << p.log2N);
         const int k1 = tile * C + seq;
+        float2 *E = p.E + ((int64_t)slot << p.log2N) + ((int64_t)b << LG1) + k1;   // row j2 = b
         float2 w = unit_root<SIGN>((uint32_t)(b * k1), p.log2N);
         const float2 step = unit_root<SIGN>((uint32_t)(stride * k1), p.log2N);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int j2 = b + r * stride;
-            __stcg(&E[((int64_t)j2 << p.log2N1) + k1], cmul(v[r], w));
+            __stcg(&E[((int64_t)r * stride) << LG1], cmul(v[r], w));   // row j2 = b + r stride
             if (r + 1 < R) w = cmul(w, step);
         }
     }

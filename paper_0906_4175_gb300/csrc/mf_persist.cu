@@ -70,14 +70,14 @@ __device__ __forceinline__ void block_signal(unsigned *ctr) {
 // One pass-1 tile: template generation + weighting + column IFFTs -> exchange slot u % S.
 template <int N2, int N1>
 __device__ __forceinline__ void persist_p1(float2 *smem, const float2 *tw, void *scratch,
-                                        const typename TemplateSrc<N2, seqs_per_cta<N2>(N1)>::Params &sp,
-                                        const typename ExchSink<N2, seqs_per_cta<N2>(N1), +1>::Params &kp, int u,
+                                        const typename TemplateSrc<N2, seqs_per_cta<N2>(N1), cx_ilog2(N1)>::Params &sp,
+                                        const typename ExchSink<N2, seqs_per_cta<N2>(N1), +1, cx_ilog2(N1)>::Params &kp, int u,
                                         int tile, int S, int SA, unsigned *&pending) {
     constexpr int C1 = seqs_per_cta<N2>(N1);
-    TemplateSrc<N2, C1> src(sp, tile, u, u % SA, scratch);
+    TemplateSrc<N2, C1, cx_ilog2(N1)> src(sp, tile, u, u % SA, scratch);
     src.rel = pending;
     pending = nullptr;
-    ExchSink<N2, C1, +1> snk(kp, tile, u, u % S);
+    ExchSink<N2, C1, +1, cx_ilog2(N1)> snk(kp, tile, u, u % S);
     cta_fft<N2, C1, true, +1>(smem, tw, src, snk);
 }
 
@@ -172,8 +172,8 @@ __device__ __forceinline__ void flush_release(unsigned *&pending) {
 
 template <int N2, int N1>
 __global__ void __launch_bounds__(256, 2)
-    k_filter_persistent(PersistParams P, typename TemplateSrc<N2, seqs_per_cta<N2>(N1)>::Params sp1,
-                        typename ExchSink<N2, seqs_per_cta<N2>(N1), +1>::Params kp1,
+    k_filter_persistent(PersistParams P, typename TemplateSrc<N2, seqs_per_cta<N2>(N1), cx_ilog2(N1)>::Params sp1,
+                        typename ExchSink<N2, seqs_per_cta<N2>(N1), +1, cx_ilog2(N1)>::Params kp1,
                         typename RowSrc<N1, seqs_per_cta<N1>(N2)>::Params sp2,
                         typename RhoSink<N1, seqs_per_cta<N1>(N2)>::Params kp2) {
     constexpr int C1 = seqs_per_cta<N2>(N1);
@@ -301,7 +301,7 @@ size_t persist_smem() {
     constexpr int C2 = seqs_per_cta<N1>(N2);
     const size_t a = pass_data_bytes<N2, C1>(), b = pass_data_bytes<N1, C2>();
     return (a > b ? a : b) + sizeof(float2) * (TwTable<N2>::SIZE + TwTable<N1>::SIZE) +
-           TemplateSrc<N2, C1>::kScratchBytes;
+           TemplateSrc<N2, C1, cx_ilog2(N1)>::kScratchBytes;
 }
 
 namespace {
@@ -316,9 +316,9 @@ struct PersistOp {
         } else {
             constexpr int C1 = seqs_per_cta<N2>(N1);
             constexpr int C2 = seqs_per_cta<N1>(N2);
-            typename TemplateSrc<N2, C1>::Params sp1{P.seg.W, P.units, P.anchors, P.anchors4, P.max_anc,
-                                                     P.seg.log2N1, P.log2D};
-            typename ExchSink<N2, C1, +1>::Params kp1{P.exch, P.seg.log2N1, P.seg.log2N};
+            typename TemplateSrc<N2, C1, cx_ilog2(N1)>::Params sp1{P.seg.W, P.units, P.anchors, P.anchors4, P.max_anc,
+                                                                   P.log2D};
+            typename ExchSink<N2, C1, +1, cx_ilog2(N1)>::Params kp1{P.exch, P.seg.log2N1, P.seg.log2N};
             typename RowSrc<N1, C2>::Params sp2{P.exch, P.seg.log2N1, P.seg.log2N};
             typename RhoSink<N1, C2>::Params kp2{P.units, P.partials, P.staged, P.keys, P.counter, P.cap,
                                                  P.seg.log2N2, N2 / C2, P.seg_idx, P.kl};

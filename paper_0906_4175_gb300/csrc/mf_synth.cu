@@ -81,9 +81,9 @@ struct InvRealOp {
         constexpr int C1 = seqs_per_cta<N2>(N1);
         constexpr int C2 = seqs_per_cta<N1>(N2);
         const int log2N2 = log2_n2(log2N), log2N1 = log2N - log2N2;
-        typename ColComplexSrc<N2, C1, true>::Params sp{Y, log2N1, 0};
-        typename ExchSink<N2, C1, +1>::Params kp{exch, log2N1, log2N};
-        cudaError_t e = run_pass<N2, C1, true, +1, ColComplexSrc<N2, C1, true>, ExchSink<N2, C1, +1>>(
+        typename ColComplexSrc<N2, C1, true, cx_ilog2(N1)>::Params sp{Y, log2N1, 0};
+        typename ExchSink<N2, C1, +1, cx_ilog2(N1)>::Params kp{exch, log2N1, log2N};
+        cudaError_t e = run_pass<N2, C1, true, +1, ColComplexSrc<N2, C1, true, cx_ilog2(N1)>, ExchSink<N2, C1, +1, cx_ilog2(N1)>>(
             dim3(N1 / C1, 1), sp, kp, st);
         if (e != cudaSuccess) return e;
         typename RowSrc<N1, C2>::Params sp2{exch, log2N1, log2N};
@@ -96,7 +96,7 @@ struct InvAttrOp {
     cudaError_t run() {
         constexpr int C1 = seqs_per_cta<N2>(N1);
         constexpr int C2 = seqs_per_cta<N1>(N2);
-        cudaError_t e = set_pass_attrs<N2, C1, true, +1, ColComplexSrc<N2, C1, true>, ExchSink<N2, C1, +1>>();
+        cudaError_t e = set_pass_attrs<N2, C1, true, +1, ColComplexSrc<N2, C1, true, cx_ilog2(N1)>, ExchSink<N2, C1, +1, cx_ilog2(N1)>>();
         if (e != cudaSuccess) return e;
         return set_pass_attrs<N1, C2, false, +1, RowSrc<N1, C2>, RowRealOut<N1, C2>>();
     }
