@@ -4,9 +4,12 @@
 A step is one pass of the hot path over the 1024-template, N = 2^20 workload
 (32x32 mass lattice over [1, 3] Msun, fs = 4096 Hz, 256 s of seeded coloured
 Gaussian noise with 8 injections, threshold rho = 6): segment conditioning
-(mf_segment_upload) plus the bank filter (mf_filter_bank).  Inputs are resident
-in HBM when timing starts; L2 is flushed (256 MiB write) before every timed
-step; each step is timed with CUDA events on the launching stream.
+(mf_segment_refresh of the resident samples) plus the bank filter
+(mf_filter_bank), captured once as a CUDA graph and replayed per step
+(--eager times the plain calls).  Inputs are resident in HBM when timing
+starts; L2 is flushed (256 MiB write) before every timed step; each step is
+timed with CUDA events on the launching stream.  The per-stage shares and the
+roofline come from the same number of eager steps with per-stage events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mfgb|reference]
 
@@ -42,7 +45,7 @@ KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mfgb", choices=["mfgb", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle baseline")
@@ -51,6 +54,7 @@ def _args():
     ap.add_argument("--templates", type=int, default=0,
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
+    ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
     return ap.parse_args()
 
 
@@ -94,8 +98,10 @@ def _ncu_traffic(kernel_stage: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; start()
+    waits for the first sample, and only samples taken between mark_begin()
+    and mark_end() (host wall clock) are kept."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -103,18 +109,39 @@ class ClockSampler:
         self.path = tempfile.mktemp(prefix="mfgb_clocks_", suffix=".csv")
         self.proc = None
         self.gpu = gpu_index
+        self.t0 = self.t1 = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 10.0
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         if self.proc is None:
             return out
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -127,6 +154,9 @@ class ClockSampler:
             for line in fh:
                 p = [x.strip() for x in line.split(",")]
                 if len(p) < 9:
+                    continue
+                ts = self._stamp(p[0])
+                if ts is not None and self.t0 is not None and not (self.t0 - 0.1 <= ts <= self.t1 + 0.1):
                     continue
                 try:
                     sm.append(float(p[1]))
@@ -252,18 +282,18 @@ def main():
             torch.empty((cap, 6), dtype=torch.float32, device=dev),
             torch.zeros(1, dtype=torch.int64, device=dev))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    segs = []
+    # one segment handle: every step re-conditions the resident samples into it
+    seg = mf.Segment(s_dev, spec.fs)
+    seg.refresh(s_dev)
 
     def step():
-        seg = mf.Segment(s_dev, spec.fs)
+        seg.refresh(s_dev)
         mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
-        segs.append(seg)   # keep alive until the stream has drained
 
     schedule = {"scheduler": "default"}
     if not args.no_autotune:
-        seg0 = mf.Segment(s_dev, spec.fs)
         cache = os.path.join(tempfile.gettempdir(), "mfgb_autotune_%d.json" % rank)
-        mf.autotune(bank, [seg0], wl.threshold, repeats=2, cache_path=cache)
+        mf.autotune(bank, [seg], wl.threshold, repeats=2, cache_path=cache)
         with open(cache) as fh:
             schedule = json.load(fh)
         os.unlink(cache)
@@ -272,31 +302,59 @@ def main():
         step()
     torch.cuda.synchronize()
     assert bank.check() == 0
-    segs.clear()
     n_trig = int(outb[2].item())
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    graph = None
+    launches_per_step = None
+    if not args.eager:
+        # one CUDA graph per step: refresh + filter, replayed on the current stream
+        l0 = mf.launch_count()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        launches_per_step = mf.launch_count() - l0
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        assert bank.check() == 0
+        assert int(outb[2].item()) == n_trig
+
+    def timed(run, profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            bank.profile(True)
+        l0 = mf.launch_count()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            run()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        w = time.perf_counter() - w0
+        n_l = mf.launch_count() - l0
+        pr = None
+        if profile:
+            pr = bank.profile_read()
+            bank.profile(False)
+        return sum(a.elapsed_time(b) for a, b in ev), w, n_l, pr
+
     sampler = ClockSampler(local)
-    bank.profile(True)
-    l0 = mf.launch_count()
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    launches = mf.launch_count() - l0
+    sampler.mark_begin()
+    # eager steps with per-stage CUDA events: the stage shares and the roofline
+    eager_ms, eager_wall, eager_launches, prof = timed(step, True)
+    if graph is not None:
+        tot_ms, wall, _, _ = timed(graph.replay, False)
+        launches = launches_per_step * args.steps
+    else:
+        tot_ms, wall, launches = eager_ms, eager_wall, eager_launches
+    sampler.mark_end()
     clocks = sampler.stop()
-    prof = bank.profile_read()
-    bank.profile(False)
-    segs.clear()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
+    assert bank.check() == 0
     if dist:
         t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -314,6 +372,7 @@ def main():
     tmpl_per_launch = wl.n_templates * args.steps / max(1, d_n) if dom in ("pass1", "pass2", "anchors", "fused") else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "timed_on": "the eager steps (same workload, per-stage CUDA events on the launching stream)",
             "algorithmic_bytes_per_launch": d_bytes / max(1, d_n), "launches": d_n,
             "avg_launch_ms": d_ms / max(1, d_n), "templates_per_launch": tmpl_per_launch,
             "stage_share": {k: v[0] / sum(x[0] for x in stages.values()) for k, v in stages.items()}}
@@ -333,7 +392,7 @@ def main():
     for k in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        seg = mf.Segment(s_host.numpy(), spec.fs)
+        seg.refresh(s_host.numpy())     # H2D of the step's samples (pinned) + conditioning
         mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
         peaks_h.copy_(outb[0], non_blocking=True)
         ntr_h.copy_(outb[2], non_blocking=True)
@@ -342,7 +401,6 @@ def main():
         trig_h[:n].copy_(outb[1][:n], non_blocking=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        seg.close()
         if k >= 2:
             e2e_ms.append(dt * 1e3)
             d2h.append(peaks_h.numel() * 4 + 8 + n * 24)
@@ -353,7 +411,7 @@ def main():
         e2e_tot = float(t.item())
     e2e = {"value": world * wl.n_templates * len(e2e_ms) / (e2e_tot / 1e3) if e2e_ms else None, "unit": UNIT,
            "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)) if d2h else 0,
-           "includes": "host s -> mf_segment_upload (H2D inside), mf_filter_bank, D2H peaks + n_trig + triggers"}
+           "includes": "pinned host s -> mf_segment_refresh (H2D inside), mf_filter_bank, D2H peaks + n_trig + triggers"}
 
     cpu = None
     acc = None
@@ -382,6 +440,10 @@ def main():
                     "measure": "|rho_gpu - rho_fp64| / max(rho_fp64, 1)"}
         cpu, acc = cpu_baseline(wl, args.cpu_seconds, gpu_check)
 
+    launch_mode = {"mode": "eager" if graph is None else "cuda_graph",
+                   "eager_ms_per_step": eager_ms / args.steps,
+                   "graph_ms_per_step": tot_ms / args.steps if graph is not None else None,
+                   "launches_per_step": launches / args.steps}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -389,7 +451,9 @@ def main():
             "config": {"workload": WORKLOAD, "templates": wl.n_templates, "N": spec.N, "fs": spec.fs,
                        "segments": 1, "threshold": wl.threshold, "n_trig_per_step": n_trig,
                        "l2": "flushed before every timed step (256 MiB write)",
-                       "step": "mf_segment_upload (device s) + mf_filter_bank",
+                       "step": "mf_segment_refresh (device s) + mf_filter_bank, one CUDA-graph replay"
+                               if graph is not None else "mf_segment_refresh (device s) + mf_filter_bank",
+                       "launch": launch_mode,
                        "schedule": schedule,
                        "phase": "FP64 anchors + FP32 Taylor; FFT FP32"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "path_roofline": path,

@@ -116,6 +116,21 @@ int mf_segment_upload(const float *s, int64_t N, double fs, const double *psd,
                       double psd_f0, double psd_S0, int s_on_device, void *cuda_stream,
                       mf_segment *out);
 int mf_segment_destroy(mf_segment seg);
+
+/* mf_segment_refresh -- conditions new samples s (N float32, the segment's N,
+ * fs and PSD; device if s_on_device, else host) into the existing segment, as
+ * mf_segment_upload would, reusing its device memory: a search that walks
+ * consecutive segments of one length keeps one handle per stream.  The first
+ * call allocates the conditioning scratch (about 20 N bytes) that the segment
+ * then keeps; later calls with device samples allocate nothing and queue only
+ * kernels on cuda_stream, so they may be captured in a CUDA graph together
+ * with mf_filter_bank (the first call must precede the capture).  Work already
+ * queued that reads the segment must be ordered before this call (same stream
+ * or an event).  Host samples are copied and the stream synchronised before
+ * return; they cannot be refreshed inside a capture.
+ * Errors: MF_EINVAL (NULL, wrong device, first call or host samples inside a
+ * capture), MF_ENOMEM, MF_ECUDA. */
+int mf_segment_refresh(mf_segment seg, const float *s, int s_on_device, void *cuda_stream);
 /* Segment length and sample rate (host outs; either may be NULL). */
 int mf_segment_info(mf_segment seg, int64_t *N, double *fs);
 
@@ -130,8 +145,13 @@ int mf_segment_info(mf_segment seg, int64_t *N, double *fs);
  * cuda_stream and returns; mf_bank_check() reports overflow and device-side
  * timeouts of the last call on this bank.
  * The first call for a given (segment length, bank size, trig_cap) allocates
- * the bank's workspace; later calls allocate nothing.
- * Errors: MF_EINVAL (f_low >= f_cut for some pair, bad sizes), MF_ENOMEM, MF_ECUDA. */
+ * the bank's workspace; later calls allocate nothing and queue only kernels
+ * and memsets, so a call may be captured in a CUDA graph once an identical
+ * call has run outside the capture (the graph keeps the segment, output and
+ * workspace pointers; replays recompute from the segments' current contents).
+ * Errors: MF_EINVAL (f_low >= f_cut for some pair, bad sizes, a workspace that
+ * would have to grow or stage profiling switched on inside a stream capture),
+ * MF_ENOMEM, MF_ECUDA. */
 int mf_filter_bank(mf_bank bank, const mf_segment *segs, int n_seg, float threshold,
                    mf_peak *peaks, mf_trigger *trig, int64_t trig_cap, int64_t *n_trig,
                    void *cuda_stream);

@@ -15,7 +15,7 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (INJ_DTYPE, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
+from ._native import (INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
                       MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
 
 __all__ = ["Bank", "Segment", "filter_bank", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
@@ -133,6 +133,25 @@ class Segment:
     @property
     def handle(self):
         return self._h
+
+    def refresh(self, s, stream=None):
+        """mf_segment_refresh: condition new samples (same N, fs and PSD) into
+        this segment's device memory; capturable in a CUDA graph for device s
+        after the first call."""
+        torch = _torch()
+        on_dev = isinstance(s, torch.Tensor) and s.is_cuda
+        if on_dev:
+            if s.dtype != torch.float32 or not s.is_contiguous() or s.numel() != self.N:
+                raise ValueError("device s must be a contiguous float32 tensor of N samples")
+            ptr, keep = s.data_ptr(), s
+        else:
+            keep = np.ascontiguousarray(s, dtype=np.float32)
+            if keep.size != self.N:
+                raise ValueError("s must hold N samples")
+            ptr = keep.ctypes.data
+        check(_native.lib().mf_segment_refresh(self._h, ptr, 1 if on_dev else 0, _stream_ptr(stream)))
+        self._keep = keep
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -35,6 +35,7 @@ SIGNATURES = {
     "mf_bank_size": (_I, [_P, _P]),
     "mf_segment_upload": (_I, [_P, _I64, _D, _P, _D, _D, _I, _P, _P]),
     "mf_segment_destroy": (_I, [_P]),
+    "mf_segment_refresh": (_I, [_P, _P, _I, _P]),
     "mf_segment_info": (_I, [_P, _P, _P]),
     "mf_filter_bank": (_I, [_P, _P, _I, _F, _P, _P, _I64, _P, _P]),
     "mf_bank_check": (_I, [_P, _P]),

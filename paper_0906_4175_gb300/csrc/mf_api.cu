@@ -182,7 +182,26 @@ struct mf_segment_s {
     double *P = nullptr;
     SegConsts *consts = nullptr;
     int device = 0;
+    // kept for mf_segment_refresh: the PSD (device copy of a table, or the
+    // Eq. (2) parameters) and, after the first refresh, conditioning scratch
+    double *psd = nullptr;
+    double psd_f0 = 0.0, psd_S0 = 0.0;
+    float2 *r_exch = nullptr, *r_X = nullptr;
+    double *r_q = nullptr, *r_btmp = nullptr;
+    float *r_s = nullptr;
+    void release() {
+        cudaFree(W); cudaFree(P); cudaFree(consts); cudaFree(psd);
+        cudaFree(r_exch); cudaFree(r_X); cudaFree(r_q); cudaFree(r_btmp); cudaFree(r_s);
+        W = nullptr; P = nullptr; consts = nullptr; psd = nullptr;
+        r_exch = nullptr; r_X = nullptr; r_q = nullptr; r_btmp = nullptr; r_s = nullptr;
+    }
 };
+
+static bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
 
 static mf_bank_params default_params() {
     mf_bank_params p;
@@ -283,6 +302,8 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     g->N = N;
     g->fs = fs;
     g->log2N = ilog2(N);
+    g->psd_f0 = psd_f0;
+    g->psd_S0 = psd_S0;
     cudaGetDevice(&g->device);
     float *s_dev = nullptr;
     float2 *exch = nullptr, *X = nullptr;
@@ -299,10 +320,11 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
         e = cudaMallocAsync(&s_dev, sizeof(float) * N, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s_dev, s, sizeof(float) * N, cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess && psd) {
-        e = cudaMallocAsync(&psd_dev, sizeof(double) * (half + 1), st);
+    if (e == cudaSuccess && psd) {   // kept by the segment for mf_segment_refresh
+        e = cudaMalloc(&g->psd, sizeof(double) * (half + 1));
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(psd_dev, psd, sizeof(double) * (half + 1), cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(g->psd, psd, sizeof(double) * (half + 1), cudaMemcpyHostToDevice, st);
+        psd_dev = g->psd;
     }
     const float *s_use = s_on_device ? s : s_dev;
     if (e == cudaSuccess) e = launch_forward_fft(s_use, N, exch, X, st);
@@ -311,7 +333,6 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     if (e == cudaSuccess) e = launch_weight_data(X, psd_dev, psd_f0, psd_S0, N, fs, g->P, g->consts, g->W, st);
     if (e == cudaSuccess) count_launches(7);   // 2 FFT passes, weights, 3 scan kernels, weighting
     if (s_dev) cudaFreeAsync(s_dev, st);
-    if (psd_dev) cudaFreeAsync(psd_dev, st);
     if (exch) cudaFreeAsync(exch, st);
     if (X) cudaFreeAsync(X, st);
     if (q) cudaFreeAsync(q, st);
@@ -319,7 +340,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     if (e == cudaSuccess && !s_on_device) e = cudaStreamSynchronize(st);   // host s / psd consumed before return
     else if (e == cudaSuccess && psd) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-        cudaFree(g->W); cudaFree(g->P); cudaFree(g->consts);
+        g->release();
         delete g;
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "segment_upload: %s",
                        cudaGetErrorString(e));
@@ -328,11 +349,47 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     return MF_OK;
 }
 
+extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device, void *cuda_stream) {
+    if (!g || !s) return set_err(MF_EINVAL, "NULL argument");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != g->device) return set_err(MF_EINVAL, "segment lives on device %d, current is %d", g->device, cur);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool capturing = stream_capturing(st);
+    const int64_t N = g->N, half = N / 2;
+    if (!g->r_exch) {
+        if (capturing) return set_err(MF_EINVAL, "the first mf_segment_refresh of a segment must precede stream capture");
+        const int64_t nbt = prefix_block_tmp_count(half);
+        cudaError_t e = cudaMalloc(&g->r_exch, sizeof(float2) * N);
+        if (e == cudaSuccess) e = cudaMalloc(&g->r_X, sizeof(float2) * (half + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&g->r_q, sizeof(double) * half);
+        if (e == cudaSuccess) e = cudaMalloc(&g->r_btmp, sizeof(double) * nbt);
+        if (e != cudaSuccess) {
+            cudaFree(g->r_exch); cudaFree(g->r_X); cudaFree(g->r_q); cudaFree(g->r_btmp);
+            g->r_exch = nullptr; g->r_X = nullptr; g->r_q = nullptr; g->r_btmp = nullptr;
+            return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "segment_refresh: %s",
+                           cudaGetErrorString(e));
+        }
+    }
+    const float *s_use = s;
+    if (!s_on_device) {
+        if (capturing) return set_err(MF_EINVAL, "host samples cannot be refreshed inside a stream capture");
+        if (!g->r_s) MF_CUDA(cudaMalloc(&g->r_s, sizeof(float) * N));
+        MF_CUDA(cudaMemcpyAsync(g->r_s, s, sizeof(float) * N, cudaMemcpyHostToDevice, st));
+        s_use = g->r_s;
+    }
+    MF_CUDA(launch_forward_fft(s_use, N, g->r_exch, g->r_X, st));
+    MF_CUDA(launch_psd_weights(g->r_X, g->psd, g->psd_f0, g->psd_S0, N, g->fs, g->r_q, st));
+    MF_CUDA(launch_prefix_f64(g->r_q, half, g->P, g->r_btmp, st));
+    MF_CUDA(launch_weight_data(g->r_X, g->psd, g->psd_f0, g->psd_S0, N, g->fs, g->P, g->consts, g->W, st));
+    count_launches(7);
+    if (!s_on_device) MF_CUDA(cudaStreamSynchronize(st));   // host s consumed before return
+    return MF_OK;
+}
+
 extern "C" int mf_segment_destroy(mf_segment g) {
     if (!g) return MF_OK;
-    cudaFree(g->W);
-    cudaFree(g->P);
-    cudaFree(g->consts);
+    g->release();
     delete g;
     return MF_OK;
 }
@@ -388,11 +445,15 @@ static int64_t choose_batch(int64_t N, int64_t n_t, int64_t tuned) {
     return b;
 }
 
-static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch, int64_t max_anc, int64_t nblk) {
+static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch, int64_t max_anc, int64_t nblk,
+                            bool capturing) {
     Workspace &w = b->ws;
     if (w.units && w.N >= N && w.n_t >= b->n && w.cap >= cap && w.batch >= batch && w.max_anc >= max_anc &&
         w.nblk >= nblk)
         return MF_OK;
+    if (capturing)
+        return set_err(MF_EINVAL, "the workspace must grow: call mf_filter_bank once with these segments and "
+                                  "trig_cap before capturing it");
     const int64_t nN = std::max(w.N, N), ncap = std::max(std::max(w.cap, cap), (int64_t)1);
     const int64_t nb = std::max(w.batch, batch), na = std::max(w.max_anc, max_anc);
     const int64_t nbl = std::max(w.nblk, nblk);
@@ -512,7 +573,6 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     const int key_bits = kl.j_bits + kl.seg_bits + kl.tmpl_bits;
     if (key_bits > 64) return set_err(MF_EINVAL, "trigger key needs %d bits", key_bits);
 
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     int64_t batch = choose_batch(maxN, b->n, b->tuned_batch);
     for (int s = 0; s < n_seg; ++s)
         if (use_persistent(b, segs[s])) batch = std::max<int64_t>(batch, std::max(kS, kSA));
@@ -522,7 +582,10 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         max_anc = std::max(max_anc, ((segs[s]->N / 2) >> lgD) + 2);
         nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
     }
-    int rc = ensure_workspace(b, maxN, trig_cap, batch, max_anc, nblk);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool capturing = stream_capturing(st);
+    if (capturing && b->prof_on) return set_err(MF_EINVAL, "stage profiling cannot run inside a stream capture");
+    int rc = ensure_workspace(b, maxN, trig_cap, batch, max_anc, nblk, capturing);
     if (rc) return rc;
     Workspace &w = b->ws;
     MF_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st));
@@ -595,7 +658,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             P.spin_limit = b->spin_limit;
             P.stall_unit = (int)b->stall_unit;
             P.stats = nullptr;
-            const bool want_stats = getenv("MFGB_SCHED_STATS") != nullptr;
+            const bool want_stats = getenv("MFGB_SCHED_STATS") != nullptr && !capturing;
             if (want_stats) {
                 MF_CUDA(cudaMallocAsync(&P.stats, sizeof(unsigned long long) * 12, st));
                 MF_CUDA(cudaMemsetAsync(P.stats, 0, sizeof(unsigned long long) * 12, st));
