@@ -55,6 +55,9 @@ def _args():
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
+    ap.add_argument("--workload", default="scale", choices=["scale", "uneven", "precision", "refine"],
+                    help="scale: the benchmark line; the others print their own measurement line "
+                         "(uneven bank over mixed segment lengths, phase precision forms, trigger refinement)")
     return ap.parse_args()
 
 
@@ -248,10 +251,281 @@ def run_reference(args):
     return 0
 
 
+def _timed_steps(torch, run, steps, warmup, flush, stream):
+    """ms per step of run() over `steps` CUDA-event-timed steps after `warmup`
+    untimed ones, L2 flushed before each timed step."""
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        run()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def _capture(torch, run):
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run()
+    return g
+
+
+def run_uneven(args, mf, torch, dev):
+    """4096 templates (m1, m2 in [1, 34], M <= 35, each cut at its own ISCO
+    frequency) over 8 segments of 2^18, 2^18, 2^19, 2^19, 2^20, 2^20, 2^21,
+    2^21 samples in one mf_filter_bank call: the per-segment persistent
+    launches as one CUDA graph, the per-batch launches, and per-template
+    launches."""
+    import workloads
+    wl = workloads.uneven(0)
+    segs = [mf.Segment(mf.synth_segment(sp.normals(), sp.N, sp.fs, wl.f_low, sp.injections), sp.fs)
+            for sp in wl.segments]
+    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
+    cap = 1 << 22
+    n_seg = len(segs)
+    out = (torch.empty((wl.n_templates * n_seg, 4), dtype=torch.float32, device=dev),
+           torch.empty((cap, 6), dtype=torch.float32, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        mf.filter_bank(bank, segs, wl.threshold, trig_cap=cap, out=out)
+
+    res = {}
+    for name, env in (("persistent_graph", {}), ("batch_graph", {"MFGB_SCHED": "batch"}),
+                      ("per_template_eager", {"MFGB_SCHED": "batch", "MFGB_BATCH": "1"})):
+        old = {k: os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH")}
+        for k in old:
+            os.environ.pop(k, None)
+        os.environ.update(env)
+        call()
+        torch.cuda.synchronize()
+        assert bank.check() == 0
+        l0 = mf.launch_count()
+        call()
+        launches = mf.launch_count() - l0
+        if name.endswith("graph"):
+            g = _capture(torch, call)
+            ms = _timed_steps(torch, g.replay, args.steps, args.warmup, flush, stream)
+        else:
+            ms = _timed_steps(torch, call, max(3, args.steps // 10), 1, flush, stream)
+        assert bank.check() == 0
+        res[name] = {"ms_per_call": ms, "launches_per_call": launches, "n_trig": int(out[2].item())}
+        for k, v in old.items():
+            os.environ.pop(k, None)
+            if v is not None:
+                os.environ[k] = v
+    units = wl.n_templates * n_seg
+    eq = wl.n_templates * sum(sp.N for sp in wl.segments) / float(1 << 20)
+    best = min(res.values(), key=lambda r: r["ms_per_call"])["ms_per_call"]
+    line = {"workload": "uneven", "metric": "template-segment units/s (uneven bank, mixed segment lengths)",
+            "value": units / (best / 1e3), "unit": "units/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 2 injections per segment)",
+            "config": {"workload": "4096 templates m1,m2 in [1,34] Msun with M <= 35, 8 segments "
+                                   "N = 2^18,2^18,2^19,2^19,2^20,2^20,2^21,2^21 at 4096 Hz, thr 6",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "equivalent_2p20_templates_per_s": eq / (best / 1e3), "schedules": res}
+    print(json.dumps(line))
+    return 0
+
+
+def run_precision(args, mf, torch, dev):
+    """The phase forms on the 1024-template, N = 2^20 workload: speed of each
+    (one CUDA-graph replay per step) and its rho error against the FP64 oracle
+    on a seeded sample of templates (full series)."""
+    import numpy as np
+    import oracle
+    import workloads
+    oracle.build()
+    wl = workloads.scale(0)
+    spec = wl.segments[0]
+    s32 = oracle.synth(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections).astype(np.float32)
+    s64 = s32.astype(np.float64)
+    s_dev = torch.from_numpy(s32).to(dev)
+    seg = mf.Segment(s_dev, spec.fs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(77)
+    sample = np.sort(rng.choice(wl.n_templates, 8, replace=False))
+    st, S = oracle.data_spectrum(s64, spec.fs), oracle.psd_bins(spec.N, spec.fs)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        ref = list(ex.map(lambda t: oracle.filter_template(float(wl.m1[t]), float(wl.m2[t]), st, S, spec.N,
+                                                           spec.fs, wl.f_low)["rho"], sample))
+    forms = {}
+    cap = 1 << 22
+    for name, mode in (("fp64_anchors_fp32_taylor", mf.MF_PHASE_ANCHOR), ("fp64_per_bin", mf.MF_PHASE_FP64),
+                       ("fp32_only", mf.MF_PHASE_FP32)):
+        bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low, phase_mode=mode)
+        out = (torch.empty((wl.n_templates, 4), dtype=torch.float32, device=dev),
+               torch.empty((cap, 6), dtype=torch.float32, device=dev),
+               torch.zeros(1, dtype=torch.int64, device=dev))
+
+        def call():
+            mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=out)
+
+        call()
+        torch.cuda.synchronize()
+        g = _capture(torch, call)
+        ms = _timed_steps(torch, g.replay, args.steps, args.warmup, flush, stream)
+        # accuracy: full series of the sample (threshold 0)
+        b2 = mf.Bank(wl.m1[sample], wl.m2[sample], f_low=wl.f_low, phase_mode=mode)
+        p, t, n = mf.filter_bank(b2, [seg], 0.0, trig_cap=len(sample) * spec.N)
+        tr = mf.triggers_to_numpy(t, n)
+        rho = tr["rho"].reshape(len(sample), spec.N).astype(np.float64)
+        pk = mf.peaks_to_numpy(p)
+        err = np.concatenate([np.abs(rho[i] - ref[i]) / np.maximum(ref[i], 1.0) for i in range(len(sample))])
+        idx = sum(int(pk["j"][i]) == int(np.argmax(ref[i])) for i in range(len(sample)))
+        mism = 0
+        for i in range(len(sample)):
+            mism += int(np.sum((rho[i] > wl.threshold) != (ref[i] > wl.threshold)))
+        forms[name] = {"templates_per_s": wl.n_templates / (ms / 1e3), "ms_per_call": ms,
+                       "rho_err_max": float(err.max()), "rho_err_median": float(np.median(err)),
+                       "peak_index_agree": "%d/%d" % (idx, len(sample)), "trigger_mismatches": mism}
+    line = {"workload": "precision", "metric": "templates/s and max rho rel err vs FP64 per phase form",
+            "value": forms["fp64_anchors_fp32_taylor"]["templates_per_s"], "unit": "templates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (oracle-synthesised seeded segment, rounded to float32)",
+            "config": {"workload": WORKLOAD, "error_sample": "%d seeded templates, all 2^20 samples" % len(sample),
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "fft": "FP32 in every form (no tensor-core DFT stage is built)"},
+            "forms": forms}
+    print(json.dumps(line))
+    return 0
+
+
+def _ascend(mf, torch, seg, theta0, steps, rel_m=5e-3, step_t=2e-4):
+    """Adam ascent of rho^2 on (m1, m2, t) through RefineFn (x = theta / scale,
+    unit learning rate); best point per row over steps + 1 evaluations."""
+    th0 = theta0
+    sc = torch.stack([rel_m * th0[:, 0], rel_m * th0[:, 1], torch.full_like(th0[:, 2], step_t)], dim=1)
+    x = (th0 / sc).clone().requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=1.0)
+    best_th = th0.clone()
+    best_J = torch.full((th0.shape[0],), -1.0, dtype=torch.float64, device=th0.device)
+    for k in range(steps + 1):
+        th = x * sc
+        J = mf.RefineFn.apply(th, seg)
+        with torch.no_grad():
+            better = J > best_J
+            best_J = torch.where(better, J.detach(), best_J)
+            best_th[better] = th.detach()[better]
+        if k == steps:
+            break
+        opt.zero_grad()
+        (-J.sum()).backward()
+        opt.step()
+    return best_th, best_J
+
+
+def run_refine(args, mf, torch, dev):
+    """Coarse triggers of the 210-template 1-Msun bank on 32 segments of 2^20
+    samples with 8 injections each (256), then 20 Adam steps of rho^2 on
+    (m1, m2, t) per trigger through RefineFn; reports the refinement
+    throughput, the SNR gain and the recovered-mass error."""
+    import numpy as np
+    import workloads
+    wl = workloads.refine_bank(0)
+    fs = wl.segments[0].fs
+    N = wl.segments[0].N
+    segs = [mf.Segment(mf.synth_segment(sp.normals(), sp.N, sp.fs, wl.f_low, sp.injections), sp.fs)
+            for sp in wl.segments]
+    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
+    cap = 1 << 24
+    t0 = time.perf_counter()
+    p, t, n = mf.filter_bank(bank, segs, 4.0, trig_cap=cap)
+    torch.cuda.synchronize()
+    coarse_s = time.perf_counter() - t0
+    assert bank.check() == 0
+    tr = mf.triggers_to_numpy(t, n)
+    starts, truth, rho0 = [], [], []
+    for si, sp in enumerate(wl.segments):
+        ts = tr[tr["seg"] == si]
+        th, tru, r0 = [], [], []
+        for inj in sp.injections:
+            jc = (N - int(inj["j0"])) % N
+            d = np.abs(((ts["j"].astype(np.int64) - jc + N // 2) % N) - N // 2)
+            near = ts[d < int(2.0 * fs)]
+            if near.size == 0:
+                continue
+            b = near[np.argmax(near["rho"])]
+            th.append([wl.m1[int(b["tmpl"])], wl.m2[int(b["tmpl"])], int(b["j"]) / fs])
+            tru.append([inj["m1"], inj["m2"], jc / fs])
+            r0.append(float(b["rho"]))
+        starts.append(torch.tensor(th, dtype=torch.float64, device=dev))
+        truth.append(np.array(tru))
+        rho0.append(np.array(r0))
+    n_trig = sum(int(x.shape[0]) for x in starts)
+    steps = 20
+    # timed: the ascent of every segment's triggers (steps + 1 objective+gradient evaluations each)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = mf.launch_count()
+    ev0.record()
+    results = [_ascend(mf, torch, segs[si], starts[si], steps) for si in range(len(segs))]
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = mf.launch_count() - l0
+    gain, dmc, dm = [], [], []
+    for si, (th, J) in enumerate(results):
+        thn = th.cpu().numpy()
+        rho = np.sqrt(J.cpu().numpy())
+        gain.extend(list(rho / rho0[si]))
+        tru = truth[si]
+        mc = lambda a, b: (a * b) ** 0.6 / (a + b) ** 0.2
+        for k in range(thn.shape[0]):
+            a, b = sorted(thn[k, :2], reverse=True)
+            ta, tb = sorted(tru[k, :2], reverse=True)
+            dmc.append(abs(mc(a, b) - mc(ta, tb)) / mc(ta, tb))
+            dm.append(max(abs(a - ta), abs(b - tb)))
+        # starting-point errors for comparison
+    dmc0, dm0 = [], []
+    for si in range(len(segs)):
+        s0 = starts[si].cpu().numpy()
+        for k in range(s0.shape[0]):
+            a, b = sorted(s0[k, :2], reverse=True)
+            ta, tb = sorted(truth[si][k, :2], reverse=True)
+            mcf = lambda x, y: (x * y) ** 0.6 / (x + y) ** 0.2
+            dmc0.append(abs(mcf(a, b) - mcf(ta, tb)) / mcf(ta, tb))
+            dm0.append(max(abs(a - ta), abs(b - tb)))
+    evals = n_trig * (steps + 1)
+    line = {"workload": "refine", "metric": "trigger objective+gradient evaluations/s (Adam ascent of rho^2)",
+            "value": evals / (ms / 1e3), "unit": "evaluations/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64 phase, f32 sums", "ms_total": ms, "gpu_launches": launches,
+            "data": "synthetic (seeded coloured Gaussian noise, 8 injections per segment, m in [1, 20], SNR 8-15)",
+            "config": {"workload": "210-template 1-Msun bank (m1 >= m2 in 1..20), 32 segments N=2^20 at 4096 Hz, "
+                                   "256 injections; coarse threshold 4; %d Adam steps, steps rel 5e-3 m and 2e-4 s"
+                                   % steps,
+                       "coarse_filter_s": coarse_s},
+            "triggers": n_trig,
+            "snr_gain": {"median": float(np.median(gain)), "min": float(np.min(gain)),
+                         "max": float(np.max(gain))},
+            "chirp_mass_rel_err": {"coarse_median": float(np.median(dmc0)), "refined_median": float(np.median(dmc))},
+            "component_mass_err_msun": {"coarse_median": float(np.median(dm0)), "refined_median": float(np.median(dm))}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "scale":
+        if args.warmup < 3:
+            args.warmup = 3
+        import torch
+        torch.cuda.set_device(0)
+        from paper_0906_4175_gb300 import build as _b
+        _b.build()
+        import paper_0906_4175_gb300 as mf
+        fn = {"uneven": run_uneven, "precision": run_precision, "refine": run_refine}[args.workload]
+        return fn(args, mf, torch, torch.device("cuda", 0))
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = _dist()
