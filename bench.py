@@ -296,7 +296,7 @@ def run_uneven(args, mf, torch, dev):
         mf.filter_bank(bank, segs, wl.threshold, trig_cap=cap, out=out)
 
     res = {}
-    for name, env in (("persistent_graph", {}), ("batch_graph", {"MFGB_SCHED": "batch"}),
+    for name, env in (("persistent_graph", {"MFGB_SCHED": "persistent"}), ("batch_graph", {"MFGB_SCHED": "batch"}),
                       ("per_template_eager", {"MFGB_SCHED": "batch", "MFGB_BATCH": "1"})):
         old = {k: os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH")}
         for k in old:
@@ -314,7 +314,13 @@ def run_uneven(args, mf, torch, dev):
         else:
             ms = _timed_steps(torch, call, max(3, args.steps // 10), 1, flush, stream)
         assert bank.check() == 0
-        res[name] = {"ms_per_call": ms, "launches_per_call": launches, "n_trig": int(out[2].item())}
+        bank.profile(True)
+        call()
+        torch.cuda.synchronize()
+        stages = {k: round(v[0], 3) for k, v in bank.profile_read().items() if v[2] > 0}
+        bank.profile(False)
+        res[name] = {"ms_per_call": ms, "launches_per_call": launches, "n_trig": int(out[2].item()),
+                     "stage_ms_eager": stages}
         for k, v in old.items():
             os.environ.pop(k, None)
             if v is not None:

@@ -163,8 +163,10 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
 
 /* mf_autotune -- times the candidate schedules of mf_filter_bank for this
  * bank on these segments (the persistent scheduler with 55/60/65% of the SMs
- * starting on template generation + column FFTs, and per-batch launches of
- * 16..128 templates) and keeps the fastest in the bank for later calls.  It
+ * starting on template generation + column FFTs, and per-batch launches with
+ * 128 MiB..1 GiB of exchange in flight, i.e. 16..128 templates per batch at
+ * N = 2^20 and proportionally more at shorter segments) and keeps the fastest
+ * in the bank for later calls (the default is per-batch launches with 1 GiB).  It
  * runs each candidate 1 + repeats times on cuda_stream and synchronises; it
  * allocates temporary outputs and may grow the bank's workspace.  threshold
  * should be the one the search will use (it sets the trigger traffic).  If

@@ -112,7 +112,7 @@ static double psi_deriv_bound(const double *rec, double f, int n) {
 // handles
 // ---------------------------------------------------------------------------
 struct Workspace {
-    int64_t N = 0, n_t = 0, cap = 0, batch = 0, max_anc = 0, nblk = 0;
+    int64_t exch_elems = 0, n_t = 0, cap = 0, anc_elems = 0, nblk = 0;
     UnitInfo *units = nullptr;
     float2 *exch = nullptr;
     float4 *anchors = nullptr;
@@ -121,12 +121,16 @@ struct Workspace {
     mf_trigger *staged = nullptr;
     uint64_t *keys = nullptr, *keys_tmp = nullptr;
     uint32_t *idx_a = nullptr, *idx_b = nullptr;
+    uint32_t *ghist = nullptr;    // trigger sort: digit histograms of every pass
+    uint64_t *tstat = nullptr;    // trigger sort: look-back status per (tile, digit)
+    unsigned *tickets = nullptr;  // trigger sort: tile tickets per pass
     unsigned long long *counter = nullptr;
     int *status = nullptr;
     unsigned *ctl = nullptr;      // persistent scheduler: [1] abort, then doneA, done1, done2 per unit
     void release() {
         cudaFree(units); cudaFree(exch); cudaFree(anchors); cudaFree(anchors4); cudaFree(partials);
         cudaFree(staged); cudaFree(keys); cudaFree(keys_tmp); cudaFree(idx_a); cudaFree(idx_b);
+        cudaFree(ghist); cudaFree(tstat); cudaFree(tickets);
         cudaFree(counter); cudaFree(status); cudaFree(ctl);
         *this = Workspace();
     }
@@ -151,10 +155,11 @@ struct mf_bank_s {
     int64_t stall_unit = -1;          // test hook (mf_bank_debug_stall)
     long long spin_limit = 4000000;   // bounded-wait iterations, back-off <= ~1 us each
     // schedule (defaults until mf_autotune measures this bank): 0 = persistent
-    // scheduler, 1 = per-batch launches; templates per batch (0 = by L2 size);
+    // scheduler, 1 = per-batch launches; exchange bytes in flight per batch
+    // (templates per batch = tuned_exch / (8 N), 0 = the default budget);
     // fraction of SMs that start on queue 1
-    int sched = 0;
-    int64_t tuned_batch = 0;
+    int sched = 1;
+    int64_t tuned_exch = 0;
     double split = 0.60;
 };
 
@@ -436,8 +441,13 @@ static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
 }
 
 // templates in flight per batch (exchange ring of batch * N complex64)
-static int64_t choose_batch(int64_t N, int64_t n_t, int64_t tuned) {
-    int64_t b = tuned > 0 ? tuned : ((int64_t)64 << 20) / (8 * N);
+// Default exchange budget of the per-batch launches: 1 GiB (128 templates in
+// flight at N = 2^20), the fastest budget measured on GB300 at 2^18..2^21;
+// mf_autotune replaces it per bank.
+constexpr int64_t kExchBudget = (int64_t)1 << 30;
+
+static int64_t choose_batch(int64_t N, int64_t n_t, int64_t tuned_exch) {
+    int64_t b = (tuned_exch > 0 ? tuned_exch : kExchBudget) / (8 * N);
     if (const char *env = getenv("MFGB_BATCH")) b = atoll(env);
     if (b < 1) b = 1;
     if (b > 65535) b = 65535;
@@ -445,35 +455,40 @@ static int64_t choose_batch(int64_t N, int64_t n_t, int64_t tuned) {
     return b;
 }
 
-static int ensure_workspace(mf_bank_s *b, int64_t N, int64_t cap, int64_t batch, int64_t max_anc, int64_t nblk,
+// exch_elems: complex64 entries of the exchange ring (max over the call's
+// segments of batch * N); anc_elems: anchor records (max of batch * anchors)
+static int ensure_workspace(mf_bank_s *b, int64_t exch_elems, int64_t cap, int64_t anc_elems, int64_t nblk,
                             bool capturing) {
     Workspace &w = b->ws;
-    if (w.units && w.N >= N && w.n_t >= b->n && w.cap >= cap && w.batch >= batch && w.max_anc >= max_anc &&
+    if (w.units && w.exch_elems >= exch_elems && w.n_t >= b->n && w.cap >= cap && w.anc_elems >= anc_elems &&
         w.nblk >= nblk)
         return MF_OK;
     if (capturing)
         return set_err(MF_EINVAL, "the workspace must grow: call mf_filter_bank once with these segments and "
                                   "trig_cap before capturing it");
-    const int64_t nN = std::max(w.N, N), ncap = std::max(std::max(w.cap, cap), (int64_t)1);
-    const int64_t nb = std::max(w.batch, batch), na = std::max(w.max_anc, max_anc);
+    const int64_t ne = std::max(w.exch_elems, exch_elems), ncap = std::max(std::max(w.cap, cap), (int64_t)1);
+    const int64_t na = std::max(w.anc_elems, anc_elems);
     const int64_t nbl = std::max(w.nblk, nblk);
     MF_CUDA(cudaDeviceSynchronize());
     w.release();
     MF_CUDA(cudaMalloc(&w.units, sizeof(UnitInfo) * b->n));
-    MF_CUDA(cudaMalloc(&w.exch, sizeof(float2) * nN * nb));
-    MF_CUDA(cudaMalloc(&w.anchors, sizeof(float4) * na * nb));
-    MF_CUDA(cudaMalloc(&w.anchors4, sizeof(float) * na * nb));
+    MF_CUDA(cudaMalloc(&w.exch, sizeof(float2) * ne));
+    MF_CUDA(cudaMalloc(&w.anchors, sizeof(float4) * na));
+    MF_CUDA(cudaMalloc(&w.anchors4, sizeof(float) * na));
     MF_CUDA(cudaMalloc(&w.partials, sizeof(float4) * nbl * b->n));
     MF_CUDA(cudaMalloc(&w.staged, sizeof(mf_trigger) * ncap));
     MF_CUDA(cudaMalloc(&w.keys, sizeof(uint64_t) * ncap));
     MF_CUDA(cudaMalloc(&w.keys_tmp, sizeof(uint64_t) * ncap));
     MF_CUDA(cudaMalloc(&w.idx_a, sizeof(uint32_t) * ncap));
     MF_CUDA(cudaMalloc(&w.idx_b, sizeof(uint32_t) * ncap));
+    MF_CUDA(cudaMalloc(&w.ghist, sizeof(uint32_t) * 256 * 8));
+    MF_CUDA(cudaMalloc(&w.tstat, sizeof(uint64_t) * sort_tile_words(ncap)));
+    MF_CUDA(cudaMalloc(&w.tickets, sizeof(unsigned) * 8));
     MF_CUDA(cudaMalloc(&w.counter, sizeof(unsigned long long)));
     MF_CUDA(cudaMalloc(&w.status, sizeof(int)));
     MF_CUDA(cudaMemset(w.status, 0, sizeof(int)));
     MF_CUDA(cudaMalloc(&w.ctl, sizeof(unsigned) * (4 + 3 * b->n)));
-    w.N = nN; w.n_t = b->n; w.cap = ncap; w.batch = nb; w.max_anc = na; w.nblk = nbl;
+    w.exch_elems = ne; w.n_t = b->n; w.cap = ncap; w.anc_elems = na; w.nblk = nbl;
     return MF_OK;
 }
 
@@ -486,7 +501,10 @@ constexpr double kSplit = 0.60;
 
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
     if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32) return false;
-    if (const char *e = getenv("MFGB_SCHED")) return strcmp(e, "batch") != 0;
+    if (const char *e = getenv("MFGB_SCHED")) {
+        if (strcmp(e, "batch") == 0) return false;
+        if (strcmp(e, "persistent") == 0) return true;
+    }
     return b->sched == 0;
 }
 
@@ -573,19 +591,23 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     const int key_bits = kl.j_bits + kl.seg_bits + kl.tmpl_bits;
     if (key_bits > 64) return set_err(MF_EINVAL, "trigger key needs %d bits", key_bits);
 
-    int64_t batch = choose_batch(maxN, b->n, b->tuned_batch);
-    for (int s = 0; s < n_seg; ++s)
-        if (use_persistent(b, segs[s])) batch = std::max<int64_t>(batch, std::max(kS, kSA));
-    int64_t max_anc = 0, nblk = 0;
+    // templates in flight per segment: the exchange budget over the segment's
+    // length (the persistent scheduler needs its ring slots)
+    std::vector<int64_t> seg_batch((size_t)n_seg);
+    int64_t exch_elems = 0, anc_elems = 0, nblk = 0;
     for (int s = 0; s < n_seg; ++s) {
+        int64_t bt = choose_batch(segs[s]->N, b->n, b->tuned_exch);
+        if (use_persistent(b, segs[s])) bt = std::max<int64_t>(bt, std::max(kS, kSA));
+        seg_batch[(size_t)s] = bt;
         const int lgD = choose_log2D(b, segs[s]);
-        max_anc = std::max(max_anc, ((segs[s]->N / 2) >> lgD) + 2);
+        exch_elems = std::max(exch_elems, bt * segs[s]->N);
+        anc_elems = std::max(anc_elems, bt * (((segs[s]->N / 2) >> lgD) + 2));
         nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool capturing = stream_capturing(st);
     if (capturing && b->prof_on) return set_err(MF_EINVAL, "stage profiling cannot run inside a stream capture");
-    int rc = ensure_workspace(b, maxN, trig_cap, batch, max_anc, nblk, capturing);
+    int rc = ensure_workspace(b, exch_elems, trig_cap, anc_elems, nblk, capturing);
     if (rc) return rc;
     Workspace &w = b->ws;
     MF_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st));
@@ -687,6 +709,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             count_launches(1);
             continue;
         }
+        const int64_t batch = seg_batch[(size_t)s];
         for (int u0 = 0; u0 < n_t; u0 += (int)batch) {
             const int nb = (int)std::min<int64_t>(batch, n_t - u0);
             double by_band = 0.0, by_anc = 0.0;
@@ -715,10 +738,11 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         count_launches(1);
     }
     int pf = prof_begin(b, MF_STAGE_FINAL, 0.0, st);
-    MF_CUDA(launch_sort_triggers(w.counter, trig_cap, key_bits, w.staged, w.keys, w.keys_tmp, w.idx_a, w.idx_b,
-                                 trig, n_trig, w.status, st));
+    MF_CUDA(launch_sort_triggers(w.counter, std::max<int64_t>(trig_cap, 0), key_bits, w.staged, w.keys,
+                                 w.keys_tmp, w.idx_a, w.idx_b, w.ghist, w.tstat, w.tickets, trig, n_trig, w.status,
+                                 sm_count(), b->spin_limit, st));
     prof_end(b, pf, st);
-    count_launches(1);
+    count_launches(sort_launches(key_bits));
     return MF_OK;
 }
 
@@ -773,13 +797,12 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     if (!b || !segs || n_seg < 1) return set_err(MF_EINVAL, "need a bank and n_seg >= 1 segments");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (repeats < 1) repeats = 2;
-    struct Cand { int sched; int64_t batch; double split; };
+    struct Cand { int sched; int64_t exch; double split; };
     std::vector<Cand> cands;
     for (double sp : {0.55, 0.60, 0.65}) cands.push_back({0, 0, sp});
     int64_t maxN = 0;
     for (int s = 0; s < n_seg; ++s) maxN = std::max(maxN, segs[s]->N);
-    for (int64_t bt : {16, 32, 64, 128})
-        if (bt * maxN * 8 <= ((int64_t)2 << 30)) cands.push_back({1, bt, 0.60});
+    for (int64_t mib : {128, 256, 512, 1024}) cands.push_back({1, mib << 20, 0.60});
     const int64_t cap = 1 << 16;
     mf_peak *pk = nullptr;
     mf_trigger *tr = nullptr;
@@ -791,14 +814,14 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_sched = b->sched;
-    const int64_t saved_batch = b->tuned_batch;
+    const int64_t saved_exch = b->tuned_exch;
     const double saved_split = b->split;
     float best_ms = 1e30f;
-    Cand best = {saved_sched, saved_batch, saved_split};
+    Cand best = {saved_sched, saved_exch, saved_split};
     int rc = MF_OK;
     for (const Cand &c : cands) {
         b->sched = c.sched;
-        b->tuned_batch = c.batch;
+        b->tuned_exch = c.exch;
         b->split = c.split;
         rc = mf_filter_bank(b, segs, n_seg, threshold, pk, tr, cap, nt, cuda_stream);   // warm-up, sizes workspace
         if (rc) break;
@@ -817,16 +840,17 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     cudaFree(tr);
     cudaFree(nt);
     b->sched = best.sched;
-    b->tuned_batch = best.batch;
+    b->tuned_exch = best.exch;
     b->split = best.split;
     if (rc) return rc;
     if (cache_path && cache_path[0]) {
         FILE *f = fopen(cache_path, "w");
         if (!f) return set_err(MF_EINVAL, "cannot write %s", cache_path);
-        fprintf(f, "{\"N\": %lld, \"templates\": %lld, \"segments\": %d, \"scheduler\": \"%s\", \"batch\": %lld, "
-                   "\"split\": %.3f, \"ms_per_call\": %.4f}\n",
+        const int64_t ex = best.exch > 0 ? best.exch : kExchBudget;
+        fprintf(f, "{\"N\": %lld, \"templates\": %lld, \"segments\": %d, \"scheduler\": \"%s\", "
+                   "\"exchange_mib\": %lld, \"batch_at_max_N\": %lld, \"split\": %.3f, \"ms_per_call\": %.4f}\n",
                 (long long)maxN, (long long)b->n, n_seg, best.sched == 0 ? "persistent" : "batch",
-                (long long)best.batch, best.split, best_ms / repeats);
+                (long long)(ex >> 20), (long long)choose_batch(maxN, b->n, ex), best.split, best_ms / repeats);
         fclose(f);
     }
     return MF_OK;

@@ -229,113 +229,211 @@ cudaError_t launch_reduce_peaks(const SegDev &seg, const UnitInfo *units, int n_
 }
 
 // ---------------------------------------------------------------------------
-// Trigger compaction: stable LSD radix sort of the (tmpl, seg, j) keys by one
-// CTA of 32 warps (8-bit digits; warp w owns the w-th contiguous chunk; ranks
-// inside a warp by __match_any_sync keep equal digits in input order), then a
-// gather into the caller's buffer.  Sets status bit 0 on overflow.
+// Trigger compaction: stable LSD radix sort of the (tmpl, seg, j) keys with
+// 8-bit digits over the whole GPU, then a gather into the caller's buffer.
+//   k_sort_prepare   n = min(count, cap); *n_out; overflow bit; digit
+//                    histograms of every pass over all keys; zeroes the
+//                    tile status words and the tile tickets.
+//   k_sort_pass      one per digit: CTAs take 2048-key tiles in ticket order,
+//                    rank keys stably inside the tile (warp w owns keys
+//                    [256 w, 256 w + 256) in 8 rows of 32; __match_any_sync
+//                    ranks equal digits of a row in lane order), publish the
+//                    tile's digit counts and find the counts of all earlier
+//                    tiles by decoupled look-back (Merrill & Garland's
+//                    single-pass scan), then scatter.  The last pass writes
+//                    the records themselves.
+// A tile only waits on tiles with smaller tickets, which running CTAs hold,
+// so the look-back always progresses; each wait is still bounded and sets
+// status bit 1 when it gives up.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t block_exclusive_scan_1024(uint32_t x, uint32_t *wtot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = wtot[lane], wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        wtot[lane] = wi - w;
-    }
-    __syncthreads();
-    const uint32_t r = wtot[warp] + incl - x;
-    __syncthreads();
-    return r;
+constexpr int kSortThreads = 256, kSortRows = 8, kSortTile = kSortThreads * kSortRows;
+constexpr int kSortMaxPass = 8;
+
+__device__ __forceinline__ int64_t sort_count(const unsigned long long *counter, int64_t cap) {
+    const unsigned long long total = *counter;
+    return (int64_t)(total < (unsigned long long)cap ? total : (unsigned long long)cap);
 }
 
-__global__ void __launch_bounds__(1024, 1)
-    k_sort_triggers(const unsigned long long *__restrict__ counter, int64_t cap, int key_bits,
-                    const mf_trigger *__restrict__ staged, uint64_t *keys, uint64_t *keys_tmp, uint32_t *idx_a,
-                    uint32_t *idx_b, mf_trigger *__restrict__ out, int64_t *n_out, int *status) {
-    __shared__ uint32_t hist[256][33];
-    __shared__ uint32_t wtot[32];
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_prepare(const unsigned long long *__restrict__ counter, int64_t cap, int npass,
+                   const uint64_t *__restrict__ keys, uint32_t *__restrict__ ghist, uint64_t *__restrict__ tstat,
+                   unsigned *__restrict__ tickets, int64_t *__restrict__ n_out, int *status) {
+    __shared__ uint32_t h[kSortMaxPass][256];
     const unsigned long long total = *counter;
-    const int64_t n = (int64_t)(total < (unsigned long long)cap ? total : (unsigned long long)cap);
-    if (threadIdx.x == 0) {
+    const int64_t n = sort_count(counter, cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *n_out = (int64_t)total;
         if (total > (unsigned long long)cap) atomicOr(status, 1);
     }
-    if (n == 0) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t chunk = (n + 31) / 32;
-    const int64_t lo = (int64_t)warp * chunk;
-    const int64_t hi = (lo + chunk < n) ? lo + chunk : n;
-    const int npass = key_bits > 0 ? (key_bits + 7) / 8 : 1;
-    const uint64_t *kin = keys;
-    const uint32_t *iin = nullptr;
-    uint64_t *kbuf[2] = {keys_tmp, keys};
-    uint32_t *ibuf[2] = {idx_a, idx_b};
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int pass = 0; pass < npass; ++pass) {
-        uint64_t *kout = kbuf[pass & 1];
-        uint32_t *iout = ibuf[pass & 1];
-        const int shift = 8 * pass;
-        for (int e = threadIdx.x; e < 256 * 32; e += 1024) hist[e >> 5][e & 31] = 0u;
-        __syncthreads();
-        if (lo < hi)
-            for (int64_t i = lo + lane; i < hi; i += 32) atomicAdd(&hist[(kin[i] >> shift) & 255u][warp], 1u);
-        __syncthreads();
-        uint32_t loc[8], s = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = threadIdx.x * 8 + q;
-            loc[q] = s;
-            s += hist[e >> 5][e & 31];
-        }
-        const uint32_t off = block_exclusive_scan_1024(s, wtot);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = threadIdx.x * 8 + q;
-            hist[e >> 5][e & 31] = off + loc[q];
-        }
-        __syncthreads();
-        for (int64_t base = lo; base < hi; base += 32) {
-            const int64_t i = base + lane;
-            const bool act = i < hi;
-            const uint64_t key = act ? kin[i] : 0ull;
-            const uint32_t id = act ? (iin ? iin[i] : (uint32_t)i) : 0u;
-            const uint32_t d = act ? (uint32_t)((key >> shift) & 255u) : (256u + (uint32_t)lane);
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int rank = __popc(peers & lt_mask);
-            if (act) {
-                const uint32_t pos = hist[d][warp] + (uint32_t)rank;
-                kout[pos] = key;
-                iout[pos] = id;
-            }
-            __syncwarp();
-            if (act && rank == 0) hist[d][warp] += (uint32_t)__popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        kin = kout;
-        iin = iout;
+    if (blockIdx.x == 0 && threadIdx.x < kSortMaxPass) tickets[threadIdx.x] = 0u;
+    const int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < n_tiles * 256; i += stride) tstat[i] = 0ull;
+    for (int e = threadIdx.x; e < kSortMaxPass * 256; e += blockDim.x) h[e >> 8][e & 255] = 0u;
+    __syncthreads();
+    for (int64_t i = t0; i < n; i += stride) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
     }
-    for (int64_t i = threadIdx.x; i < n; i += 1024) out[i] = staged[iin[i]];
+    __syncthreads();
+    for (int e = threadIdx.x; e < npass * 256; e += blockDim.x) {
+        const uint32_t c = h[e >> 8][e & 255];
+        if (c) atomicAdd(&ghist[e], c);
+    }
+}
+
+// status word of (tile, digit): bits 63..60 = pass + 1, bit 59 = inclusive
+// prefix, bit 58 = tile aggregate, bits 31..0 = count
+__device__ __forceinline__ uint64_t tstat_load(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void tstat_store(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_pass(const unsigned long long *__restrict__ counter, int64_t cap, int pass, int last,
+                const uint64_t *__restrict__ kin, const uint32_t *__restrict__ iin, uint64_t *__restrict__ kout,
+                uint32_t *__restrict__ iout, const uint32_t *__restrict__ ghist, uint64_t *tstat,
+                unsigned *tickets, const mf_trigger *__restrict__ staged, mf_trigger *__restrict__ out,
+                int *status, int64_t spin_limit) {
+    __shared__ uint32_t whist[kSortThreads / 32][256];
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t gpre[256];
+    __shared__ uint32_t wsum[kSortThreads / 32];
+    __shared__ int s_tile, s_abort;
+    const int64_t n = sort_count(counter, cap);
+    const int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, d_own = threadIdx.x;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int shift = 8 * pass;
+    const uint64_t tag = (uint64_t)(pass + 1) << 60;
+    const uint64_t kPrefix = 1ull << 59, kAgg = 1ull << 58;
+    // exclusive prefix of this pass's global digit counts (256 threads = 256 digits)
+    {
+        const uint32_t x = ghist[pass * 256 + d_own];
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t wo = 0;
+        for (int w = 0; w < warp; ++w) wo += wsum[w];
+        gpre[d_own] = wo + incl - x;
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&tickets[pass], 1u);
+        for (int e = lane; e < 256; e += 32) whist[warp][e] = 0u;
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= n_tiles || s_abort) break;
+        const int64_t row0 = tile * kSortTile + (int64_t)warp * (32 * kSortRows);
+        uint64_t key[kSortRows];
+        uint32_t id[kSortRows], dg[kSortRows], lr[kSortRows];
+#pragma unroll
+        for (int r = 0; r < kSortRows; ++r) {
+            const int64_t i = row0 + r * 32 + lane;
+            const bool act = i < n;
+            key[r] = act ? kin[i] : 0ull;
+            id[r] = act ? (iin ? iin[i] : (uint32_t)i) : 0u;
+            dg[r] = act ? (uint32_t)((key[r] >> shift) & 255u) : (256u + (uint32_t)lane);
+        }
+#pragma unroll
+        for (int r = 0; r < kSortRows; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+            const uint32_t rank = (uint32_t)__popc(peers & lt_mask);
+            const bool act = dg[r] < 256u;
+            lr[r] = act ? whist[warp][dg[r]] + rank : 0u;
+            __syncwarp();
+            if (act && rank == 0) whist[warp][dg[r]] += (uint32_t)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // digit d_own: offsets of the warps inside the tile, and the tile total
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t c = whist[w][d_own];
+            whist[w][d_own] = tot;
+            tot += c;
+        }
+        uint64_t *my = tstat + tile * 256 + d_own;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            tstat_store(my, tag | kPrefix | tot);
+        } else {
+            tstat_store(my, tag | kAgg | tot);
+            int64_t pt = tile - 1;
+            int64_t spins = 0;
+            while (pt >= 0) {
+                const uint64_t v = tstat_load(tstat + pt * 256 + d_own);
+                if ((v >> 60) == (uint64_t)(pass + 1) && (v & (kPrefix | kAgg))) {
+                    excl += (uint32_t)v;
+                    if (v & kPrefix) break;
+                    --pt;
+                    continue;
+                }
+                if (++spins > spin_limit || *(volatile int *)&s_abort) {
+                    atomicOr(status, 2);
+                    s_abort = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            tstat_store(my, tag | kPrefix | (uint32_t)(excl + tot));
+        }
+        base[d_own] = gpre[d_own] + excl;
+        __syncthreads();
+        if (s_abort) break;
+#pragma unroll
+        for (int r = 0; r < kSortRows; ++r) {
+            if (dg[r] < 256u) {
+                const uint32_t pos = base[dg[r]] + whist[warp][dg[r]] + lr[r];
+                if (last) {
+                    out[pos] = staged[id[r]];
+                } else {
+                    kout[pos] = key[r];
+                    iout[pos] = id[r];
+                }
+            }
+        }
+    }
 }
 
 cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,
                                  const mf_trigger *staged, const uint64_t *keys, uint64_t *keys_tmp,
-                                 uint32_t *idx_a, uint32_t *idx_b, mf_trigger *out, int64_t *n_out, int *status,
-                                 cudaStream_t st) {
-    k_sort_triggers<<<1, 1024, 0, st>>>(counter, cap, key_bits, staged, const_cast<uint64_t *>(keys), keys_tmp,
-                                        idx_a, idx_b, out, n_out, status);
+                                 uint32_t *idx_a, uint32_t *idx_b, uint32_t *ghist, uint64_t *tstat,
+                                 unsigned *tickets, mf_trigger *out, int64_t *n_out, int *status, int n_sm,
+                                 int64_t spin_limit, cudaStream_t st) {
+    int npass = key_bits > 0 ? (key_bits + 7) / 8 : 1;
+    if (npass > kSortMaxPass) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * 256 * kSortMaxPass, st);
+    if (e != cudaSuccess) return e;
+    const int grid = 2 * n_sm;
+    k_sort_prepare<<<grid, kSortThreads, 0, st>>>(counter, cap, npass, keys, ghist, tstat, tickets, n_out, status);
+    uint64_t *kbuf[2] = {keys_tmp, const_cast<uint64_t *>(keys)};
+    uint32_t *ibuf[2] = {idx_a, idx_b};
+    const uint64_t *kin = keys;
+    const uint32_t *iin = nullptr;
+    for (int p = 0; p < npass; ++p) {
+        uint64_t *kout = kbuf[p & 1];
+        uint32_t *iout = ibuf[p & 1];
+        k_sort_pass<<<grid, kSortThreads, 0, st>>>(counter, cap, p, p == npass - 1 ? 1 : 0, kin, iin, kout, iout,
+                                                   ghist, tstat, tickets, staged, out, status, spin_limit);
+        kin = kout;
+        iin = iout;
+    }
     return cudaGetLastError();
 }
+
+int sort_launches(int key_bits) { return 1 + (key_bits > 0 ? (key_bits + 7) / 8 : 1); }
 
 }  // namespace mf

@@ -128,8 +128,12 @@ cudaError_t launch_reduce_peaks(const SegDev &seg, const UnitInfo *units, int n_
                                 int nblk, int seg_idx, int n_seg, mf_peak *peaks, cudaStream_t st);
 cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,
                                  const mf_trigger *staged, const uint64_t *keys, uint64_t *keys_tmp,
-                                 uint32_t *idx_a, uint32_t *idx_b, mf_trigger *out, int64_t *n_out,
-                                 int *status, cudaStream_t st);
+                                 uint32_t *idx_a, uint32_t *idx_b, uint32_t *ghist, uint64_t *tstat,
+                                 unsigned *tickets, mf_trigger *out, int64_t *n_out, int *status, int n_sm,
+                                 int64_t spin_limit, cudaStream_t st);
+int sort_launches(int key_bits);   // kernels queued by launch_sort_triggers
+// tile status words the sort needs for cap records (one per 2048-key tile and digit)
+inline int64_t sort_tile_words(int64_t cap) { return ((cap + 2047) / 2048) * 256; }
 
 // refinement (mf_refine.cu)
 cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,

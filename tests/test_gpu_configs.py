@@ -108,7 +108,7 @@ def test_uneven_bank_schedules_and_graph_agree(mf, uneven_data, monkeypatch):
     replay gives bit-identical peaks and triggers."""
     import torch
     wl, _, segs = uneven_data
-    monkeypatch.delenv("MFGB_SCHED", raising=False)
+    monkeypatch.setenv("MFGB_SCHED", "persistent")
     monkeypatch.delenv("MFGB_BATCH", raising=False)
     _, pk_a, tr_a, n_a = _uneven_call(mf, wl, segs)
     monkeypatch.setenv("MFGB_SCHED", "batch")
@@ -121,7 +121,7 @@ def test_uneven_bank_schedules_and_graph_agree(mf, uneven_data, monkeypatch):
     monkeypatch.setenv("MFGB_BATCH", "1")
     _, pk_c, tr_c, n_c = _uneven_call(mf, sub, segs)
     monkeypatch.delenv("MFGB_BATCH")
-    monkeypatch.delenv("MFGB_SCHED")
+    monkeypatch.setenv("MFGB_SCHED", "persistent")
     _, pk_d, tr_d, n_d = _uneven_call(mf, sub, segs)
     assert n_c == n_d
     assert np.array_equal(pk_c.view(np.uint8), pk_d.view(np.uint8))

@@ -73,10 +73,7 @@ def test_refresh_keeps_psd_table(mf):
 @pytest.mark.parametrize("sched", ["persistent", "batch"])
 def test_graph_replay_equals_eager(mf, monkeypatch, sched):
     import torch
-    if sched == "batch":
-        monkeypatch.setenv("MFGB_SCHED", "batch")
-    else:
-        monkeypatch.delenv("MFGB_SCHED", raising=False)
+    monkeypatch.setenv("MFGB_SCHED", sched)
     s1, s2 = _two_segments(mf)
     wl = workloads.tiny()
     bank = mf.Bank(wl.m1, wl.m2)

@@ -307,6 +307,7 @@ def test_persistent_and_batch_schedulers_agree(mf, monkeypatch):
     s32, _ = oracle_segment(spec)
     seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
     bank = mf.Bank(wl.m1, wl.m2)
+    monkeypatch.setenv("MFGB_SCHED", "persistent")
     a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 18)]
     monkeypatch.setenv("MFGB_SCHED", "batch")
     b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 18)]
@@ -316,11 +317,12 @@ def test_persistent_and_batch_schedulers_agree(mf, monkeypatch):
     assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
 
 
-def test_bounded_wait_timeout_reports_and_recovers(mf):
-    """A wait that can never be satisfied (test hook) runs out after its
-    iteration limit: the call reports MF_ETIMEOUT, nothing faults, and the next
-    call on the same bank is correct again."""
+def test_bounded_wait_timeout_reports_and_recovers(mf, monkeypatch):
+    """A wait of the persistent scheduler that can never be satisfied (test
+    hook) runs out after its iteration limit: the call reports MF_ETIMEOUT,
+    nothing faults, and the next call on the same bank is correct again."""
     import torch
+    monkeypatch.setenv("MFGB_SCHED", "persistent")
     wl = workloads.small(seed=13, N=1 << 14, fs=4096.0, n_templates=6)
     spec = wl.segments[0]
     s32, _ = oracle_segment(spec)
