@@ -204,8 +204,20 @@ int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, const doubl
                        int64_t n, const int64_t *band, double *obj, double *grad,
                        void *cuda_stream);
 
+/* mf_refine_triggers_multi -- mf_refine_triggers for rows that belong to
+ * different segments, in one launch: row i uses segs[row_seg[i]] (row_seg:
+ * device int32 [n]; segs: host array of 1 <= n_seg <= 256 handles on the
+ * current device).  A row whose row_seg is outside [0, n_seg) gets NaN in
+ * obj and grad.  Other arguments, layouts and errors as mf_refine_triggers;
+ * a row's result equals that of mf_refine_triggers on its segment up to the
+ * grouping of the partial sums (which depends on n). */
+int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const int32_t *row_seg,
+                             const mf_bank_params *params, const double *theta, int64_t n,
+                             const int64_t *band, double *obj, double *grad, void *cuda_stream);
+
 /* mf_refine_triggers_static -- the same computation as mf_refine_triggers
- * (same arguments, same results) for callers that cannot allocate device
+ * (same arguments; results agree to rounding, as the partial sums are
+ * grouped differently) for callers that cannot allocate device
  * memory while they refine: the call makes no cudaMalloc, cudaMallocAsync,
  * cudaFree or other allocating call.  The paper has no counterpart; it exists
  * for ascent loops that run while another component owns the device

@@ -229,24 +229,46 @@ def synth_segment(g, N: int, fs: float, f_low: float = 40.0, injections=None, ps
     return s
 
 
-def refine(segment: Segment, theta, band=None, f_low: float = 40.0, stream=None):
-    """mf_refine_triggers: rho^2 and d rho^2 / d(m1, m2, t) for theta [n, 3] (float64 cuda)."""
-    torch = _torch()
+def _refine_args(theta, band, torch):
     theta = theta.contiguous()
     if theta.dtype != torch.float64 or not theta.is_cuda or theta.dim() != 2 or theta.shape[1] != 3:
         raise ValueError("theta must be a float64 cuda tensor of shape [n, 3]")
     n = theta.shape[0]
-    obj = torch.empty(n, dtype=torch.float64, device=theta.device)
-    grad = torch.empty((n, 3), dtype=torch.float64, device=theta.device)
     bp = None
     if band is not None:
         band = band.contiguous()
         if band.dtype != torch.int64 or not band.is_cuda or tuple(band.shape) != (n, 2):
             raise ValueError("band must be an int64 cuda tensor of shape [n, 2]")
         bp = band.data_ptr()
-    p = params(f_low)
-    check(_native.lib().mf_refine_triggers(segment.handle, ctypes.byref(p), theta.data_ptr(), n, bp,
-                                           obj.data_ptr(), grad.data_ptr(), _stream_ptr(stream)))
+    obj = torch.empty(n, dtype=torch.float64, device=theta.device)
+    grad = torch.empty((n, 3), dtype=torch.float64, device=theta.device)
+    return theta, n, bp, band, obj, grad
+
+
+def refine(segment, theta, band=None, f_low: float = 40.0, stream=None,
+           phase_mode: int = MF_PHASE_ANCHOR, row_seg=None):
+    """mf_refine_triggers: rho^2 and d rho^2 / d(m1, m2, t) for theta [n, 3] (float64 cuda).
+
+    segment: one Segment, or a list of Segments with row_seg (int32 cuda [n])
+    naming each row's segment (mf_refine_triggers_multi, one launch).
+    phase_mode: MF_PHASE_ANCHOR (FP64 anchors + FP32 Taylor, default) or
+    MF_PHASE_FP64 (FP64 phase at every bin)."""
+    torch = _torch()
+    theta, n, bp, band, obj, grad = _refine_args(theta, band, torch)
+    p = params(f_low, phase_mode=phase_mode)
+    if isinstance(segment, (list, tuple)):
+        if row_seg is None:
+            raise ValueError("row_seg is required with a list of segments")
+        row_seg = row_seg.contiguous()
+        if row_seg.dtype != torch.int32 or not row_seg.is_cuda or row_seg.numel() != n:
+            raise ValueError("row_seg must be an int32 cuda tensor of n entries")
+        arr = (ctypes.c_void_p * len(segment))(*[s.handle.value for s in segment])
+        check(_native.lib().mf_refine_triggers_multi(arr, len(segment), row_seg.data_ptr(), ctypes.byref(p),
+                                                     theta.data_ptr(), n, bp, obj.data_ptr(), grad.data_ptr(),
+                                                     _stream_ptr(stream)))
+    else:
+        check(_native.lib().mf_refine_triggers(segment.handle, ctypes.byref(p), theta.data_ptr(), n, bp,
+                                               obj.data_ptr(), grad.data_ptr(), _stream_ptr(stream)))
     return obj, grad
 
 
@@ -256,20 +278,21 @@ def _make_refine_fn():
     class RefineFn(torch.autograd.Function):
         """rho^2(m1, m2, t) of each trigger row with the hand-written adjoint.
 
-        forward(theta [n, 3] float64 cuda, segment, band=None, f_low=40) -> rho^2 [n];
-        backward returns grad_out[:, None] * d rho^2 / d theta (no gradient for
-        segment, band, f_low)."""
+        forward(theta [n, 3] float64 cuda, segment, band=None, f_low=40, row_seg=None)
+        -> rho^2 [n]; segment may be a list of Segments with row_seg (int32
+        cuda [n]).  backward returns grad_out[:, None] * d rho^2 / d theta (no
+        gradient for segment, band, f_low, row_seg)."""
 
         @staticmethod
-        def forward(ctx, theta, segment, band=None, f_low=40.0):
-            obj, grad = refine(segment, theta.detach(), band=band, f_low=f_low)
+        def forward(ctx, theta, segment, band=None, f_low=40.0, row_seg=None):
+            obj, grad = refine(segment, theta.detach(), band=band, f_low=f_low, row_seg=row_seg)
             ctx.save_for_backward(grad)
             return obj
 
         @staticmethod
         def backward(ctx, grad_out):
             (grad,) = ctx.saved_tensors
-            return grad_out[:, None] * grad, None, None, None
+            return grad_out[:, None] * grad, None, None, None, None
 
     return RefineFn
 

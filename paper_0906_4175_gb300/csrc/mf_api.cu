@@ -427,17 +427,7 @@ static SegDev seg_dev(const mf_segment_s *g) {
 // f-derivatives times df^n).
 static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
     if (b->params.phase_mode == MF_PHASE_FP64) return 0;
-    const double df = g->fs / (double)g->N;
-    int lg = 0;
-    while (lg < 8) {
-        const double D2 = (double)(1 << (lg + 1));
-        const double h = D2 / 2.0;
-        const double taylor = b->B5 * pow(df, 5) * h * h * h * h * h / 120.0;
-        const double mag = b->B1 * df * h;
-        if (taylor > 5e-7 || mag > 16.0) break;
-        ++lg;
-    }
-    return lg;
+    return anchor_log2D(b->B1, b->B5, g->fs / (double)g->N);
 }
 
 // templates in flight per batch (exchange ring of batch * N complex64)
@@ -941,14 +931,50 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
     if (r0) return r0;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const SegDev sd = seg_dev(seg);
-    const int bpr = refine_blocks_per_row();
+    const int bpr = refine_blocks_for(n, sm_count());
     double *partial = nullptr;
     cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * 8 * bpr * n, st);
-    if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, st);
+    if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, bpr, st);
     if (e == cudaSuccess) count_launches(2);
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers: %s",
+                       cudaGetErrorString(e));
+    return MF_OK;
+}
+
+extern "C" int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const int32_t *row_seg,
+                                        const mf_bank_params *params, const double *theta, int64_t n,
+                                        const int64_t *band, double *obj, double *grad, void *cuda_stream) {
+    if (!segs || !row_seg || !theta || !obj || !grad) return set_err(MF_EINVAL, "NULL argument");
+    if (n_seg < 1 || n_seg > kRefineMaxSegs)
+        return set_err(MF_EINVAL, "n_seg = %d outside [1, %d]", n_seg, kRefineMaxSegs);
+    if (n < 0) return set_err(MF_EINVAL, "n < 0");
+    if (n == 0) return MF_OK;
+    mf_bank_params p = params ? *params : default_params();
+    int rc = check_params(p);
+    if (rc) return rc;
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    std::vector<SegDev> sd((size_t)n_seg);
+    for (int s = 0; s < n_seg; ++s) {
+        if (!segs[s]) return set_err(MF_EINVAL, "segs[%d] is NULL", s);
+        if (segs[s]->device != cur) return set_err(MF_EINVAL, "segs[%d] lives on device %d", s, segs[s]->device);
+        sd[(size_t)s] = seg_dev(segs[s]);
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int bpr = refine_blocks_for(n, sm_count());
+    double *partial = nullptr;
+    cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * 8 * bpr * n, st);
+    if (e == cudaSuccess)
+        e = launch_refine_multi(sd.data(), n_seg, row_seg, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial,
+                                bpr, st);
+    if (e == cudaSuccess) count_launches(2);
+    if (partial) cudaFreeAsync(partial, st);
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers_multi: %s",
                        cudaGetErrorString(e));
     return MF_OK;
 }
@@ -1005,7 +1031,8 @@ extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *p
     // every partial sum the final kernel reads is written by the first kernel of
     // the same call, so nothing in the scratch needs clearing
     const SegDev sd = seg_dev(seg);
-    MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, (cudaStream_t)cuda_stream));
+    MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, kRefineStaticBpr,
+                          (cudaStream_t)cuda_stream));
     count_launches(2);
     return MF_OK;
 }

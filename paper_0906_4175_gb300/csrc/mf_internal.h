@@ -137,8 +137,15 @@ inline int64_t sort_tile_words(int64_t cap) { return ((cap + 2047) / 2048) * 256
 
 // refinement (mf_refine.cu)
 cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,
-                          const int64_t *band, double *obj, double *grad, double *partial, cudaStream_t st);
+                          const int64_t *band, double *obj, double *grad, double *partial, int bpr,
+                          cudaStream_t st);
+// segments of one mf_refine_triggers_multi call (kernel-parameter table)
+constexpr int kRefineMaxSegs = 256;
+cudaError_t launch_refine_multi(const SegDev *segs, int n_seg, const int32_t *row_seg, double f_low,
+                                int phase_mode, const double *theta, int64_t n, const int64_t *band, double *obj,
+                                double *grad, double *partial, int bpr, cudaStream_t st);
 int refine_blocks_per_row();
+int refine_blocks_for(int64_t n, int n_sm);   // blocks per row that fill the GPU
 
 // persistent scheduler (mf_persist.cu): segments with N >= 2^13
 cudaError_t launch_persistent(const PersistParams &P, int grid, cudaStream_t st);

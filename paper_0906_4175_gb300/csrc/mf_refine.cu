@@ -5,19 +5,42 @@
 //   rho^2 = |R|^2 P_tot / Q,  Q = P[k_hi] - P[k_lo]  (Eqs. 3-4; A cancels),
 //   d rho^2/dt  = (P_tot/Q) 2 Re(conj R * 2 pi i sum W e^{i phi} f_k),
 //   d rho^2/dm  = (P_tot/Q) 2 Re(conj R * (-2 pi i) sum W e^{i phi} dpsi_k/dm).
-// The phase is FP64 at every bin (psi in turns, reduced mod 1), sincos and the
-// products in FP32; per-thread FP32 partial sums, FP64 block and row totals in
-// a fixed order (deterministic).  The time is split t = j dt + tau so that
-// f_k t = (k j mod N)/N + k df tau with the first term exact in integers.
-#include "mf_fft.cuh"
-#include "mf_internal.h"
+// The time is split t = j dt + tau so that f_k t = (k j mod N)/N + k df tau,
+// the first term exact in integers and the second below a quarter turn.
+// Phase forms (the bank's phase_mode):
+//   anchors (default, also for the FP32-only mode): psi in FP64 at the centre
+//     of every D = 2^log2D bins, reduced mod 1, with its first four
+//     derivatives; FP32 quartic Taylor between anchors (the filter's form; D
+//     from the same remainder bound, per row);
+//   FP64 per bin: psi in FP64 at every bin, reduced mod 1.
+// sincos and the products in FP32; per-thread FP32 partial sums, FP64 block
+// and row totals in a fixed order (deterministic for a given blocks-per-row).
+#include "mf_filter.cuh"
 #include "mf_tmpl.cuh"
 
 namespace mf {
 
 constexpr int kRefThreads = 256;
-constexpr int kRefBlocksPerRow = 16;
+constexpr int kRefBlocksPerRow = 16;          // minimum (and the allocation-free entry point's)
+constexpr int kRefMaxBlocksPerRow = 256;
+constexpr int kRefAnchorsPerChunk = kRefThreads;
 int refine_blocks_per_row() { return kRefBlocksPerRow; }
+
+// The segments of one call, passed by value as a kernel parameter: row i
+// reads segment row_seg[i] (0 when row_seg is NULL).
+template <int NS>
+struct SegTable {
+    SegDev s[NS];
+    int n;
+};
+
+int refine_blocks_for(int64_t n, int n_sm) {
+    // about four resident blocks per SM over the whole call
+    int64_t b = (4 * (int64_t)n_sm + n - 1) / (n > 0 ? n : 1);
+    if (b < kRefBlocksPerRow) b = kRefBlocksPerRow;
+    if (b > kRefMaxBlocksPerRow) b = kRefMaxBlocksPerRow;
+    return (int)b;
+}
 
 struct RefRow {
     double c[4];     // psi coefficients for u^1, u^2, u^3, u^5 (turns)
@@ -26,10 +49,11 @@ struct RefRow {
     double pratio;   // P_tot / Q
     int64_t k_lo, k_hi;
     uint32_t j;      // nearest sample (mod N)
+    int log2D;       // anchor spacing (0: FP64 phase at every bin)
 };
 
-__device__ void refine_row_setup(const SegDev &seg, double f_low, const double *theta, const int64_t *band,
-                                 int64_t i, RefRow &r) {
+__device__ void refine_row_setup(const SegDev &seg, double f_low, int anchored, const double *theta,
+                                 const int64_t *band, int64_t i, RefRow &r) {
     const double m1 = theta[3 * i], m2 = theta[3 * i + 1], t = theta[3 * i + 2];
     double rec[kTmplStride];
     template_constants(m1, m2, rec);
@@ -62,46 +86,109 @@ __device__ void refine_row_setup(const SegDev &seg, double f_low, const double *
     if (j < 0) j += seg.N;
     r.j = (uint32_t)j;
     r.dftau = seg.df * tau;
+    r.log2D = 0;
+    if (anchored) {
+        const double f0 = (double)lo * seg.df;
+        r.log2D = anchor_log2D(psi_deriv_bound_u(r.c, f0, 1), psi_deriv_bound_u(r.c, f0, 5), seg.df);
+    }
 }
 
-__global__ void __launch_bounds__(kRefThreads)
-    k_refine_partial(SegDev seg, double f_low, const double *__restrict__ theta, const int64_t *__restrict__ band,
-                     double *__restrict__ partial) {
-    __shared__ RefRow row;
-    __shared__ double red[8][kRefThreads / 32];
-    const int64_t i = blockIdx.y;
-    if (threadIdx.x == 0) refine_row_setup(seg, f_low, theta, band, i, row);
-    __syncthreads();
-    const int64_t K = row.k_hi - row.k_lo;
-    const int64_t chunk = (K + gridDim.x - 1) / gridDim.x;
-    const int64_t k0 = row.k_lo + (int64_t)blockIdx.x * chunk;
-    const int64_t k1 = (k0 + chunk < row.k_hi) ? k0 + chunk : row.k_hi;
-    const uint32_t nmask = (uint32_t)(seg.N - 1);
-    const double invN = 1.0 / (double)seg.N;
+struct RefAcc {
     float ar = 0.f, ai = 0.f, fr = 0.f, fi = 0.f, ar1 = 0.f, ai1 = 0.f, ar2 = 0.f, ai2 = 0.f;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        const double f = (double)k * seg.df;
-        // u = f^(-1/3): FP32 seed refined by one FP64 Newton step
-        double u = (double)rcbrtf((float)f);
-        u = u * (4.0 - f * u * u * u) / 3.0;
-        const double psi = -0.125 + u * (row.c[0] + u * (row.c[1] + u * (row.c[2] + u * u * row.c[3])));
-        const double tt = (double)(((uint32_t)k * row.j) & nmask) * invN + (double)k * row.dftau;
-        double ph = tt - psi;
-        ph -= rint(ph);
+    // one bin: phase (turns, reduced to [-1/2, 1/2]) and the FP32 factors
+    __device__ __forceinline__ void add(const RefRow &row, const float2 w, float ph, float ff, float uf) {
         float s, c;
-        __sincosf(6.283185307179586f * (float)ph, &s, &c);
-        const float2 w = __ldg(&seg.W[k]);
+        __sincosf(6.283185307179586f * ph, &s, &c);
         const float qr = w.x * c - w.y * s, qi = w.x * s + w.y * c;
-        const float uf = (float)u, uf2 = uf * uf, uf3 = uf2 * uf, uf5 = uf3 * uf2;
+        const float uf2 = uf * uf, uf3 = uf2 * uf, uf5 = uf3 * uf2;
         const float g1 = row.d1[0] * uf + row.d1[1] * uf2 + row.d1[2] * uf3 + row.d1[3] * uf5;
         const float g2 = row.d2[0] * uf + row.d2[1] * uf2 + row.d2[2] * uf3 + row.d2[3] * uf5;
-        const float ff = (float)f;
         ar += qr; ai += qi;
         fr = fmaf(qr, ff, fr); fi = fmaf(qi, ff, fi);
         ar1 = fmaf(qr, g1, ar1); ai1 = fmaf(qi, g1, ai1);
         ar2 = fmaf(qr, g2, ar2); ai2 = fmaf(qi, g2, ai2);
     }
-    double v[8] = {ar, ai, fr, fi, ar1, ai1, ar2, ai2};
+};
+
+// segment of row i, or -1 when row_seg names no segment of the table
+template <int NS>
+__device__ __forceinline__ int row_segment(const SegTable<NS> &tab, const int32_t *row_seg, int64_t i) {
+    const int s = row_seg ? row_seg[i] : 0;
+    return (s >= 0 && s < tab.n) ? s : -1;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kRefThreads)
+    k_refine_partial(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg, double f_low,
+                     int anchored, const double *__restrict__ theta, const int64_t *__restrict__ band,
+                     double *__restrict__ partial) {
+    __shared__ RefRow row;
+    __shared__ double red[8][kRefThreads / 32];
+    __shared__ float4 sanc[kRefAnchorsPerChunk];
+    __shared__ float sanc4[kRefAnchorsPerChunk];
+    const int64_t i = blockIdx.y;
+    const int si = row_segment(tab, row_seg, i);
+    if (si < 0) {   // invalid segment index: an empty sum (the final kernel reports NaN)
+        if (threadIdx.x < 8) partial[(i * gridDim.x + blockIdx.x) * 8 + threadIdx.x] = 0.0;
+        return;
+    }
+    const SegDev &seg = tab.s[si];
+    if (threadIdx.x == 0) refine_row_setup(seg, f_low, anchored, theta, band, i, row);
+    __syncthreads();
+    const uint32_t nmask = (uint32_t)(seg.N - 1);
+    RefAcc acc;
+    if (row.log2D > 0) {
+        // this block's anchor groups g (bins [g D, g D + D) clipped to the band)
+        const int lg = row.log2D;
+        const int64_t g_lo = row.k_lo >> lg, g_hi = (row.k_hi - 1) >> lg;
+        const int64_t ng = row.k_hi > row.k_lo ? g_hi - g_lo + 1 : 0;
+        const int64_t gpb = (ng + gridDim.x - 1) / gridDim.x;
+        const int64_t gb0 = g_lo + (int64_t)blockIdx.x * gpb;
+        const int64_t gb1 = (gb0 + gpb < g_lo + ng) ? gb0 + gpb : g_lo + ng;
+        const float invN = 1.0f / (float)seg.N;
+        const float dftau = (float)row.dftau, dff = (float)seg.df;
+        const int half = (1 << lg) >> 1;
+        for (int64_t gc = gb0; gc < gb1; gc += kRefAnchorsPerChunk) {
+            const int64_t gce = (gc + kRefAnchorsPerChunk < gb1) ? gc + kRefAnchorsPerChunk : gb1;
+            if (gc + threadIdx.x < gce)
+                anchor_record(row.c[0], row.c[1], row.c[2], row.c[3], gc + threadIdx.x, lg, seg.df,
+                              sanc[threadIdx.x], sanc4[threadIdx.x]);
+            __syncthreads();
+            int64_t kb0 = gc << lg, kb1 = gce << lg;
+            if (kb0 < row.k_lo) kb0 = row.k_lo;
+            if (kb1 > row.k_hi) kb1 = row.k_hi;
+            for (int64_t k = kb0 + threadIdx.x; k < kb1; k += kRefThreads) {
+                const int a = (int)((k >> lg) - gc);
+                const float4 an = sanc[a];
+                const float d = (float)(int)((k & ((1 << lg) - 1)) - half);
+                const float psi = an.x + d * (an.y + d * (an.z + d * (an.w + d * sanc4[a])));
+                const float tt = (float)(((uint32_t)k * row.j) & nmask) * invN + (float)k * dftau;
+                float ph = tt - psi;
+                ph -= rintf(ph);
+                const float ff = (float)k * dff;
+                acc.add(row, __ldg(&seg.W[k]), ph, ff, rcbrtf(ff));
+            }
+            __syncthreads();
+        }
+    } else {
+        const int64_t K = row.k_hi - row.k_lo;
+        const int64_t chunk = (K + gridDim.x - 1) / gridDim.x;
+        const int64_t k0 = row.k_lo + (int64_t)blockIdx.x * chunk;
+        const int64_t k1 = (k0 + chunk < row.k_hi) ? k0 + chunk : row.k_hi;
+        const double invN = 1.0 / (double)seg.N;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            const double f = (double)k * seg.df;
+            // u = f^(-1/3): FP32 seed refined by one FP64 Newton step
+            double u = (double)rcbrtf((float)f);
+            u = u * (4.0 - f * u * u * u) * (1.0 / 3.0);
+            const double psi = -0.125 + u * (row.c[0] + u * (row.c[1] + u * (row.c[2] + u * u * row.c[3])));
+            const double tt = (double)(((uint32_t)k * row.j) & nmask) * invN + (double)k * row.dftau;
+            double ph = tt - psi;
+            ph -= rint(ph);
+            acc.add(row, __ldg(&seg.W[k]), (float)ph, (float)f, (float)u);
+        }
+    }
+    double v[8] = {acc.ar, acc.ai, acc.fr, acc.fi, acc.ar1, acc.ai1, acc.ar2, acc.ai2};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -117,13 +204,23 @@ __global__ void __launch_bounds__(kRefThreads)
     }
 }
 
-__global__ void k_refine_final(SegDev seg, double f_low, const double *__restrict__ theta,
-                               const int64_t *__restrict__ band, const double *__restrict__ partial, int bpr,
-                               int64_t n, double *__restrict__ obj, double *__restrict__ grad) {
+template <int NS>
+__global__ void k_refine_final(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg,
+                               double f_low, const double *__restrict__ theta, const int64_t *__restrict__ band,
+                               const double *__restrict__ partial, int bpr, int64_t n, double *__restrict__ obj,
+                               double *__restrict__ grad) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int si = row_segment(tab, row_seg, i);
+    if (si < 0) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        obj[i] = nan;
+        grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = nan;
+        return;
+    }
+    const SegDev &seg = tab.s[si];
     RefRow row;
-    refine_row_setup(seg, f_low, theta, band, i, row);
+    refine_row_setup(seg, f_low, 0, theta, band, i, row);
     double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < bpr; ++b)
         for (int q = 0; q < 8; ++q) a[q] += partial[(i * bpr + b) * 8 + q];
@@ -137,15 +234,43 @@ __global__ void k_refine_final(SegDev seg, double f_low, const double *__restric
     grad[3 * i + 2] = two_pi * pr * 2.0 * (Ri * a[2] - Rr * a[3]);
 }
 
-cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,
-                          const int64_t *band, double *obj, double *grad, double *partial, cudaStream_t st) {
-    (void)phase_mode;
-    k_refine_partial<<<dim3(kRefBlocksPerRow, (unsigned)n), kRefThreads, 0, st>>>(seg, f_low, theta, band, partial);
+template <int NS>
+static cudaError_t launch_refine_table(const SegTable<NS> &tab, const int32_t *row_seg, double f_low,
+                                       int phase_mode, const double *theta, int64_t n, const int64_t *band,
+                                       double *obj, double *grad, double *partial, int bpr, cudaStream_t st) {
+    const int anchored = phase_mode == MF_PHASE_FP64 ? 0 : 1;
+    k_refine_partial<NS><<<dim3((unsigned)bpr, (unsigned)n), kRefThreads, 0, st>>>(tab, row_seg, f_low, anchored,
+                                                                                   theta, band, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_refine_final<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(seg, f_low, theta, band, partial,
-                                                                 kRefBlocksPerRow, n, obj, grad);
+    k_refine_final<NS><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, row_seg, f_low, theta, band, partial, bpr,
+                                                                     n, obj, grad);
     return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,
+                          const int64_t *band, double *obj, double *grad, double *partial, int bpr,
+                          cudaStream_t st) {
+    SegTable<1> tab;
+    tab.s[0] = seg;
+    tab.n = 1;
+    return launch_refine_table(tab, nullptr, f_low, phase_mode, theta, n, band, obj, grad, partial, bpr, st);
+}
+
+cudaError_t launch_refine_multi(const SegDev *segs, int n_seg, const int32_t *row_seg, double f_low,
+                                int phase_mode, const double *theta, int64_t n, const int64_t *band, double *obj,
+                                double *grad, double *partial, int bpr, cudaStream_t st) {
+    if (n_seg < 1 || n_seg > kRefineMaxSegs) return cudaErrorInvalidValue;
+    if (n_seg <= 8) {
+        SegTable<8> tab;
+        for (int s = 0; s < n_seg; ++s) tab.s[s] = segs[s];
+        tab.n = n_seg;
+        return launch_refine_table(tab, row_seg, f_low, phase_mode, theta, n, band, obj, grad, partial, bpr, st);
+    }
+    SegTable<kRefineMaxSegs> tab;
+    for (int s = 0; s < n_seg; ++s) tab.s[s] = segs[s];
+    tab.n = n_seg;
+    return launch_refine_table(tab, row_seg, f_low, phase_mode, theta, n, band, obj, grad, partial, bpr, st);
 }
 
 cudaError_t refine_kernel_attributes() { return cudaSuccess; }

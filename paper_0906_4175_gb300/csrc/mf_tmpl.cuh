@@ -60,4 +60,41 @@ __host__ __device__ inline void template_mass_derivs(double m1, double m2, doubl
     }
 }
 
+// Bound on |d^n psi / df^n| (turns / Hz^n) at frequency f: the sum of the
+// magnitudes of the n-th derivatives of the four terms c_p u^p, u = f^(-1/3),
+//   d^n (f^(-p/3)) / df^n = (-1)^n (p/3)(p/3 + 1)...(p/3 + n - 1) u^(p + 3n).
+// Every term decreases with f, so the value at the lowest band frequency
+// bounds the whole band.
+__host__ __device__ inline double psi_deriv_bound_u(const double *c4, double f, int n) {
+    const int pw[4] = {1, 2, 3, 5};
+    const double u = 1.0 / cbrt(f);
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        const double q = pw[i] / 3.0;
+        double fac = 1.0;
+        for (int m = 0; m < n; ++m) fac *= (q + m);
+        double up = 1.0;
+        for (int e = 0; e < pw[i] + 3 * n; ++e) up *= u;
+        s += fabs(c4[i]) * fac * up;
+    }
+    return s;
+}
+
+// Anchor spacing D = 2^log2D (bins) for the FP32 quartic Taylor expansion of
+// psi about FP64 anchors at the centre of every D bins: the largest D <= 256
+// whose fifth-order remainder B5 df^5 (D/2)^5 / 120 stays <= 5e-7 turns and
+// whose linear term B1 df D/2 stays <= 16 turns (bounds at the band's lowest
+// frequency).
+__host__ __device__ inline int anchor_log2D(double B1, double B5, double df) {
+    int lg = 0;
+    while (lg < 8) {
+        const double h = (double)(1 << (lg + 1)) / 2.0;
+        const double taylor = B5 * df * df * df * df * df * h * h * h * h * h / 120.0;
+        const double mag = B1 * df * h;
+        if (taylor > 5e-7 || mag > 16.0) break;
+        ++lg;
+    }
+    return lg;
+}
+
 }  // namespace mf

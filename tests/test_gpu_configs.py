@@ -217,7 +217,7 @@ def coarse_triggers(tr, injections, N, fs, window_s=2.0):
     return out
 
 
-def ascend(mf, seg, theta0, steps=20, rel_m=5e-3, step_t=2e-4):
+def ascend(mf, seg, theta0, steps=20, rel_m=5e-3, step_t=2e-4, row_seg=None):
     """Adam ascent of rho^2 on (m1, m2, t) through RefineFn.  The optimiser
     works on x = theta / scale (scale = rel_m * m for the masses, step_t for
     t), so one unit-rate Adam step moves each coordinate by about its scale.
@@ -231,11 +231,11 @@ def ascend(mf, seg, theta0, steps=20, rel_m=5e-3, step_t=2e-4):
     best_J = torch.full((th0.shape[0],), -1.0, dtype=torch.float64, device="cuda")
     for k in range(steps + 1):
         th = x * sc
-        J = mf.RefineFn.apply(th, seg)
+        J = mf.RefineFn.apply(th, seg, None, 40.0, row_seg)
         with torch.no_grad():
             better = J > best_J
             best_J = torch.where(better, J.detach(), best_J)
-            best_th[better] = th.detach()[better]
+            best_th = torch.where(better[:, None], th.detach(), best_th)
         if k == steps:
             break
         opt.zero_grad()
@@ -280,3 +280,37 @@ def test_refinement_of_coarse_triggers(mf):
         gs = np.abs(ref_grad).max(axis=0)
         assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * gs)
         assert np.all(np.sqrt(obj) >= rho0 * (1 - 1e-4)), (np.sqrt(obj), rho0)
+
+
+def test_refine_multi_segment_rows(mf):
+    """mf_refine_triggers_multi: rows of three segments (two lengths) in one
+    launch equal mf_refine_triggers on each row's own segment (to rounding of
+    the grouped partial sums); a row naming no segment gets NaN."""
+    import torch
+    segs, thetas, rs = [], [], []
+    for si, (lg, seed) in enumerate([(14, 1), (15, 2), (14, 3)]):
+        N, fs = 1 << lg, 4096.0
+        inj = np.zeros(1, dtype=oracle.INJ_DTYPE)
+        inj[0] = (1.6 + 0.1 * si, 1.3, 14.0, 1000 + 77 * si, 0.2)
+        spec = workloads.SegmentSpec(N, fs, 900 + seed, inj)
+        s32, _ = oracle_segment(spec)
+        segs.append(mf.Segment(torch.from_numpy(s32).cuda(), fs))
+        t0 = ((N - int(inj[0]["j0"])) % N) / fs
+        for d in (0.0, 0.4, -1.3):
+            thetas.append([1.6 + 0.1 * si + 0.01 * d, 1.3, t0 + d / fs])
+            rs.append(si)
+    order = np.random.default_rng(4).permutation(len(rs))
+    theta = torch.tensor(np.array(thetas)[order], dtype=torch.float64, device="cuda")
+    row_seg = torch.tensor(np.array(rs, dtype=np.int32)[order], device="cuda")
+    obj, grad = mf.refine(segs, theta, row_seg=row_seg)
+    for si in range(3):
+        sel = torch.nonzero(row_seg == si).flatten()
+        o1, g1 = mf.refine(segs[si], theta[sel])
+        # FP32 per-thread sums over differently grouped bins: agreement to FP32 rounding
+        assert torch.allclose(obj[sel], o1, rtol=2e-5, atol=1e-6)
+        assert torch.allclose(grad[sel], g1, rtol=1e-4, atol=1e-4 * float(g1.abs().max()))
+    bad = row_seg.clone()
+    bad[0] = 7
+    ob, gb = mf.refine(segs, theta, row_seg=bad)
+    assert torch.isnan(ob[0]) and torch.all(torch.isnan(gb[0]))
+    assert torch.equal(ob[1:], obj[1:])

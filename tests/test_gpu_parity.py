@@ -269,12 +269,13 @@ def test_refine_matches_oracle(mf):
     lo_hi = [oracle.band(N, fs, 40.0, oracle.f_isco(a, b)) for a, b, _ in theta]
     ref_obj, ref_grad = oracle.refine(theta, s64, fs, 40.0, bands=np.array(lo_hi))
     th = torch.tensor(theta, dtype=torch.float64, device="cuda")
-    obj, grad = mf.refine(seg, th)
-    obj = obj.cpu().numpy()
-    grad = grad.cpu().numpy()
-    assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < 2e-4), (obj, ref_obj)
     scale = np.abs(ref_grad).max(axis=0)
-    assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * scale), (grad, ref_grad)
+    for mode in (mf.MF_PHASE_FP64, mf.MF_PHASE_ANCHOR):     # per-bin FP64 phase, then the default anchors
+        obj, grad = mf.refine(seg, th, phase_mode=mode)
+        obj = obj.cpu().numpy()
+        grad = grad.cpu().numpy()
+        assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < 2e-4), (mode, obj, ref_obj)
+        assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * scale), (mode, grad, ref_grad)
     # explicit band gives the same as the default band at the same masses
     band = torch.tensor(np.array(lo_hi), dtype=torch.int64, device="cuda")
     obj2, grad2 = mf.refine(seg, th, band=band)
