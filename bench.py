@@ -61,6 +61,21 @@ def _args():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (every rank gets it): the job's time is
+    its slowest rank's."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, ms: float) -> float:
+    """Units all ranks processed (each rank filters its own replica) per
+    second of the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -662,11 +677,9 @@ def main():
     clocks = sampler.stop()
     assert bank.check() == 0
     if dist:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+        tot_ms = max_over_ranks(tot_ms, dist, dev)
         dist.barrier()
-    value = world * wl.n_templates * args.steps / (tot_ms / 1e3)
+    value = whole_job_rate(world, wl.n_templates * args.steps, tot_ms)
 
     # roofline of the dominant kernel (largest share of the filter's device time)
     stages = {k: v for k, v in prof.items() if v[2] > 0}
@@ -712,10 +725,8 @@ def main():
             d2h.append(peaks_h.numel() * 4 + 8 + n * 24)
     e2e_tot = sum(e2e_ms) if e2e_ms else float("nan")
     if dist:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e = {"value": world * wl.n_templates * len(e2e_ms) / (e2e_tot / 1e3) if e2e_ms else None, "unit": UNIT,
+        e2e_tot = max_over_ranks(e2e_tot, dist, dev)
+    e2e = {"value": whole_job_rate(world, wl.n_templates * len(e2e_ms), e2e_tot) if e2e_ms else None, "unit": UNIT,
            "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)) if d2h else 0,
            "includes": "pinned host s -> mf_segment_refresh (H2D inside), mf_filter_bank, D2H peaks + n_trig + triggers"}
 
