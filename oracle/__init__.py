@@ -110,6 +110,9 @@ def lib():
             L.or_refine.argtypes = [_P, _I64, _P, _I64, ctypes.c_double, ctypes.c_double, _P,
                                     ctypes.c_double, ctypes.c_double, _P, _P, _P]
             L.or_refine.restype = ctypes.c_int
+            L.or_chisq_series.argtypes = [ctypes.c_double, ctypes.c_double, _P, _P, _P, _I64, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P]
+            L.or_chisq_series.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -211,6 +214,28 @@ def filter_template(m1, m2, st: np.ndarray, S: np.ndarray, N: int, fs: float, f_
     if rc != 0:
         raise RuntimeError("or_filter_template failed: %d" % rc)
     return dict(z=z_re + 1j * z_im, rho=rho, sigma=sigma.value, k_lo=lo.value, k_hi=hi.value)
+
+
+def chisq_series(m1, m2, st: np.ndarray, S: np.ndarray, N: int, fs: float, f_low: float, p: int = 16,
+                 edges=None):
+    """Eq. (5) for one template: chi^2 at every sample with p equal-sigma^2
+    sub-bands (Sec. 1.2).  edges: optional p+1 band edges replacing the
+    equal-share rule.  Returns dict(chisq, rho, edges, sig2_l)."""
+    st_re = _f64(st.real)
+    st_im = _f64(st.imag)
+    S = _f64(S)
+    chisq = np.empty(N)
+    rho = np.empty(N)
+    e_out = np.empty(p + 1, dtype=np.int64)
+    sig2_l = np.empty(p)
+    e_in = None if edges is None else np.ascontiguousarray(edges, dtype=np.int64)
+    if e_in is not None and e_in.size != p + 1:
+        raise ValueError("edges must hold p+1 values")
+    rc = lib().or_chisq_series(float(m1), float(m2), _ptr(st_re), _ptr(st_im), _ptr(S), N, fs, f_low, p,
+                               _ptr(e_in), _ptr(chisq), _ptr(rho), _ptr(e_out), _ptr(sig2_l))
+    if rc != 0:
+        raise RuntimeError("or_chisq_series failed: %d" % rc)
+    return dict(chisq=chisq, rho=rho, edges=e_out, sig2_l=sig2_l)
 
 
 def filter_bank(m1, m2, s, fs: float, f_low: float, thr: float, psd=None,

@@ -21,6 +21,7 @@
  *   z_j   = 4 df sum_band h~_k conj(s~_k) / S_k exp(+2 pi i j k / N)   Eq. (1)
  *   sigma^2 = 4 df sum_band |h~_k|^2 / S_k                       Eq. (4)
  *   rho_j = |z_j| / sigma                                        Eq. (3)
+ *   chi^2_j = (p / sigma^2) sum_l |z_l,j - z_j / p|^2            Eq. (5), p sub-bands of equal sigma^2 share
  *
  * Readings where the paper is silent (the 2PN phase formula, the ISCO
  * frequency, bin-edge rules, amplitude constant, PSD scale) are stated next to
@@ -227,6 +228,98 @@ int or_filter_template(double m1, double m2, const double *st_re, const double *
     if (k_lo_out) *k_lo_out = k_lo;
     if (k_hi_out) *k_hi_out = k_hi;
     free(h_re); free(h_im);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (5), the chi^2 consistency test of Sec. 1.2: the band integral of     */
+/* Eq. (1) is split into p sub-bands that contribute equally to sigma^2, giving */
+/* p series z_l(t), and                                                     */
+/*   chi^2(t_j) = (p / sigma^2) sum_l |z_l(t_j) - z(t_j)/p|^2.              */
+/* Band edges (the paper gives no discretisation): with                     */
+/*   c(k) = sum_{k_lo <= k' < k} |h~_k'|^2 / S_k',                          */
+/* b_0 = k_lo, b_p = k_hi and, for 0 < l < p, b_l = the smallest k in        */
+/* [k_lo, k_hi] with c(k) >= (l/p) c(k_hi).  Sub-band l is b_l <= k < b_{l+1}.*/
+/* edges_in (optional, p+1 values) replaces that rule by given edges.        */
+/* Outputs: chisq_j and rho_j for j = 0..N-1, edges (p+1), sigma_l^2 (p).    */
+/* ------------------------------------------------------------------------ */
+int or_chisq_series(double m1, double m2, const double *st_re, const double *st_im,
+                    const double *S, int64_t N, double fs, double f_low, int p,
+                    const int64_t *edges_in, double *chisq, double *rho,
+                    int64_t *edges_out, double *sig2_l_out)
+{
+    if (p < 1) return -1;
+    double df = fs / (double)N;
+    int64_t nh = N / 2 + 1;
+    double *h_re = (double *)malloc(sizeof(double) * (size_t)nh);
+    double *h_im = (double *)malloc(sizeof(double) * (size_t)nh);
+    double *c = (double *)malloc(sizeof(double) * (size_t)(nh + 1));
+    double *z_re = (double *)malloc(sizeof(double) * (size_t)N);
+    double *z_im = (double *)malloc(sizeof(double) * (size_t)N);
+    double *zl_re = (double *)malloc(sizeof(double) * (size_t)N);
+    double *zl_im = (double *)malloc(sizeof(double) * (size_t)N);
+    int64_t *b = (int64_t *)malloc(sizeof(int64_t) * (size_t)(p + 1));
+    int rc = 0;
+    if (!h_re || !h_im || !c || !z_re || !z_im || !zl_re || !zl_im || !b) { rc = -2; goto done; }
+    int64_t k_lo, k_hi;
+    or_htilde(m1, m2, N, fs, f_low, h_re, h_im, &k_lo, &k_hi);
+
+    /* cumulative |h|^2/S over the band: c[k - k_lo] = c(k) */
+    c[0] = 0.0;
+    for (int64_t k = k_lo; k < k_hi; ++k)
+        c[k - k_lo + 1] = c[k - k_lo] + (h_re[k] * h_re[k] + h_im[k] * h_im[k]) / S[k];
+    double ctot = c[k_hi - k_lo];
+    if (edges_in) {
+        for (int l = 0; l <= p; ++l) b[l] = edges_in[l];
+    } else {
+        b[0] = k_lo;
+        b[p] = k_hi;
+        for (int l = 1; l < p; ++l) {
+            double target = ((double)l / (double)p) * ctot;
+            int64_t k = k_lo;
+            while (k < k_hi && c[k - k_lo] < target) ++k;
+            b[l] = k;
+        }
+    }
+    double sig2 = 4.0 * df * ctot;                      /* Eq. (4) */
+
+    /* z over the whole band (Eq. 1) */
+    for (int64_t k = 0; k < N; ++k) { z_re[k] = 0.0; z_im[k] = 0.0; }
+    for (int64_t k = k_lo; k < k_hi; ++k) {
+        double br = st_re[k], bi = -st_im[k];
+        z_re[k] = (h_re[k] * br - h_im[k] * bi) / S[k];
+        z_im[k] = (h_re[k] * bi + h_im[k] * br) / S[k];
+    }
+    rc = or_fft(z_re, z_im, N, +1);
+    if (rc) goto done;
+    for (int64_t j = 0; j < N; ++j) {
+        z_re[j] *= 4.0 * df; z_im[j] *= 4.0 * df;
+        if (rho) rho[j] = sqrt(z_re[j] * z_re[j] + z_im[j] * z_im[j]) / sqrt(sig2);
+        chisq[j] = 0.0;
+    }
+    /* z_l over each sub-band, and the sum of |z_l - z/p|^2 */
+    for (int l = 0; l < p; ++l) {
+        double s2 = 0.0;
+        for (int64_t k = 0; k < N; ++k) { zl_re[k] = 0.0; zl_im[k] = 0.0; }
+        for (int64_t k = b[l]; k < b[l + 1]; ++k) {
+            double br = st_re[k], bi = -st_im[k];
+            zl_re[k] = (h_re[k] * br - h_im[k] * bi) / S[k];
+            zl_im[k] = (h_re[k] * bi + h_im[k] * br) / S[k];
+            s2 += (h_re[k] * h_re[k] + h_im[k] * h_im[k]) / S[k];
+        }
+        if (sig2_l_out) sig2_l_out[l] = 4.0 * df * s2;
+        rc = or_fft(zl_re, zl_im, N, +1);
+        if (rc) goto done;
+        for (int64_t j = 0; j < N; ++j) {
+            double dr = 4.0 * df * zl_re[j] - z_re[j] / (double)p;
+            double di = 4.0 * df * zl_im[j] - z_im[j] / (double)p;
+            chisq[j] += dr * dr + di * di;
+        }
+    }
+    for (int64_t j = 0; j < N; ++j) chisq[j] *= (double)p / sig2;   /* Eq. (5) */
+    if (edges_out) for (int l = 0; l <= p; ++l) edges_out[l] = b[l];
+done:
+    free(h_re); free(h_im); free(c); free(z_re); free(z_im); free(zl_re); free(zl_im); free(b);
     return rc;
 }
 

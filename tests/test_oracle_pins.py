@@ -403,3 +403,85 @@ def test_refine_stationary_at_true_parameters(oracle_lib):
     # scale of the gradient one sample or 0.01 Msun away
     _, g_off = oracle_lib.refine_objective(1.61, 1.4, t + 0.5 / fs, st, S, N, fs, lo, hi)
     assert np.all(np.abs(g) < 1e-6 * np.abs(g_off).max())
+
+
+# ---------------------------------------------------------------------------
+# Eq. (5), the chi^2 consistency test (Sec. 1.2)
+# ---------------------------------------------------------------------------
+def _chisq_case(oracle_lib, N, fs, seed, m=(1.5, 1.4), inj=None, noise_scale=1.0, p=16, edges=None):
+    S = oracle_lib.psd_bins(N, fs)
+    g = np.random.default_rng([seed, 77]).standard_normal(2 * (N // 2))
+    s = oracle_lib.synth(g, N, fs, 40.0, inj, noise_scale=noise_scale)
+    st = oracle_lib.data_spectrum(s, fs)
+    return oracle_lib.chisq_series(m[0], m[1], st, S, N, fs, 40.0, p, edges=edges)
+
+
+@pytest.mark.parametrize("p", [4, 16])
+def test_chisq_noise_mean_is_2p_minus_2(oracle_lib, p):
+    """In stationary Gaussian noise E[chi^2] = 2p - 2 for ANY partition of the
+    band into p disjoint sub-bands: the bins are independent, so with
+    E|z_l|^2 = 2 sigma_l^2 and no cross terms, (p/sigma^2) sum_l E|z_l - z/p|^2
+    = (p/sigma^2)[2 sigma^2 (1 - 2/p) + 2 sigma^2 / p] = 2p - 2 (the paper's
+    2p - 2 degrees of freedom).  Checked on the mean over 24 realisations."""
+    means = [float(_chisq_case(oracle_lib, 1 << 13, 4096.0, seed, p=p)["chisq"].mean()) for seed in range(24)]
+    m = float(np.mean(means))
+    se = float(np.std(means, ddof=1) / np.sqrt(len(means)))
+    assert se < 0.05 * (2 * p - 2)
+    assert abs(m - (2 * p - 2)) < 4 * se + 1e-9, (m, se)
+
+
+def test_chisq_single_band_is_zero(oracle_lib):
+    r = _chisq_case(oracle_lib, 1 << 12, 4096.0, 3, p=1)
+    assert np.max(np.abs(r["chisq"])) < 1e-20 * max(1.0, float(np.max(r["rho"]) ** 2)) + 1e-24
+
+
+def test_chisq_band_edges_split_sigma2_equally(oracle_lib):
+    """Edges run from k_lo to k_hi, increase, and each sub-band's sigma_l^2 is
+    sigma^2/p to within one bin's |h|^2/S (the discretisation of the rule)."""
+    N, fs, p = 1 << 14, 4096.0, 16
+    r = _chisq_case(oracle_lib, N, fs, 5, p=p)
+    h, (lo, hi) = oracle_lib.htilde(1.5, 1.4, N, fs, 40.0)
+    S = oracle_lib.psd_bins(N, fs)
+    q = np.abs(h[lo:hi]) ** 2 / S[lo:hi]
+    e = r["edges"]
+    assert e[0] == lo and e[-1] == hi and np.all(np.diff(e) > 0)
+    df = fs / N
+    sig2 = 4 * df * q.sum()
+    assert np.isclose(r["sig2_l"].sum(), sig2, rtol=1e-12)
+    assert np.max(np.abs(r["sig2_l"] - sig2 / p)) <= 4 * df * q.max() * (1 + 1e-9)
+
+
+def test_chisq_matched_injection_closed_form(oracle_lib):
+    """Noiseless data = the template itself at SNR rho0 coalescing at j0: at
+    the peak z_l = conj(a) sigma_l^2 and z = conj(a) sigma^2 with |a| sigma =
+    rho0, so chi^2 = p rho0^2 sum_l (sigma_l^2 - sigma^2/p)^2 / sigma^4."""
+    N, fs, p = 1 << 14, 4096.0, 16
+    inj = np.zeros(1, dtype=oracle_lib.INJ_DTYPE)
+    inj[0] = (1.5, 1.4, 12.0, 3000, 0.7)
+    r = _chisq_case(oracle_lib, N, fs, 1, inj=inj, noise_scale=0.0, p=p)
+    jp = (N - 3000) % N
+    assert int(np.argmax(r["rho"])) == jp and abs(r["rho"][jp] - 12.0) < 1e-9
+    s2 = r["sig2_l"]
+    sig2 = s2.sum()
+    expect = p * 144.0 * np.sum((s2 - sig2 / p) ** 2) / sig2 ** 2
+    assert abs(r["chisq"][jp] - expect) <= 1e-9 * max(expect, 1e-6)
+
+
+def test_chisq_mismatched_signal_scales_with_snr_squared(oracle_lib):
+    """A noiseless signal from another template: chi^2 is large at the peak and
+    homogeneous of degree 2 in the signal amplitude (z_l and z scale by a)."""
+    N, fs, p = 1 << 14, 4096.0, 16
+    res = []
+    for snr in (8.0, 16.0):
+        inj = np.zeros(1, dtype=oracle_lib.INJ_DTYPE)
+        inj[0] = (2.0, 1.1, snr, 2000, 0.0)
+        res.append(_chisq_case(oracle_lib, N, fs, 2, m=(1.5, 1.4), inj=inj, noise_scale=0.0, p=p))
+    j = int(np.argmax(res[1]["rho"]))
+    assert res[1]["chisq"][j] > 2 * (2 * p - 2)           # far above the noise mean 2p - 2
+    assert np.allclose(res[1]["chisq"], 4.0 * res[0]["chisq"], rtol=1e-9, atol=1e-12)
+
+
+def test_chisq_given_edges_reproduce_rule(oracle_lib):
+    r = _chisq_case(oracle_lib, 1 << 12, 4096.0, 9)
+    r2 = _chisq_case(oracle_lib, 1 << 12, 4096.0, 9, edges=r["edges"])
+    assert np.array_equal(r["chisq"], r2["chisq"])
