@@ -55,7 +55,7 @@ def _args():
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
-    ap.add_argument("--workload", default="scale", choices=["scale", "uneven", "precision", "refine"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "uneven", "precision", "refine", "chisq"],
                     help="scale: the benchmark line; the others print their own measurement line "
                          "(uneven bank over mixed segment lengths, phase precision forms, trigger refinement)")
     return ap.parse_args()
@@ -357,31 +357,21 @@ def run_uneven(args, mf, torch, dev):
 
 def run_precision(args, mf, torch, dev):
     """The phase forms on the 1024-template, N = 2^20 workload: speed of each
-    (one CUDA-graph replay per step) and its rho error against the FP64 oracle
-    on a seeded sample of templates (full series)."""
+    (one CUDA-graph replay per step) and, in the CPU-baseline leg, its rho
+    error against the FP64 oracle on a seeded sample of templates (full
+    series, oracle-synthesised input)."""
     import numpy as np
-    import oracle
     import workloads
-    oracle.build()
     wl = workloads.scale(0)
     spec = wl.segments[0]
-    s32 = oracle.synth(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections).astype(np.float32)
-    s64 = s32.astype(np.float64)
-    s_dev = torch.from_numpy(s32).to(dev)
-    seg = mf.Segment(s_dev, spec.fs)
+    seg = mf.Segment(mf.synth_segment(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections), spec.fs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    rng = np.random.default_rng(77)
-    sample = np.sort(rng.choice(wl.n_templates, 8, replace=False))
-    st, S = oracle.data_spectrum(s64, spec.fs), oracle.psd_bins(spec.N, spec.fs)
-    from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max_workers=8) as ex:
-        ref = list(ex.map(lambda t: oracle.filter_template(float(wl.m1[t]), float(wl.m2[t]), st, S, spec.N,
-                                                           spec.fs, wl.f_low)["rho"], sample))
     forms = {}
     cap = 1 << 22
-    for name, mode in (("fp64_anchors_fp32_taylor", mf.MF_PHASE_ANCHOR), ("fp64_per_bin", mf.MF_PHASE_FP64),
-                       ("fp32_only", mf.MF_PHASE_FP32)):
+    modes = (("fp64_anchors_fp32_taylor", mf.MF_PHASE_ANCHOR), ("fp64_per_bin", mf.MF_PHASE_FP64),
+             ("fp32_only", mf.MF_PHASE_FP32))
+    for name, mode in modes:
         bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low, phase_mode=mode)
         out = (torch.empty((wl.n_templates, 4), dtype=torch.float32, device=dev),
                torch.empty((cap, 6), dtype=torch.float32, device=dev),
@@ -394,7 +384,46 @@ def run_precision(args, mf, torch, dev):
         torch.cuda.synchronize()
         g = _capture(torch, call)
         ms = _timed_steps(torch, g.replay, args.steps, args.warmup, flush, stream)
-        # accuracy: full series of the sample (threshold 0)
+        forms[name] = {"templates_per_s": wl.n_templates / (ms / 1e3), "ms_per_call": ms}
+    acc = None
+    if not args.no_cpu_baseline:
+        acc = _precision_cpu_baseline(mf, torch, dev, wl, modes)
+        for name in forms:
+            forms[name].update(acc["forms"][name])
+    line = {"workload": "precision", "metric": "templates/s and max rho rel err vs FP64 per phase form",
+            "value": forms["fp64_anchors_fp32_taylor"]["templates_per_s"], "unit": "templates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections)",
+            "config": {"workload": WORKLOAD, "error_sample": acc["sample"] if acc else None,
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "fft": "FP32 in every form (no tensor-core DFT stage is built)"},
+            "forms": forms, "cpu_baseline": acc["cpu_baseline"] if acc else None}
+    print(json.dumps(line))
+    return 0
+
+
+def _precision_cpu_baseline(mf, torch, dev, wl, modes):
+    """The oracle's full rho series for 8 seeded templates (timed, host cores)
+    and each phase form's error against it on the same input."""
+    import numpy as np
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
+    spec = wl.segments[0]
+    s32 = oracle.synth(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections).astype(np.float32)
+    s64 = s32.astype(np.float64)
+    seg = mf.Segment(torch.from_numpy(s32).to(dev), spec.fs)
+    rng = np.random.default_rng(77)
+    sample = np.sort(rng.choice(wl.n_templates, 8, replace=False))
+    ncores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    st, S = oracle.data_spectrum(s64, spec.fs), oracle.psd_bins(spec.N, spec.fs)
+    with ThreadPoolExecutor(max_workers=min(8, ncores)) as ex:
+        ref = list(ex.map(lambda t: oracle.filter_template(float(wl.m1[t]), float(wl.m2[t]), st, S, spec.N,
+                                                           spec.fs, wl.f_low)["rho"], sample))
+    cpu_s = time.perf_counter() - t0
+    forms = {}
+    for name, mode in modes:
         b2 = mf.Bank(wl.m1[sample], wl.m2[sample], f_low=wl.f_low, phase_mode=mode)
         p, t, n = mf.filter_bank(b2, [seg], 0.0, trig_cap=len(sample) * spec.N)
         tr = mf.triggers_to_numpy(t, n)
@@ -402,22 +431,118 @@ def run_precision(args, mf, torch, dev):
         pk = mf.peaks_to_numpy(p)
         err = np.concatenate([np.abs(rho[i] - ref[i]) / np.maximum(ref[i], 1.0) for i in range(len(sample))])
         idx = sum(int(pk["j"][i]) == int(np.argmax(ref[i])) for i in range(len(sample)))
-        mism = 0
-        for i in range(len(sample)):
-            mism += int(np.sum((rho[i] > wl.threshold) != (ref[i] > wl.threshold)))
-        forms[name] = {"templates_per_s": wl.n_templates / (ms / 1e3), "ms_per_call": ms,
-                       "rho_err_max": float(err.max()), "rho_err_median": float(np.median(err)),
+        mism = sum(int(np.sum((rho[i] > wl.threshold) != (ref[i] > wl.threshold))) for i in range(len(sample)))
+        forms[name] = {"rho_err_max": float(err.max()), "rho_err_median": float(np.median(err)),
                        "peak_index_agree": "%d/%d" % (idx, len(sample)), "trigger_mismatches": mism}
-    line = {"workload": "precision", "metric": "templates/s and max rho rel err vs FP64 per phase form",
-            "value": forms["fp64_anchors_fp32_taylor"]["templates_per_s"], "unit": "templates/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic (oracle-synthesised seeded segment, rounded to float32)",
-            "config": {"workload": WORKLOAD, "error_sample": "%d seeded templates, all 2^20 samples" % len(sample),
-                       "l2": "flushed before every timed step (256 MiB write)",
-                       "fft": "FP32 in every form (no tensor-core DFT stage is built)"},
-            "forms": forms}
+    return {"forms": forms, "sample": "%d seeded templates, all 2^20 samples" % len(sample),
+            "cpu_baseline": {"value": len(sample) / cpu_s, "unit": "templates/s", "cores": min(8, ncores),
+                             "kind": "oracle", "sample": "%d templates, full N=2^20 rho series" % len(sample)}}
+
+
+MSUN_S = 4.925490947e-6
+
+
+def _band_bins(m1, m2, N, fs, f_low):
+    """In-band bin counts K_t (Sec. 1.1 band rule: f_cut = min(f_isco, fs/2),
+    k_lo = ceil(f_low/df), k_hi = min(floor(f_cut/df) + 1, N/2)), for the
+    algorithmic-byte models."""
+    import numpy as np
+    fisco = 1.0 / (6.0 * np.sqrt(6.0) * np.pi * (np.asarray(m1) + np.asarray(m2)) * MSUN_S)
+    fc = np.minimum(fisco, 0.5 * fs)
+    lo = np.maximum(1, np.ceil(f_low * N / fs)).astype(np.int64)
+    hi = np.minimum(np.floor(fc * N / fs).astype(np.int64) + 1, N // 2)
+    return np.maximum(hi - lo, 0)
+
+
+def run_chisq(args, mf, torch, dev):
+    """Eq. (5) chi^2 series (p = 16 sub-bands, every one of the 2^20 samples)
+    for the 64 loudest templates of the 1024-template bench workload: one
+    mf_chisq_series call per step, CUDA events, L2 flushed.  The CPU-baseline
+    leg times the FP64 oracle on a bounded template sample and measures the
+    GPU's chi^2 error on the same (oracle-synthesised) input."""
+    import numpy as np
+    import workloads
+    wl = workloads.scale(0)
+    spec = wl.segments[0]
+    N = spec.N
+    s_dev = mf.synth_segment(spec.normals(), N, spec.fs, wl.f_low, spec.injections)
+    seg = mf.Segment(s_dev, spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
+    pk = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], wl.threshold, trig_cap=1 << 20)[0])
+    n, p = 64, 16
+    sel = np.sort(np.argsort(-pk["rho"])[:n]).astype(np.int32)
+    tmpl = torch.tensor(sel, device=dev)
+    chi = torch.empty((n, N), dtype=torch.float32, device=dev)
+    edges = torch.empty((n, p + 1), dtype=torch.int64, device=dev)
+    import ctypes
+    from paper_0906_4175_gb300 import _native
+
+    def call(segment=seg):
+        _native.check(_native.lib().mf_chisq_series(bank.handle, segment.handle, tmpl.data_ptr(), n, p,
+                                                    chi.data_ptr(), edges.data_ptr(),
+                                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    l0 = mf.launch_count()
+    call()
+    launches = mf.launch_count() - l0
+    steps = max(3, args.steps // 10)
+    ms = _timed_steps(torch, call, steps, args.warmup, flush, torch.cuda.current_stream())
+    # algorithmic bytes per template (model): the W band once; anchors and the
+    # exchange write + read for each sub-band and the full band; the
+    # accumulator's first store, later read-modify-writes and the final
+    # read + write of chi^2
+    K = _band_bins(wl.m1[sel], wl.m2[sel], N, spec.fs, wl.f_low).astype(np.float64)
+    n_anc = K / 128.0
+    per_t = 8.0 * K + (p + 1) * (20.0 * n_anc + 16.0 * N) + 4.0 * N + (p - 1) * 8.0 * N + 8.0 * N
+    achieved = float(per_t.sum()) / (ms / 1e3) / 1e9
+    peak, peak_kind = _hbm_peak()
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        cpu, err = _chisq_cpu_baseline(mf, torch, dev, wl, bank, sel, p, call, chi)
+    line = {"workload": "chisq", "metric": "templates/s of the Eq. (5) chi^2 series at N=2^20, p=16",
+            "value": n / (ms / 1e3), "unit": "templates/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32 (FP64 anchors, FP64 band edges)",
+            "data": "synthetic (seeded coloured Gaussian noise of the bench workload, 8 injections)",
+            "config": {"workload": "64 loudest of the 1024-template bench bank, 1 segment N=2^20 at 4096 Hz, "
+                                   "p = 16 sub-bands, every sample", "l2": "flushed before every timed step"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "model_bytes_per_template": float(per_t.mean())},
+            "chisq_err": err, "cpu_baseline": cpu}
     print(json.dumps(line))
     return 0
+
+
+def _chisq_cpu_baseline(mf, torch, dev, wl, bank, sel, p, call, chi):
+    """The oracle's chi^2 series on a bounded sample of the templates (all
+    host cores), and the GPU's error on the same oracle-synthesised input."""
+    import numpy as np
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
+    spec = wl.segments[0]
+    N = spec.N
+    s32 = oracle.synth(spec.normals(), N, spec.fs, wl.f_low, spec.injections).astype(np.float32)
+    st, S = oracle.data_spectrum(s32.astype(np.float64), spec.fs), oracle.psd_bins(N, spec.fs)
+    ncores = os.cpu_count() or 1
+    m_cpu = min(len(sel), max(ncores, 16))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=ncores) as ex:
+        refs = list(ex.map(lambda t: oracle.chisq_series(float(wl.m1[t]), float(wl.m2[t]), st, S, N, spec.fs,
+                                                         wl.f_low, p), sel[:m_cpu]))
+    cpu_s = time.perf_counter() - t0
+    seg2 = mf.Segment(torch.from_numpy(s32).to(dev), spec.fs)
+    call(seg2)
+    got = chi[:m_cpu].cpu().numpy().astype(np.float64)
+    rel = max(float(np.max(np.abs(got[i] - r["chisq"]) / (r["chisq"] + 2 * r["rho"] ** 2 + 1.0)))
+              for i, r in enumerate(refs))
+    cpu = {"value": m_cpu / cpu_s, "unit": "templates/s", "cores": ncores, "kind": "oracle",
+           "sample": "%d of the 64 templates, full N=2^20 series, p=16, %.1f s wall" % (m_cpu, cpu_s)}
+    err = {"max": rel, "measure": "|chi2_gpu - chi2_fp64| / (chi2 + 2 rho^2 + 1), all samples of the sample"}
+    return cpu, err
 
 
 def _ascend(mf, torch, seg, theta0, steps, rel_m=5e-3, step_t=2e-4, row_seg=None):
@@ -571,7 +696,8 @@ def main():
         from paper_0906_4175_gb300 import build as _b
         _b.build()
         import paper_0906_4175_gb300 as mf
-        fn = {"uneven": run_uneven, "precision": run_precision, "refine": run_refine}[args.workload]
+        fn = {"uneven": run_uneven, "precision": run_precision, "refine": run_refine,
+              "chisq": run_chisq}[args.workload]
         return fn(args, mf, torch, torch.device("cuda", 0))
     if args.warmup < 3:
         args.warmup = 3

@@ -156,6 +156,25 @@ int mf_filter_bank(mf_bank bank, const mf_segment *segs, int n_seg, float thresh
                    mf_peak *peaks, mf_trigger *trig, int64_t trig_cap, int64_t *n_trig,
                    void *cuda_stream);
 
+/* mf_chisq_series -- the chi^2 consistency test of Eq. (5) (Sec. 1.2) at every
+ * sample of one segment, for the bank templates tmpl[0..n) (device int32):
+ *   chi^2_j = (p / sigma^2) sum_l |z_l(t_j) - z(t_j)/p|^2,
+ * z_l the Eq. (1) sum over sub-band l = [b_l, b_{l+1}) of the template's band,
+ * the p sub-bands splitting sigma^2 of Eq. (4) equally: b_0 = k_lo, b_p = k_hi
+ * and b_l = the smallest bin k with P[k] - P[k_lo] >= (l/p)(P[k_hi] - P[k_lo]),
+ * P the FP64 prefix of |h~|^2/S_n.  In stationary Gaussian noise chi^2 has
+ * 2p - 2 degrees of freedom (the paper uses p = 16).
+ * chisq: device FP32 [n][N] (row i for template tmpl[i]); edges: NULL or
+ * device int64 [n][p+1] receiving b_0..b_p.  A template index outside the
+ * bank gives an empty band (a zero row).  1 <= p <= 64, 1 <= n <= 2^24.
+ * Cost: p + 1 inverse FFTs of length N per template.  Allocates scratch on
+ * cuda_stream (so it cannot be captured in a graph) and returns without
+ * synchronising.
+ * Errors: MF_EINVAL (NULL, sizes, devices, f_low >= f_cut, inside a capture),
+ * MF_ENOMEM, MF_ECUDA. */
+int mf_chisq_series(mf_bank bank, mf_segment seg, const int32_t *tmpl, int64_t n, int p,
+                    float *chisq, int64_t *edges, void *cuda_stream);
+
 /* mf_bank_check -- synchronises cuda_stream, then returns MF_OK, MF_EOVERFLOW
  * (the last mf_filter_bank on this bank found more than trig_cap triggers) or
  * MF_ETIMEOUT (a bounded device-side wait of that call expired). */

@@ -18,7 +18,7 @@ from . import _native
 from ._native import (INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
                       MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
 
-__all__ = ["Bank", "Segment", "filter_bank", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
+__all__ = ["Bank", "Segment", "filter_bank", "chisq_series", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
            "PEAK_DTYPE", "TRIG_DTYPE", "INJ_DTYPE", "MF_PHASE_ANCHOR", "MF_PHASE_FP64", "MF_PHASE_FP32",
            "peaks_to_numpy", "triggers_to_numpy", "version"]
 
@@ -187,6 +187,22 @@ def filter_bank(bank: Bank, segments, threshold: float, trig_cap: int = 1 << 20,
                                        trig.data_ptr(), int(trig_cap), n_trig.data_ptr(),
                                        _stream_ptr(stream)))
     return peaks, trig, n_trig
+
+
+def chisq_series(bank: Bank, segment: Segment, tmpl, p: int = 16, stream=None):
+    """mf_chisq_series: Eq. (5) chi^2 at every sample for the bank templates
+    tmpl (sequence of indices or an int32 cuda tensor).  Returns (chisq
+    float32 cuda [n, N], edges int64 cuda [n, p+1])."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = tmpl if isinstance(tmpl, torch.Tensor) else torch.tensor(np.asarray(tmpl, dtype=np.int32), device=dev)
+    t = t.to(device=dev, dtype=torch.int32).contiguous()
+    n = int(t.numel())
+    chisq = torch.empty((n, segment.N), dtype=torch.float32, device=dev)
+    edges = torch.empty((n, p + 1), dtype=torch.int64, device=dev)
+    check(_native.lib().mf_chisq_series(bank.handle, segment.handle, t.data_ptr(), n, int(p), chisq.data_ptr(),
+                                        edges.data_ptr(), _stream_ptr(stream)))
+    return chisq, edges
 
 
 def autotune(bank: Bank, segments, threshold: float, repeats: int = 2, cache_path: str = None, stream=None):

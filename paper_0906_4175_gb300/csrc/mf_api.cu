@@ -19,6 +19,7 @@ cudaError_t filter_kernel_attributes();
 cudaError_t prep_kernel_attributes();
 cudaError_t synth_kernel_attributes();
 cudaError_t refine_kernel_attributes();
+cudaError_t chisq_kernel_attributes();
 cudaError_t persist_kernel_attributes();
 }  // namespace mf
 
@@ -73,6 +74,7 @@ static int ensure_device_init() {
     MF_CUDA(persist_kernel_attributes());
     MF_CUDA(synth_kernel_attributes());
     MF_CUDA(refine_kernel_attributes());
+    MF_CUDA(chisq_kernel_attributes());
     done.push_back(dev);
     return MF_OK;
 }
@@ -733,6 +735,67 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
                                  sm_count(), b->spin_limit, st));
     prof_end(b, pf, st);
     count_launches(sort_launches(key_bits));
+    return MF_OK;
+}
+
+extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, int64_t n, int p, float *chisq,
+                               int64_t *edges, void *cuda_stream) {
+    if (!b || !seg || !tmpl || !chisq) return set_err(MF_EINVAL, "NULL argument");
+    if (n < 1 || n > ((int64_t)1 << 24)) return set_err(MF_EINVAL, "n = %lld outside [1, 2^24]", (long long)n);
+    if (p < 1 || p > kChisqMaxBands) return set_err(MF_EINVAL, "p = %d outside [1, %d]", p, kChisqMaxBands);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != b->device || seg->device != cur) return set_err(MF_EINVAL, "bank and segment must live on the current device");
+    {
+        const double fc = std::min(b->fisco_min, 0.5 * seg->fs);
+        const int64_t lo = std::max((int64_t)1, (int64_t)ceil(b->params.f_low * (double)seg->N / seg->fs));
+        const int64_t hi = std::min((int64_t)floor(fc * (double)seg->N / seg->fs) + 1, seg->N / 2);
+        if (hi <= lo) return set_err(MF_EINVAL, "f_low >= f_cut for some template of the bank");
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (stream_capturing(st)) return set_err(MF_EINVAL, "mf_chisq_series allocates scratch and cannot be captured");
+    const SegDev sd = seg_dev(seg);
+    const int lgD = choose_log2D(b, seg);
+    const int man = (int)(((seg->N / 2) >> lgD) + 2);
+    const int n_t = (int)b->n;
+    const int64_t batch = std::min<int64_t>(n, choose_batch(seg->N, n, b->tuned_exch));
+    const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
+    UnitInfo *all = nullptr, *units = nullptr;
+    float4 *anc = nullptr;
+    float *anc4 = nullptr;
+    float2 *exch = nullptr;
+    cudaError_t e = cudaMallocAsync(&all, sizeof(UnitInfo) * n_t, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&units, sizeof(UnitInfo) * (size_t)(p + 1) * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&anc, sizeof(float4) * man * batch, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&anc4, sizeof(float) * man * batch, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * seg->N * batch, st);
+    int launches = 0;
+    if (e == cudaSuccess) e = launch_units(sd, b->d_tmpl, n_t, b->params.f_low, 0.f, lgD, all, st);
+    if (e == cudaSuccess) e = launch_chisq_units(sd, all, n_t, tmpl, (int)n, p, units, edges, st);
+    launches += 2;
+    const UnitInfo *full = units + (size_t)p * n;
+    for (int64_t u0 = 0; u0 < n && e == cudaSuccess; u0 += batch) {
+        const int nb = (int)std::min<int64_t>(batch, n - u0);
+        if (anchors) {
+            e = launch_anchors(sd, b->d_tmpl, full, (int)u0, nb, lgD, man, anc, anc4, st);
+            ++launches;
+        }
+        for (int l = 0; l <= p && e == cudaSuccess; ++l) {
+            const UnitInfo *ul = units + (size_t)l * n;
+            e = launch_pass1(sd, ul, (int)u0, nb, lgD, man, anc, anc4, exch, b->params.phase_mode, b->d_tmpl, st);
+            if (e == cudaSuccess)
+                e = launch_chisq_pass2(sd, ul, (int)u0, nb, exch, chisq, l == p ? 2 : (l == 0 ? 0 : 1), p, st);
+            launches += 2;
+        }
+    }
+    if (all) cudaFreeAsync(all, st);
+    if (units) cudaFreeAsync(units, st);
+    if (anc) cudaFreeAsync(anc, st);
+    if (anc4) cudaFreeAsync(anc4, st);
+    if (exch) cudaFreeAsync(exch, st);
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "chisq_series: %s", cudaGetErrorString(e));
+    count_launches(launches);
     return MF_OK;
 }
 

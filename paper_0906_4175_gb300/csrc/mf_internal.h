@@ -139,6 +139,14 @@ inline int64_t sort_tile_words(int64_t cap) { return ((cap + 2047) / 2048) * 256
 cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,
                           const int64_t *band, double *obj, double *grad, double *partial, int bpr,
                           cudaStream_t st);
+// chi^2 series (Eq. 5): at most this many sub-bands
+constexpr int kChisqMaxBands = 64;
+cudaError_t launch_chisq_units(const SegDev &seg, const UnitInfo *all, int n_t, const int32_t *tmpl, int n, int p,
+                               UnitInfo *out, int64_t *edges, cudaStream_t st);
+// mode 0: first sub-band (store |raw|^2), 1: later sub-band (add), 2: full band (write chi^2)
+cudaError_t launch_chisq_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
+                               float *acc, int mode, int p, cudaStream_t st);
+
 // segments of one mf_refine_triggers_multi call (kernel-parameter table)
 constexpr int kRefineMaxSegs = 256;
 cudaError_t launch_refine_multi(const SegDev *segs, int n_seg, const int32_t *row_seg, double f_low,
