@@ -55,7 +55,7 @@ def _args():
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
-    ap.add_argument("--workload", default="scale", choices=["scale", "uneven", "precision", "refine", "chisq"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "uneven", "precision", "refine", "chisq", "fft"],
                     help="scale: the benchmark line; the others print their own measurement line "
                          "(uneven bank over mixed segment lengths, phase precision forms, trigger refinement)")
     return ap.parse_args()
@@ -439,6 +439,69 @@ def _precision_cpu_baseline(mf, torch, dev, wl, modes):
                              "kind": "oracle", "sample": "%d templates, full N=2^20 rho series" % len(sample)}}
 
 
+def run_fft(args, mf, torch, dev):
+    """The batched complex FFT alone (the paper's Figs. 1-2 experiment): for
+    N = 2^10 .. 2^22, batches of 2^26 points (512 MiB in, 512 MiB out) through
+    mf_fft_c2c, CUDA events; the CPU-baseline leg times the oracle's FP64
+    radix-2 FFT on the host cores for a bounded number of transforms."""
+    import ctypes
+    import numpy as np
+    from paper_0906_4175_gb300 import _native
+    total = 1 << 26
+    x = torch.randn(total, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = _hbm_peak()
+    rows = {}
+    for lg in range(10, 23):
+        N = 1 << lg
+        batch = total // N
+
+        def call():
+            _native.check(_native.lib().mf_fft_c2c(x.data_ptr(), y.data_ptr(), N, batch, -1,
+                                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+        l0 = mf.launch_count()
+        call()
+        launches = mf.launch_count() - l0
+        ms = _timed_steps(torch, call, max(3, args.steps // 10), args.warmup, flush, torch.cuda.current_stream())
+        gbs = 16.0 * total / (ms / 1e3) / 1e9
+        rows["2^%d" % lg] = {"batch": batch, "ms": ms, "transforms_per_s": batch / (ms / 1e3),
+                             "gflops": 5.0 * N * lg * batch / (ms / 1e3) / 1e9, "algorithmic_gbs": gbs,
+                             "hbm_frac": gbs / peak, "launches": launches}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        oracle.build()
+        ncores = os.cpu_count() or 1
+        cpu = {}
+        for lg in (10, 14, 18, 20, 22):
+            N = 1 << lg
+            n_t = max(ncores, int(min(256, (1 << 22) // N)) // ncores * ncores)
+            xs = [np.random.default_rng(i).standard_normal(N) + 0j for i in range(n_t)]
+            t0 = time.perf_counter()
+            with ThreadPoolExecutor(max_workers=ncores) as ex:
+                list(ex.map(lambda v: oracle.fft(v, -1), xs))
+            dt = time.perf_counter() - t0
+            cpu["2^%d" % lg] = {"transforms_per_s": n_t / dt, "gflops": 5.0 * N * lg * n_t / dt / 1e9,
+                                "transforms": n_t}
+        cpu = {"kind": "oracle", "cores": ncores, "unit": "transforms/s", "per_N": cpu,
+               "sample": "FP64 radix-2 oracle FFT, forward, one transform per thread at a time"}
+    r20 = rows["2^20"]
+    line = {"workload": "fft", "metric": "batched complex FFT transforms/s (FP32, forward), 2^26 points per call",
+            "value": r20["transforms_per_s"], "unit": "transforms/s at N=2^20", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "c64", "data": "synthetic (normal complex samples)",
+            "config": {"workload": "batches of 2^26 complex points, N = 2^10..2^22 (batch = 2^26 / N)",
+                       "l2": "input and output 512 MiB each (larger than L2), L2 flushed before every timed call"},
+            "roofline": {"bound": "hbm", "kernel": "fft_c2c (both passes)", "achieved": r20["algorithmic_gbs"],
+                         "peak": peak, "unit": "GB/s", "frac": r20["hbm_frac"], "peak_kind": peak_kind,
+                         "traffic": None, "algorithmic_bytes": "16 per point (read x, write y)"},
+            "per_N": rows, "cpu_baseline": cpu}
+    print(json.dumps(line))
+    return 0
+
+
 MSUN_S = 4.925490947e-6
 
 
@@ -697,7 +760,7 @@ def main():
         _b.build()
         import paper_0906_4175_gb300 as mf
         fn = {"uneven": run_uneven, "precision": run_precision, "refine": run_refine,
-              "chisq": run_chisq}[args.workload]
+              "chisq": run_chisq, "fft": run_fft}[args.workload]
         return fn(args, mf, torch, torch.device("cuda", 0))
     if args.warmup < 3:
         args.warmup = 3

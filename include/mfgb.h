@@ -156,6 +156,18 @@ int mf_filter_bank(mf_bank bank, const mf_segment *segs, int n_seg, float thresh
                    mf_peak *peaks, mf_trigger *trig, int64_t trig_cap, int64_t *n_trig,
                    void *cuda_stream);
 
+/* mf_fft_c2c -- batched complex FP32 FFT with the library's own four-step
+ * kernels (the batched transforms the paper timed in Figs. 1-2):
+ *   y_b[k] = sum_n x_b[n] exp(sign 2 pi i n k / N),  b < batch, k < N,
+ * unnormalised.  x, y: device complex64 (interleaved re, im float pairs,
+ * 8-byte aligned), batch entries N apart; y may equal x (in place).
+ * N a power of two in [2^10, 2^22]; sign = -1 (forward) or +1.  Allocates a
+ * complex64 exchange of up to 1 GiB on cuda_stream (not capturable), queues
+ * two kernels per 1 GiB of batch and returns without synchronising.
+ * Errors: MF_EINVAL (NULL, size, sign, alignment, inside a capture),
+ * MF_ENOMEM, MF_ECUDA. */
+int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int sign, void *cuda_stream);
+
 /* mf_chisq_series -- the chi^2 consistency test of Eq. (5) (Sec. 1.2) at every
  * sample of one segment, for the bank templates tmpl[0..n) (device int32):
  *   chi^2_j = (p / sigma^2) sum_l |z_l(t_j) - z(t_j)/p|^2,

@@ -18,7 +18,7 @@ from . import _native
 from ._native import (INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
                       MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
 
-__all__ = ["Bank", "Segment", "filter_bank", "chisq_series", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
+__all__ = ["Bank", "Segment", "filter_bank", "chisq_series", "fft", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
            "PEAK_DTYPE", "TRIG_DTYPE", "INJ_DTYPE", "MF_PHASE_ANCHOR", "MF_PHASE_FP64", "MF_PHASE_FP32",
            "peaks_to_numpy", "triggers_to_numpy", "version"]
 
@@ -187,6 +187,19 @@ def filter_bank(bank: Bank, segments, threshold: float, trig_cap: int = 1 << 20,
                                        trig.data_ptr(), int(trig_cap), n_trig.data_ptr(),
                                        _stream_ptr(stream)))
     return peaks, trig, n_trig
+
+
+def fft(x, sign: int = -1, out=None, stream=None):
+    """mf_fft_c2c: batched complex FFT over the last axis of a complex64 cuda
+    tensor (unnormalised; sign -1 forward, +1 inverse)."""
+    torch = _torch()
+    if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous complex64 cuda tensor")
+    N = int(x.shape[-1])
+    batch = int(x.numel() // N) if N else 0
+    y = torch.empty_like(x) if out is None else out
+    check(_native.lib().mf_fft_c2c(x.data_ptr(), y.data_ptr(), N, batch, int(sign), _stream_ptr(stream)))
+    return y
 
 
 def chisq_series(bank: Bank, segment: Segment, tmpl, p: int = 16, stream=None):

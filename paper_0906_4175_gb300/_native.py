@@ -41,6 +41,7 @@ SIGNATURES = {
     "mf_bank_check": (_I, [_P, _P]),
     "mf_synth_segment": (_I, [_P, _I64, _D, _D, _P, _D, _D, _P, _I64, _D, _P, _P]),
     "mf_refine_triggers": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
+    "mf_fft_c2c": (_I, [_P, _P, _I64, _I64, _I, _P]),
     "mf_chisq_series": (_I, [_P, _P, _P, _I64, _I, _P, _P, _P]),
     "mf_refine_triggers_multi": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "mf_refine_triggers_static": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),

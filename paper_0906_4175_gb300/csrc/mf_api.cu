@@ -738,6 +738,32 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     return MF_OK;
 }
 
+extern "C" int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int sign, void *cuda_stream) {
+    if (!x || !y) return set_err(MF_EINVAL, "NULL argument");
+    if (!is_pow2_in(N, 10, 22)) return set_err(MF_EINVAL, "N = %lld must be a power of two in [2^10, 2^22]", (long long)N);
+    if (batch < 1) return set_err(MF_EINVAL, "batch < 1");
+    if (sign != 1 && sign != -1) return set_err(MF_EINVAL, "sign must be +1 or -1");
+    if (((uintptr_t)x | (uintptr_t)y) & 7) return set_err(MF_EINVAL, "x and y must be 8-byte aligned complex64 arrays");
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (stream_capturing(st)) return set_err(MF_EINVAL, "mf_fft_c2c allocates its exchange and cannot be captured");
+    const int64_t chunk = std::min<int64_t>({batch, std::max<int64_t>(1, kExchBudget / (8 * N)), 65535});
+    float2 *exch = nullptr;
+    cudaError_t e = cudaMallocAsync(&exch, sizeof(float2) * N * chunk, st);
+    int launches = 0;
+    for (int64_t b0 = 0; b0 < batch && e == cudaSuccess; b0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, batch - b0);
+        e = launch_fft_c2c((const float2 *)x + b0 * N, (float2 *)y + b0 * N, N, nb, sign, exch, st);
+        launches += 2;
+    }
+    if (exch) cudaFreeAsync(exch, st);
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "fft_c2c: %s", cudaGetErrorString(e));
+    count_launches(launches);
+    return MF_OK;
+}
+
 extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, int64_t n, int p, float *chisq,
                                int64_t *edges, void *cuda_stream) {
     if (!b || !seg || !tmpl || !chisq) return set_err(MF_EINVAL, "NULL argument");

@@ -95,6 +95,9 @@ struct PersistParams {
 
 // segment preparation (mf_prep.cu)
 cudaError_t launch_forward_fft(const float *s, int64_t N, float2 *exch, float2 *X, cudaStream_t st);
+// batch <= 65535 transforms of N points, x and y batch entries N apart, exch batch * N
+cudaError_t launch_fft_c2c(const float2 *x, float2 *y, int64_t N, int batch, int sign, float2 *exch,
+                           cudaStream_t st);
 cudaError_t launch_psd_weights(const float2 *X, const double *psd, double psd_f0, double psd_S0,
                                int64_t N, double fs, double *q, cudaStream_t st);
 cudaError_t launch_prefix_f64(const double *q, int64_t n, double *P, double *block_tmp, cudaStream_t st);

@@ -198,6 +198,48 @@ struct RowComplexOut {
     __device__ __forceinline__ void finish(float2 *) const {}
 };
 
+// out[slot * out_stride + j2 + N2 j1] = v for every j.  The CTA owns C
+// consecutive rows j2, so each j1 is C consecutive outputs; when a sequence
+// fits one warp (L <= 1024) every warp parks its outputs in its own
+// sequence's shared-memory row (free once the warp has read its last stage)
+// and finish() writes the C x L tile with consecutive threads on consecutive
+// outputs.  Longer rows store element by element.
+template <int L, int C>
+struct RowTileOut {
+    static constexpr bool kTile = (L / 32) <= 32;
+    struct Params { float2 *out; int log2N2; int64_t out_stride; };
+    const Params &p;
+    const int tile, slot;
+    __device__ RowTileOut(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
+    __device__ __forceinline__ float2 *row(int seq) const {
+        extern __shared__ float2 rto_smem[];
+        return rto_smem + seq * FftShape<L>::STRIDE;
+    }
+    template <int R>
+    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
+        if constexpr (kTile) {
+            float2 *r0 = row(seq);
+            __syncwarp();   // every lane of this warp has read its last-stage inputs
+#pragma unroll
+            for (int r = 0; r < R; ++r) r0[b + r * stride] = v[r];
+        } else {
+            float2 *o = p.out + slot * p.out_stride + tile * C + seq;
+#pragma unroll
+            for (int r = 0; r < R; ++r) o[(int64_t)(b + r * stride) << p.log2N2] = v[r];
+        }
+    }
+    __device__ __forceinline__ void finish(float2 *) const {
+        if constexpr (kTile) {
+            __syncthreads();
+            float2 *o = p.out + slot * p.out_stride + tile * C;
+            for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+                const int seq = idx % C, j1 = idx / C;
+                __stcs(&o[seq + ((int64_t)j1 << p.log2N2)], row(seq)[j1]);
+            }
+        }
+    }
+};
+
 // s[j2 + N2 j1] = scale * Re(v)
 template <int L, int C>
 struct RowRealOut {

@@ -45,6 +45,43 @@ struct FwdAttrOp {
 };
 }  // namespace
 
+// Batched complex FFT y_b = sum_n x_b[n] e^{SIGN 2 pi i n k / N} (unnormalised),
+// batch entries N apart, through the same four-step passes.
+template <int SIGN>
+struct C2COp {
+    const float2 *x;
+    float2 *y, *exch;
+    int batch;
+    cudaStream_t st;
+    template <int N2, int N1>
+    cudaError_t run() {
+        constexpr int C1 = seqs_per_cta<N2>(N1);
+        constexpr int C2 = seqs_per_cta<N1>(N2);
+        constexpr int LG1 = cx_ilog2(N1), LG2 = cx_ilog2(N2);
+        const int64_t N = (int64_t)N1 * N2;
+        typename ColComplexSrc<N2, C1, false, LG1>::Params sp{x, LG1, N};
+        typename ExchSink<N2, C1, SIGN, LG1>::Params kp{exch, LG1, LG1 + LG2};
+        cudaError_t e = run_pass<N2, C1, true, SIGN, ColComplexSrc<N2, C1, false, LG1>, ExchSink<N2, C1, SIGN, LG1>>(
+            dim3(N1 / C1, batch), sp, kp, st);
+        if (e != cudaSuccess) return e;
+        typename RowSrc<N1, C2>::Params sp2{exch, LG1, LG1 + LG2};
+        typename RowTileOut<N1, C2>::Params kp2{y, LG2, N};
+        return run_pass<N1, C2, false, SIGN, RowSrc<N1, C2>, RowTileOut<N1, C2>>(dim3(N2 / C2, batch), sp2, kp2, st);
+    }
+};
+template <int SIGN>
+struct C2CAttrOp {
+    template <int N2, int N1>
+    cudaError_t run() {
+        constexpr int C1 = seqs_per_cta<N2>(N1);
+        constexpr int C2 = seqs_per_cta<N1>(N2);
+        constexpr int LG1 = cx_ilog2(N1);
+        cudaError_t e = set_pass_attrs<N2, C1, true, SIGN, ColComplexSrc<N2, C1, false, LG1>, ExchSink<N2, C1, SIGN, LG1>>();
+        if (e != cudaSuccess) return e;
+        return set_pass_attrs<N1, C2, false, SIGN, RowSrc<N1, C2>, RowTileOut<N1, C2>>();
+    }
+};
+
 static int ilog2_i64(int64_t n) {
     int r = 0;
     while ((int64_t)1 << (r + 1) <= n) ++r;
@@ -56,7 +93,25 @@ cudaError_t launch_forward_fft(const float *s, int64_t N, float2 *exch, float2 *
     return dispatch_split(op.log2N, op);
 }
 
+cudaError_t launch_fft_c2c(const float2 *x, float2 *y, int64_t N, int batch, int sign, float2 *exch,
+                           cudaStream_t st) {
+    const int lg = ilog2_i64(N);
+    if (sign < 0) {
+        C2COp<-1> op{x, y, exch, batch, st};
+        return dispatch_split(lg, op);
+    }
+    C2COp<+1> op{x, y, exch, batch, st};
+    return dispatch_split(lg, op);
+}
+
 cudaError_t prep_kernel_attributes() {
+    for (int lg = 10; lg <= 22; ++lg) {
+        C2CAttrOp<-1> a;
+        C2CAttrOp<+1> b;
+        cudaError_t e = dispatch_split(lg, a);
+        if (e == cudaSuccess) e = dispatch_split(lg, b);
+        if (e != cudaSuccess) return e;
+    }
     for (int lg = 10; lg <= 22; ++lg) {
         FwdAttrOp op;
         cudaError_t e = dispatch_split(lg, op);
