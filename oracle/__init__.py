@@ -113,6 +113,8 @@ def lib():
             L.or_chisq_series.argtypes = [ctypes.c_double, ctypes.c_double, _P, _P, _P, _I64, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P]
             L.or_chisq_series.restype = ctypes.c_int
+            L.or_cluster.argtypes = [_P, _I64, ctypes.c_int32, _P, _I64]
+            L.or_cluster.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -236,6 +238,23 @@ def chisq_series(m1, m2, st: np.ndarray, S: np.ndarray, N: int, fs: float, f_low
     if rc != 0:
         raise RuntimeError("or_chisq_series failed: %d" % rc)
     return dict(chisq=chisq, rho=rho, edges=e_out, sig2_l=sig2_l)
+
+
+EVENT_DTYPE = np.dtype([("tmpl", "i4"), ("seg", "i4"), ("j", "i4"), ("n_trig", "i4"), ("n_tmpl", "i4"),
+                        ("pad", "i4"), ("rho", "f8"), ("z_re", "f8"), ("z_im", "f8")])
+
+
+def cluster(triggers, window: int) -> np.ndarray:
+    """Two-stage single-linkage clustering of triggers sorted by (tmpl, seg, j):
+    per (template, segment) with gaps <= window samples, then the clusters'
+    loudest members across templates by (segment, j).  Returns EVENT_DTYPE
+    records sorted by (seg, j)."""
+    t = np.ascontiguousarray(triggers, dtype=TRIG_DTYPE)
+    ev = np.zeros(max(t.size, 1), dtype=EVENT_DTYPE)
+    ne = lib().or_cluster(_ptr(t), t.size, int(window), _ptr(ev), ev.size)
+    if ne < 0:
+        raise RuntimeError("or_cluster failed")
+    return ev[:ne]
 
 
 def filter_bank(m1, m2, s, fs: float, f_low: float, thr: float, psd=None,

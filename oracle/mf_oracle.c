@@ -609,3 +609,68 @@ int or_refine(const double *theta, int64_t n, const double *s, int64_t N, double
     free(st_re); free(st_im); free(S);
     return 0;
 }
+
+
+/* ------------------------------------------------------------------------ */
+/* Trigger clustering (the paper's pipeline reports events, Sec. 3.3; it    */
+/* gives no clustering rule).  Reading: single linkage in time with a       */
+/* maximum gap of `window` samples, first over the triggers of each          */
+/* (template, segment) pair, then over those clusters' loudest members of    */
+/* all templates within a segment.  An event is the loudest member (largest */
+/* rho; on ties the earlier one in the order of the pass: lower j, then      */
+/* lower template).  Input: n triggers sorted by (template, segment, j).     */
+/* Output: events sorted by (segment, j) with the number of triggers and of  */
+/* per-template clusters merged into each; returns the event count.          */
+/* ------------------------------------------------------------------------ */
+typedef struct { int32_t tmpl, seg, j, n_trig, n_tmpl, pad; double rho, z_re, z_im; } or_event;
+
+static int or_cmp_seg_j_tmpl(const void *a, const void *b)
+{
+    const or_event *x = (const or_event *)a, *y = (const or_event *)b;
+    if (x->seg != y->seg) return x->seg < y->seg ? -1 : 1;
+    if (x->j != y->j) return x->j < y->j ? -1 : 1;
+    if (x->tmpl != y->tmpl) return x->tmpl < y->tmpl ? -1 : 1;
+    return 0;
+}
+
+int64_t or_cluster(const or_trigger *t, int64_t n, int32_t window, or_event *ev, int64_t ev_cap)
+{
+    or_event *c1 = (or_event *)malloc(sizeof(or_event) * (size_t)(n > 0 ? n : 1));
+    if (!c1) return -2;
+    int64_t m = 0;
+    /* pass 1: per (template, segment), consecutive triggers at most `window` apart */
+    for (int64_t i = 0; i < n; ++i) {
+        int start = (i == 0) || t[i].tmpl != t[i - 1].tmpl || t[i].seg != t[i - 1].seg ||
+                    (int64_t)t[i].j - (int64_t)t[i - 1].j > window;
+        if (start) {
+            or_event e = {t[i].tmpl, t[i].seg, t[i].j, 1, 1, 0, t[i].rho, t[i].z_re, t[i].z_im};
+            c1[m++] = e;
+        } else {
+            or_event *e = &c1[m - 1];
+            e->n_trig += 1;
+            if (t[i].rho > e->rho) {
+                e->tmpl = t[i].tmpl; e->j = t[i].j; e->rho = t[i].rho; e->z_re = t[i].z_re; e->z_im = t[i].z_im;
+            }
+        }
+    }
+    /* pass 2: the clusters' loudest members of all templates, by (segment, j, template) */
+    qsort(c1, (size_t)m, sizeof(or_event), or_cmp_seg_j_tmpl);
+    int64_t ne = 0;
+    or_event cur = {0};
+    for (int64_t i = 0; i < m; ++i) {
+        int start = (i == 0) || c1[i].seg != c1[i - 1].seg || (int64_t)c1[i].j - (int64_t)c1[i - 1].j > window;
+        if (start) {
+            if (i > 0) { if (ne < ev_cap) ev[ne] = cur; ++ne; }
+            cur = c1[i];
+        } else {
+            cur.n_trig += c1[i].n_trig;
+            cur.n_tmpl += 1;
+            if (c1[i].rho > cur.rho) {
+                cur.tmpl = c1[i].tmpl; cur.j = c1[i].j; cur.rho = c1[i].rho; cur.z_re = c1[i].z_re; cur.z_im = c1[i].z_im;
+            }
+        }
+    }
+    if (m > 0) { if (ne < ev_cap) ev[ne] = cur; ++ne; }
+    free(c1);
+    return ne;
+}

@@ -485,3 +485,81 @@ def test_chisq_given_edges_reproduce_rule(oracle_lib):
     r = _chisq_case(oracle_lib, 1 << 12, 4096.0, 9)
     r2 = _chisq_case(oracle_lib, 1 << 12, 4096.0, 9, edges=r["edges"])
     assert np.array_equal(r["chisq"], r2["chisq"])
+
+
+# ---------------------------------------------------------------------------
+# Trigger clustering (events)
+# ---------------------------------------------------------------------------
+def _random_triggers(oracle_lib, seed, n_t=5, n_seg=3, N=4000, per=60):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for t in range(n_t):
+        for s in range(n_seg):
+            js = np.unique(rng.integers(0, N, rng.integers(0, per)))
+            for j in js:
+                rows.append((t, s, int(j), 0, float(rng.choice([6.5, 7.0, 8.0, 9.5]) + rng.integers(0, 3)),
+                             rng.standard_normal(), rng.standard_normal()))
+    tr = np.array(rows, dtype=oracle_lib.TRIG_DTYPE) if rows else np.zeros(0, dtype=oracle_lib.TRIG_DTYPE)
+    order = np.lexsort((tr["j"], tr["seg"], tr["tmpl"]))
+    return tr[order]
+
+
+def _brute_events(tr, W):
+    """The same two-stage single linkage written as sorted runs in plain
+    Python (stage 1: chains of triggers of one (tmpl, seg) at most W apart;
+    stage 2: chains of the stage-1 winners of one segment)."""
+    n = tr.size
+
+    def comps(idx, key, group):
+        idx = sorted(idx, key=key)
+        groups, cur = [], []
+        for i in idx:
+            if cur and (group(i) != group(cur[-1]) or tr["j"][i] - tr["j"][cur[-1]] > W):
+                groups.append(cur)
+                cur = []
+            cur.append(i)
+        if cur:
+            groups.append(cur)
+        return groups
+
+    g1 = comps(range(n), lambda i: (int(tr["tmpl"][i]), int(tr["seg"][i]), int(tr["j"][i])),
+               lambda i: (int(tr["tmpl"][i]), int(tr["seg"][i])))
+    win1 = []
+    for g in g1:
+        best = g[0]
+        for i in g[1:]:
+            if tr["rho"][i] > tr["rho"][best]:
+                best = i
+        win1.append((best, len(g)))
+    cnt = {b: c for b, c in win1}
+    g2 = comps([b for b, _ in win1], lambda i: (int(tr["seg"][i]), int(tr["j"][i]), int(tr["tmpl"][i])),
+               lambda i: int(tr["seg"][i]))
+    out = []
+    for g in g2:
+        best = g[0]
+        for i in g[1:]:
+            if tr["rho"][i] > tr["rho"][best]:
+                best = i
+        out.append((int(tr["tmpl"][best]), int(tr["seg"][best]), int(tr["j"][best]),
+                    sum(cnt[i] for i in g), len(g), float(tr["rho"][best])))
+    return out
+
+
+@pytest.mark.parametrize("seed,W", [(1, 0), (2, 5), (3, 40), (4, 400), (5, 5000)])
+def test_cluster_matches_python_runs(oracle_lib, seed, W):
+    tr = _random_triggers(oracle_lib, seed)
+    ev = oracle_lib.cluster(tr, W)
+    ref = _brute_events(tr, W)
+    got = [(int(e["tmpl"]), int(e["seg"]), int(e["j"]), int(e["n_trig"]), int(e["n_tmpl"]), float(e["rho"]))
+           for e in ev]
+    assert got == ref
+    assert sum(e["n_trig"] for e in ev) == tr.size                # every trigger in exactly one event
+    for a, b in zip(ev[:-1], ev[1:]):                             # sorted, separated events
+        assert (a["seg"], a["j"]) < (b["seg"], b["j"])
+
+
+def test_cluster_empty_and_single(oracle_lib):
+    assert oracle_lib.cluster(np.zeros(0, dtype=oracle_lib.TRIG_DTYPE), 10).size == 0
+    one = np.array([(3, 1, 77, 0, 6.2, 0.5, -0.5)], dtype=oracle_lib.TRIG_DTYPE)
+    ev = oracle_lib.cluster(one, 10)
+    assert ev.size == 1 and ev[0]["j"] == 77 and ev[0]["n_trig"] == 1 and ev[0]["n_tmpl"] == 1
