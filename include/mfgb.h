@@ -76,6 +76,17 @@ typedef struct {
 } mf_trigger;
 
 /* A frequency-domain injection for mf_synth_segment. */
+/* An event: a cluster of triggers (mf_cluster_triggers) and its loudest member. */
+typedef struct {
+    int32_t tmpl;     /* template of the loudest member */
+    int32_t seg;      /* segment index */
+    int32_t j;        /* sample index of the loudest member */
+    float rho;        /* its rho */
+    float z_re, z_im; /* its z */
+    int32_t n_trig;   /* triggers in the event */
+    int32_t n_tmpl;   /* per-template clusters merged into the event */
+} mf_event;
+
 typedef struct {
     double m1, m2;    /* component masses, solar masses */
     double snr;       /* optimal SNR the injection is scaled to */
@@ -186,6 +197,37 @@ int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int sign, void 
  * MF_ENOMEM, MF_ECUDA. */
 int mf_chisq_series(mf_bank bank, mf_segment seg, const int32_t *tmpl, int64_t n, int p,
                     float *chisq, int64_t *edges, void *cuda_stream);
+
+/* mf_cluster_triggers -- events from triggers (the paper reports events and
+ * gives no clustering rule; this is single linkage in time).  trig: device
+ * records sorted by (tmpl, seg, j) as mf_filter_bank returns them; *n_trig
+ * (device) their count, of which the first min(*n_trig, trig_cap) are read.
+ * Pass 1 links the triggers of one (template, segment) whose consecutive
+ * samples are at most `window` apart; pass 2 links those clusters' loudest
+ * members of all templates of one segment the same way.  Each event is the
+ * loudest member (rho; ties: lower j, then lower template).  events: device
+ * array of ev_cap records, written sorted by (seg, j); *n_events (device)
+ * receives the true event count (compare with ev_cap for truncation).
+ * n_tmpl, n_seg, max_N: the bank size, segment count and largest segment
+ * length of the filter call (they size the sort keys).  Allocates scratch
+ * (about 100 bytes per trigger of trig_cap) on cuda_stream; does not
+ * synchronise.
+ * Errors: MF_EINVAL (NULL, negative window, sizes), MF_ENOMEM, MF_ECUDA. */
+int mf_cluster_triggers(const mf_trigger *trig, const int64_t *n_trig, int64_t trig_cap, int64_t n_tmpl,
+                        int n_seg, int64_t max_N, int32_t window, mf_event *events, int64_t ev_cap,
+                        int64_t *n_events, void *cuda_stream);
+
+/* mf_chisq_points -- Eq. (5) at single samples: for each row i the template
+ * rows[i*stride], segment segs[rows[i*stride+1]] and sample j =
+ * rows[i*stride+2] (device int32; stride >= 3 int32 words, so mf_trigger
+ * (stride 6) and mf_event (stride 8) arrays can be passed directly),
+ *   chisq[i] = (p / sigma^2) sum_l |z_l(t_j) - z(t_j)/p|^2
+ * with the sub-bands of mf_chisq_series, evaluated by direct sums over the
+ * band (no FFT).  chisq: device float [n]; NaN for a row naming no template,
+ * segment or sample.  1 <= p <= 64, 1 <= n_seg <= 256.
+ * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+int mf_chisq_points(mf_bank bank, const mf_segment *segs, int n_seg, const int32_t *rows, int64_t stride,
+                    int64_t n, int p, float *chisq, void *cuda_stream);
 
 /* mf_bank_check -- synchronises cuda_stream, then returns MF_OK, MF_EOVERFLOW
  * (the last mf_filter_bank on this bank found more than trig_cap triggers) or

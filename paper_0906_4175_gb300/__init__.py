@@ -15,10 +15,11 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
+from ._native import (EVENT_DTYPE, INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
                       MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
 
-__all__ = ["Bank", "Segment", "filter_bank", "chisq_series", "fft", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
+__all__ = ["Bank", "Segment", "filter_bank", "chisq_series", "chisq_points", "cluster_triggers",
+           "events_to_numpy", "EVENT_DTYPE", "fft", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
            "PEAK_DTYPE", "TRIG_DTYPE", "INJ_DTYPE", "MF_PHASE_ANCHOR", "MF_PHASE_FP64", "MF_PHASE_FP32",
            "peaks_to_numpy", "triggers_to_numpy", "version"]
 
@@ -200,6 +201,44 @@ def fft(x, sign: int = -1, out=None, stream=None):
     y = torch.empty_like(x) if out is None else out
     check(_native.lib().mf_fft_c2c(x.data_ptr(), y.data_ptr(), N, batch, int(sign), _stream_ptr(stream)))
     return y
+
+
+def cluster_triggers(trig, n_trig, n_tmpl: int, n_seg: int, max_N: int, window: int, ev_cap: int = None,
+                     stream=None):
+    """mf_cluster_triggers: events from (tmpl, seg, j)-sorted triggers (the
+    filter_bank outputs).  Returns (events float32 cuda [ev_cap, 8] laid out
+    as EVENT_DTYPE, n_events int64 cuda [1], the true count)."""
+    torch = _torch()
+    dev = trig.device
+    cap = int(trig.shape[0])
+    ev_cap = cap if ev_cap is None else int(ev_cap)
+    ev = torch.empty((max(ev_cap, 1), 8), dtype=torch.float32, device=dev)
+    n_ev = torch.zeros(1, dtype=torch.int64, device=dev)
+    check(_native.lib().mf_cluster_triggers(trig.data_ptr(), n_trig.data_ptr(), cap, int(n_tmpl), int(n_seg),
+                                            int(max_N), int(window), ev.data_ptr(), ev_cap, n_ev.data_ptr(),
+                                            _stream_ptr(stream)))
+    return ev, n_ev
+
+
+def events_to_numpy(ev, n_ev) -> np.ndarray:
+    n = int(n_ev.item()) if hasattr(n_ev, "item") else int(n_ev)
+    n = min(n, ev.shape[0])
+    return ev[:n].detach().cpu().contiguous().numpy().view(EVENT_DTYPE).reshape(-1)
+
+
+def chisq_points(bank: Bank, segments, rows, p: int = 16, stream=None):
+    """mf_chisq_points: Eq. (5) chi^2 at the (tmpl, seg, j) of each row of a
+    trigger [n, 6] or event [n, 8] tensor (cuda, 4-byte fields)."""
+    torch = _torch()
+    segs = list(segments) if isinstance(segments, (list, tuple)) else [segments]
+    arr = (ctypes.c_void_p * len(segs))(*[sg.handle.value for sg in segs])
+    if not rows.is_cuda or rows.dim() != 2 or rows.element_size() != 4 or not rows.is_contiguous():
+        raise ValueError("rows must be a contiguous 2-D cuda tensor of 4-byte fields")
+    n = int(rows.shape[0])
+    out = torch.empty(max(n, 1), dtype=torch.float32, device=rows.device)
+    check(_native.lib().mf_chisq_points(bank.handle, arr, len(segs), rows.data_ptr(), int(rows.shape[1]), n, int(p),
+                                        out.data_ptr(), _stream_ptr(stream)))
+    return out[:n]
 
 
 def chisq_series(bank: Bank, segment: Segment, tmpl, p: int = 16, stream=None):

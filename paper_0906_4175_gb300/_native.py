@@ -42,6 +42,8 @@ SIGNATURES = {
     "mf_synth_segment": (_I, [_P, _I64, _D, _D, _P, _D, _D, _P, _I64, _D, _P, _P]),
     "mf_refine_triggers": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "mf_fft_c2c": (_I, [_P, _P, _I64, _I64, _I, _P]),
+    "mf_cluster_triggers": (_I, [_P, _P, _I64, _I64, _I, _I64, ctypes.c_int32, _P, _I64, _P, _P]),
+    "mf_chisq_points": (_I, [_P, _P, _I, _P, _I64, _I64, _I, _P, _P]),
     "mf_chisq_series": (_I, [_P, _P, _P, _I64, _I, _P, _P, _P]),
     "mf_refine_triggers_multi": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "mf_refine_triggers_static": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
@@ -62,6 +64,8 @@ class BankParams(ctypes.Structure):
 PEAK_DTYPE = np.dtype([("rho", "f4"), ("j", "i4"), ("z_re", "f4"), ("z_im", "f4")])
 TRIG_DTYPE = np.dtype([("tmpl", "i4"), ("seg", "i4"), ("j", "i4"), ("rho", "f4"), ("z_re", "f4"),
                        ("z_im", "f4")])
+EVENT_DTYPE = np.dtype([("tmpl", "i4"), ("seg", "i4"), ("j", "i4"), ("rho", "f4"), ("z_re", "f4"),
+                        ("z_im", "f4"), ("n_trig", "i4"), ("n_tmpl", "i4")])
 INJ_DTYPE = np.dtype([("m1", "f8"), ("m2", "f8"), ("snr", "f8"), ("j0", "i8"), ("phi", "f8")])
 
 

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "mf_internal.h"
@@ -731,8 +732,8 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     }
     int pf = prof_begin(b, MF_STAGE_FINAL, 0.0, st);
     MF_CUDA(launch_sort_triggers(w.counter, std::max<int64_t>(trig_cap, 0), key_bits, w.staged, w.keys,
-                                 w.keys_tmp, w.idx_a, w.idx_b, w.ghist, w.tstat, w.tickets, trig, n_trig, w.status,
-                                 sm_count(), b->spin_limit, st));
+                                 w.keys_tmp, w.idx_a, w.idx_b, w.ghist, w.tstat, w.tickets, trig, nullptr, n_trig,
+                                 w.status, sm_count(), b->spin_limit, st));
     prof_end(b, pf, st);
     count_launches(sort_launches(key_bits));
     return MF_OK;
@@ -821,6 +822,98 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     if (exch) cudaFreeAsync(exch, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "chisq_series: %s", cudaGetErrorString(e));
+    count_launches(launches);
+    return MF_OK;
+}
+
+extern "C" int mf_cluster_triggers(const mf_trigger *trig, const int64_t *n_trig, int64_t trig_cap, int64_t n_tmpl,
+                                   int n_seg, int64_t max_N, int32_t window, mf_event *events, int64_t ev_cap,
+                                   int64_t *n_events, void *cuda_stream) {
+    if (!trig || !n_trig || !n_events || (ev_cap > 0 && !events)) return set_err(MF_EINVAL, "NULL argument");
+    if (trig_cap < 1 || trig_cap > ((int64_t)1 << 31)) return set_err(MF_EINVAL, "trig_cap out of range");
+    if (ev_cap < 0 || window < 0 || n_tmpl < 1 || n_seg < 1 || max_N < 2)
+        return set_err(MF_EINVAL, "ev_cap, window, n_tmpl, n_seg or max_N out of range");
+    KeyLayout kl;
+    kl.j_bits = ilog2(max_N) + ((max_N & (max_N - 1)) ? 1 : 0);
+    kl.seg_bits = bits_for(n_seg);
+    kl.tmpl_bits = bits_for(n_tmpl);
+    const int key_bits = kl.j_bits + kl.seg_bits + kl.tmpl_bits;
+    if (key_bits > 64) return set_err(MF_EINVAL, "cluster key needs %d bits", key_bits);
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t cap = trig_cap;
+    const int64_t nb = cluster_scan_blocks(cap);
+    ClusterScratch w;
+    std::vector<void *> bufs;
+    cudaError_t e = cudaSuccess;
+    auto get = [&](auto **ptr, size_t bytes) {
+        void *q = nullptr;
+        if (e == cudaSuccess) e = cudaMallocAsync(&q, bytes, st);
+        if (e == cudaSuccess) bufs.push_back(q);
+        *ptr = (std::remove_pointer_t<decltype(ptr)>)q;
+    };
+    get(&w.flag, sizeof(uint32_t) * cap);
+    get(&w.incl, sizeof(uint32_t) * cap);
+    get(&w.bsum, sizeof(uint32_t) * nb);
+    get(&w.members, sizeof(uint32_t) * cap);
+    get(&w.wsum, sizeof(uint32_t) * cap);
+    get(&w.rep_count, sizeof(uint32_t) * cap);
+    get(&w.idx_a, sizeof(uint32_t) * cap);
+    get(&w.idx_b, sizeof(uint32_t) * cap);
+    get(&w.perm, sizeof(uint32_t) * cap);
+    get(&w.ghist, sizeof(uint32_t) * 256 * 8);
+    get(&w.best, sizeof(unsigned long long) * cap);
+    get(&w.rep, sizeof(mf_trigger) * cap);
+    get(&w.sorted, sizeof(mf_trigger) * cap);
+    get(&w.keys, sizeof(uint64_t) * cap);
+    get(&w.keys_tmp, sizeof(uint64_t) * cap);
+    get(&w.tstat, sizeof(uint64_t) * sort_tile_words(cap));
+    get(&w.tickets, sizeof(unsigned) * 8);
+    get(&w.n_c, sizeof(int64_t));
+    get(&w.n_sorted, sizeof(int64_t));
+    get(&w.status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = launch_cluster(trig, n_trig, cap, window, kl, w, events, ev_cap, n_events, sm_count(), 4000000, st);
+    for (void *q : bufs) cudaFreeAsync(q, st);
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "cluster_triggers: %s",
+                       cudaGetErrorString(e));
+    count_launches(cluster_launches(key_bits));
+    return MF_OK;
+}
+
+extern "C" int mf_chisq_points(mf_bank b, const mf_segment *segs, int n_seg, const int32_t *rows, int64_t stride,
+                               int64_t n, int p, float *chisq, void *cuda_stream) {
+    if (!b || !segs || !rows || !chisq) return set_err(MF_EINVAL, "NULL argument");
+    if (n < 0 || stride < 3) return set_err(MF_EINVAL, "n < 0 or stride < 3");
+    if (p < 1 || p > kChisqMaxBands) return set_err(MF_EINVAL, "p = %d outside [1, %d]", p, kChisqMaxBands);
+    if (n_seg < 1 || n_seg > kRefineMaxSegs) return set_err(MF_EINVAL, "n_seg outside [1, %d]", kRefineMaxSegs);
+    if (n == 0) return MF_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (b->device != cur) return set_err(MF_EINVAL, "bank lives on device %d", b->device);
+    std::vector<SegDev> sd((size_t)n_seg);
+    for (int s = 0; s < n_seg; ++s) {
+        if (!segs[s] || segs[s]->device != cur) return set_err(MF_EINVAL, "segs[%d] is NULL or on another device", s);
+        sd[(size_t)s] = seg_dev(segs[s]);
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t chunk = std::min<int64_t>(n, 65535);
+    const int bpr = (int)std::max<int64_t>(4, std::min<int64_t>(64, (4 * (int64_t)sm_count() + chunk - 1) / chunk));
+    double2 *partial = nullptr;
+    cudaError_t e = cudaMallocAsync(&partial, sizeof(double2) * (size_t)bpr * chunk * p, st);
+    int launches = 0;
+    for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += chunk) {
+        const int64_t m = std::min<int64_t>(chunk, n - i0);
+        e = launch_chisq_points(sd.data(), n_seg, b->d_tmpl, (int)b->n, b->params.f_low, b->params.phase_mode,
+                                rows + i0 * stride, stride, m, p, bpr, partial, chisq + i0, st);
+        launches += 2;
+    }
+    if (partial) cudaFreeAsync(partial, st);
+    if (e != cudaSuccess)
+        return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "chisq_points: %s", cudaGetErrorString(e));
     count_launches(launches);
     return MF_OK;
 }

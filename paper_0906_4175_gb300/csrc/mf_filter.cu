@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kSortThreads)
                 const uint64_t *__restrict__ kin, const uint32_t *__restrict__ iin, uint64_t *__restrict__ kout,
                 uint32_t *__restrict__ iout, const uint32_t *__restrict__ ghist, uint64_t *tstat,
                 unsigned *tickets, const mf_trigger *__restrict__ staged, mf_trigger *__restrict__ out,
-                int *status, int64_t spin_limit) {
+                uint32_t *__restrict__ perm_out, int *status, int64_t spin_limit) {
     __shared__ uint32_t whist[kSortThreads / 32][256];
     __shared__ uint32_t base[256];
     __shared__ uint32_t gpre[256];
@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(kSortThreads)
                 const uint32_t pos = base[dg[r]] + whist[warp][dg[r]] + lr[r];
                 if (last) {
                     out[pos] = staged[id[r]];
+                    if (perm_out) perm_out[pos] = id[r];
                 } else {
                     kout[pos] = key[r];
                     iout[pos] = id[r];
@@ -411,8 +412,8 @@ __global__ void __launch_bounds__(kSortThreads)
 cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,
                                  const mf_trigger *staged, const uint64_t *keys, uint64_t *keys_tmp,
                                  uint32_t *idx_a, uint32_t *idx_b, uint32_t *ghist, uint64_t *tstat,
-                                 unsigned *tickets, mf_trigger *out, int64_t *n_out, int *status, int n_sm,
-                                 int64_t spin_limit, cudaStream_t st) {
+                                 unsigned *tickets, mf_trigger *out, uint32_t *perm_out, int64_t *n_out,
+                                 int *status, int n_sm, int64_t spin_limit, cudaStream_t st) {
     int npass = key_bits > 0 ? (key_bits + 7) / 8 : 1;
     if (npass > kSortMaxPass) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * 256 * kSortMaxPass, st);
@@ -427,7 +428,8 @@ cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap,
         uint64_t *kout = kbuf[p & 1];
         uint32_t *iout = ibuf[p & 1];
         k_sort_pass<<<grid, kSortThreads, 0, st>>>(counter, cap, p, p == npass - 1 ? 1 : 0, kin, iin, kout, iout,
-                                                   ghist, tstat, tickets, staged, out, status, spin_limit);
+                                                   ghist, tstat, tickets, staged, out, perm_out, status,
+                                                   spin_limit);
         kin = kout;
         iin = iout;
     }

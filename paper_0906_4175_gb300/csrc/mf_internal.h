@@ -132,8 +132,8 @@ cudaError_t launch_reduce_peaks(const SegDev &seg, const UnitInfo *units, int n_
 cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,
                                  const mf_trigger *staged, const uint64_t *keys, uint64_t *keys_tmp,
                                  uint32_t *idx_a, uint32_t *idx_b, uint32_t *ghist, uint64_t *tstat,
-                                 unsigned *tickets, mf_trigger *out, int64_t *n_out, int *status, int n_sm,
-                                 int64_t spin_limit, cudaStream_t st);
+                                 unsigned *tickets, mf_trigger *out, uint32_t *perm_out, int64_t *n_out,
+                                 int *status, int n_sm, int64_t spin_limit, cudaStream_t st);
 int sort_launches(int key_bits);   // kernels queued by launch_sort_triggers
 // tile status words the sort needs for cap records (one per 2048-key tile and digit)
 inline int64_t sort_tile_words(int64_t cap) { return ((cap + 2047) / 2048) * 256; }
@@ -149,6 +149,25 @@ cudaError_t launch_chisq_units(const SegDev &seg, const UnitInfo *all, int n_t, 
 // mode 0: first sub-band (store |raw|^2), 1: later sub-band (add), 2: full band (write chi^2)
 cudaError_t launch_chisq_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                                float *acc, int mode, int p, cudaStream_t st);
+
+// trigger clustering scratch (every array sized for the trigger capacity)
+struct ClusterScratch {
+    uint32_t *flag, *incl, *bsum, *members, *wsum, *rep_count, *idx_a, *idx_b, *perm, *ghist;
+    unsigned long long *best;
+    mf_trigger *rep, *sorted;
+    uint64_t *keys, *keys_tmp, *tstat;
+    unsigned *tickets;
+    int64_t *n_c, *n_sorted;
+    int *status;
+};
+cudaError_t launch_cluster(const mf_trigger *trig, const int64_t *n_trig, int64_t cap, int window, KeyLayout kl,
+                           ClusterScratch &w, mf_event *events, int64_t ev_cap, int64_t *n_events, int n_sm,
+                           int64_t spin_limit, cudaStream_t st);
+int cluster_launches(int key_bits);
+int64_t cluster_scan_blocks(int64_t cap);
+cudaError_t launch_chisq_points(const SegDev *segs, int n_seg, const double *tmpl, int n_t, double f_low,
+                                int phase_mode, const int32_t *rows, int64_t stride, int64_t n, int p, int bpr,
+                                double2 *partial, float *chisq, cudaStream_t st);
 
 // segments of one mf_refine_triggers_multi call (kernel-parameter table)
 constexpr int kRefineMaxSegs = 256;
