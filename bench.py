@@ -55,7 +55,8 @@ def _args():
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
-    ap.add_argument("--workload", default="scale", choices=["scale", "uneven", "precision", "refine", "chisq", "fft"],
+    ap.add_argument("--workload", default="scale",
+                    choices=["scale", "uneven", "precision", "refine", "chisq", "fft", "events"],
                     help="scale: the benchmark line; the others print their own measurement line "
                          "(uneven bank over mixed segment lengths, phase precision forms, trigger refinement)")
     return ap.parse_args()
@@ -502,6 +503,64 @@ def run_fft(args, mf, torch, dev):
     return 0
 
 
+def run_events(args, mf, torch, dev):
+    """The search tail on the bench workload: filter (1024 templates, 2^20
+    samples, threshold 6) -> events (mf_cluster_triggers, 1 s window) -> chi^2
+    of Eq. (5) at every event (mf_chisq_points, p = 16); CUDA events per
+    stage over the timed steps."""
+    import numpy as np
+    import workloads
+    wl = workloads.scale(0)
+    spec = wl.segments[0]
+    seg = mf.Segment(mf.synth_segment(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
+    cap = 1 << 22
+    out = (torch.empty((wl.n_templates, 4), dtype=torch.float32, device=dev),
+           torch.empty((cap, 6), dtype=torch.float32, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+    W = int(spec.fs)                      # 1 s
+    ev_cap = 1 << 16
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    steps = max(3, args.steps // 10)
+    times = {"filter": 0.0, "cluster": 0.0, "chisq": 0.0}
+    n_ev = 0
+    chi = None
+    for k in range(args.warmup + steps):
+        flush.fill_(k & 0xFF)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(st)
+        mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=out)
+        e[1].record(st)
+        ev, n_e = mf.cluster_triggers(out[1], out[2], wl.n_templates, 1, spec.N, W, ev_cap=ev_cap)
+        e[2].record(st)
+        n_ev = min(int(n_e.item()), ev_cap)    # host read between stages (the event count sizes the chi^2 call)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e2.record(st)
+        chi = mf.chisq_points(bank, [seg], ev[:n_ev], p=16)
+        e[3].record(st)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times["filter"] += e[0].elapsed_time(e[1])
+            times["cluster"] += e[1].elapsed_time(e[2])
+            times["chisq"] += e2.elapsed_time(e[3])
+    evs = mf.events_to_numpy(ev, n_e)
+    chi = chi.cpu().numpy()
+    order = np.argsort(-evs["rho"])[:8]
+    line = {"workload": "events", "metric": "events/s through filter -> clustering -> per-event chi^2",
+            "value": n_ev / ((times["filter"] + times["cluster"] + times["chisq"]) / steps / 1e3), "unit": "events/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections)",
+            "config": {"workload": WORKLOAD, "window_samples": W, "p": 16, "n_trig": int(out[2].item()),
+                       "n_events": n_ev, "l2": "flushed before every step"},
+            "ms_per_step": {k: v / steps for k, v in times.items()},
+            "loudest_events": [{"tmpl": int(evs["tmpl"][i]), "j": int(evs["j"][i]), "rho": float(evs["rho"][i]),
+                                "chisq": float(chi[i]), "n_trig": int(evs["n_trig"][i]),
+                                "n_tmpl": int(evs["n_tmpl"][i])} for i in order],
+            "injections_j": [int((spec.N - int(x["j0"])) % spec.N) for x in spec.injections]}
+    print(json.dumps(line))
+    return 0
+
+
 MSUN_S = 4.925490947e-6
 
 
@@ -760,7 +819,7 @@ def main():
         _b.build()
         import paper_0906_4175_gb300 as mf
         fn = {"uneven": run_uneven, "precision": run_precision, "refine": run_refine,
-              "chisq": run_chisq, "fft": run_fft}[args.workload]
+              "chisq": run_chisq, "fft": run_fft, "events": run_events}[args.workload]
         return fn(args, mf, torch, torch.device("cuda", 0))
     if args.warmup < 3:
         args.warmup = 3
