@@ -132,7 +132,7 @@ int mf_segment_destroy(mf_segment seg);
  * fs and PSD; device if s_on_device, else host) into the existing segment, as
  * mf_segment_upload would, reusing its device memory: a search that walks
  * consecutive segments of one length keeps one handle per stream.  The first
- * call allocates the conditioning scratch (about 20 N bytes) that the segment
+ * call allocates the conditioning scratch (about 12 N bytes) that the segment
  * then keeps; later calls with device samples allocate nothing and queue only
  * kernels on cuda_stream, so they may be captured in a CUDA graph together
  * with mf_filter_bank (the first call must precede the capture).  Work already

@@ -155,6 +155,8 @@ struct mf_bank_s {
     Workspace ws;
     bool prof_on = false;
     std::vector<ProfRec> prof;
+    cudaStream_t side = nullptr;      // anchors of the next batch run here, beside pass 2
+    cudaEvent_t ev_p1 = nullptr, ev_anc = nullptr;
     int64_t stall_unit = -1;          // test hook (mf_bank_debug_stall)
     long long spin_limit = 4000000;   // bounded-wait iterations, back-off <= ~1 us each
     // schedule (defaults until mf_autotune measures this bank): 0 = persistent
@@ -194,14 +196,14 @@ struct mf_segment_s {
     // Eq. (2) parameters) and, after the first refresh, conditioning scratch
     double *psd = nullptr;
     double psd_f0 = 0.0, psd_S0 = 0.0;
+    float *fac = nullptr;          // a_k = alpha f^(-7/6) dt / S_k: W_k = a_k conj(X_k) for new samples
     float2 *r_exch = nullptr, *r_X = nullptr;
-    double *r_q = nullptr, *r_btmp = nullptr;
     float *r_s = nullptr;
     void release() {
-        cudaFree(W); cudaFree(P); cudaFree(consts); cudaFree(psd);
-        cudaFree(r_exch); cudaFree(r_X); cudaFree(r_q); cudaFree(r_btmp); cudaFree(r_s);
-        W = nullptr; P = nullptr; consts = nullptr; psd = nullptr;
-        r_exch = nullptr; r_X = nullptr; r_q = nullptr; r_btmp = nullptr; r_s = nullptr;
+        cudaFree(W); cudaFree(P); cudaFree(consts); cudaFree(psd); cudaFree(fac);
+        cudaFree(r_exch); cudaFree(r_X); cudaFree(r_s);
+        W = nullptr; P = nullptr; consts = nullptr; psd = nullptr; fac = nullptr;
+        r_exch = nullptr; r_X = nullptr; r_s = nullptr;
     }
 };
 
@@ -279,6 +281,9 @@ extern "C" int mf_bank_destroy(mf_bank b) {
     for (auto &r : b->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     b->ws.release();
     cudaFree(b->d_tmpl);
+    if (b->ev_p1) cudaEventDestroy(b->ev_p1);
+    if (b->ev_anc) cudaEventDestroy(b->ev_anc);
+    if (b->side) cudaStreamDestroy(b->side);
     delete b;
     return MF_OK;
 }
@@ -318,6 +323,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     double *q = nullptr, *btmp = nullptr, *psd_dev = nullptr;
     const int64_t nbt = prefix_block_tmp_count(half);
     cudaError_t e = cudaMalloc(&g->W, sizeof(float2) * half);
+    if (e == cudaSuccess) e = cudaMalloc(&g->fac, sizeof(float) * half);
     if (e == cudaSuccess) e = cudaMalloc(&g->P, sizeof(double) * (half + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->consts, sizeof(SegConsts));
     if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * N, st);
@@ -338,7 +344,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     if (e == cudaSuccess) e = launch_forward_fft(s_use, N, exch, X, st);
     if (e == cudaSuccess) e = launch_psd_weights(X, psd_dev, psd_f0, psd_S0, N, fs, q, st);
     if (e == cudaSuccess) e = launch_prefix_f64(q, half, g->P, btmp, st);
-    if (e == cudaSuccess) e = launch_weight_data(X, psd_dev, psd_f0, psd_S0, N, fs, g->P, g->consts, g->W, st);
+    if (e == cudaSuccess) e = launch_weight_data(X, psd_dev, psd_f0, psd_S0, N, fs, g->P, g->consts, g->W, g->fac, st);
     if (e == cudaSuccess) count_launches(7);   // 2 FFT passes, weights, 3 scan kernels, weighting
     if (s_dev) cudaFreeAsync(s_dev, st);
     if (exch) cudaFreeAsync(exch, st);
@@ -367,14 +373,11 @@ extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device,
     const int64_t N = g->N, half = N / 2;
     if (!g->r_exch) {
         if (capturing) return set_err(MF_EINVAL, "the first mf_segment_refresh of a segment must precede stream capture");
-        const int64_t nbt = prefix_block_tmp_count(half);
         cudaError_t e = cudaMalloc(&g->r_exch, sizeof(float2) * N);
         if (e == cudaSuccess) e = cudaMalloc(&g->r_X, sizeof(float2) * (half + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&g->r_q, sizeof(double) * half);
-        if (e == cudaSuccess) e = cudaMalloc(&g->r_btmp, sizeof(double) * nbt);
         if (e != cudaSuccess) {
-            cudaFree(g->r_exch); cudaFree(g->r_X); cudaFree(g->r_q); cudaFree(g->r_btmp);
-            g->r_exch = nullptr; g->r_X = nullptr; g->r_q = nullptr; g->r_btmp = nullptr;
+            cudaFree(g->r_exch); cudaFree(g->r_X);
+            g->r_exch = nullptr; g->r_X = nullptr;
             return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "segment_refresh: %s",
                            cudaGetErrorString(e));
         }
@@ -386,11 +389,10 @@ extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device,
         MF_CUDA(cudaMemcpyAsync(g->r_s, s, sizeof(float) * N, cudaMemcpyHostToDevice, st));
         s_use = g->r_s;
     }
+    // the PSD and with it P, sigma's normalisation and the factors a_k are unchanged
     MF_CUDA(launch_forward_fft(s_use, N, g->r_exch, g->r_X, st));
-    MF_CUDA(launch_psd_weights(g->r_X, g->psd, g->psd_f0, g->psd_S0, N, g->fs, g->r_q, st));
-    MF_CUDA(launch_prefix_f64(g->r_q, half, g->P, g->r_btmp, st));
-    MF_CUDA(launch_weight_data(g->r_X, g->psd, g->psd_f0, g->psd_S0, N, g->fs, g->P, g->consts, g->W, st));
-    count_launches(7);
+    MF_CUDA(launch_apply_weights(g->r_X, g->fac, N, g->W, st));
+    count_launches(3);
     if (!s_on_device) MF_CUDA(cudaStreamSynchronize(st));   // host s consumed before return
     return MF_OK;
 }
@@ -594,7 +596,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         seg_batch[(size_t)s] = bt;
         const int lgD = choose_log2D(b, segs[s]);
         exch_elems = std::max(exch_elems, bt * segs[s]->N);
-        anc_elems = std::max(anc_elems, bt * (((segs[s]->N / 2) >> lgD) + 2));
+        anc_elems = std::max(anc_elems, 2 * bt * (((segs[s]->N / 2) >> lgD) + 2));   // two batches in flight
         nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -703,22 +705,49 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             continue;
         }
         const int64_t batch = seg_batch[(size_t)s];
-        for (int u0 = 0; u0 < n_t; u0 += (int)batch) {
+        // Anchors of batch i + 1 run on a side stream beside pass 2 of batch i,
+        // into the other of two anchor slots (its previous reader, pass 1 of
+        // batch i - 1, finished before pass 1 of batch i, which the side
+        // stream waits for).  Stage profiling keeps everything on one stream.
+        const bool overlap = anchors && !b->prof_on && batch < n_t;
+        if (overlap && !b->side) {
+            if (capturing) return set_err(MF_EINVAL, "call mf_filter_bank once before capturing it");
+            MF_CUDA(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+            MF_CUDA(cudaEventCreateWithFlags(&b->ev_p1, cudaEventDisableTiming));
+            MF_CUDA(cudaEventCreateWithFlags(&b->ev_anc, cudaEventDisableTiming));
+        }
+        const int64_t slot_elems = batch * man;
+        for (int u0 = 0, bi = 0; u0 < n_t; u0 += (int)batch, ++bi) {
             const int nb = (int)std::min<int64_t>(batch, n_t - u0);
+            const int64_t aoff = overlap ? (bi & 1) * slot_elems : 0;
             double by_band = 0.0, by_anc = 0.0;
             if (b->prof_on)
                 for (int t = u0; t < u0 + nb; ++t) { by_band += band_bytes[(size_t)t]; by_anc += anc_bytes[(size_t)t]; }
             const double exch_bytes = 8.0 * (double)sd.N * nb;
-            if (anchors) {
+            if (anchors && (!overlap || bi == 0)) {
                 pi = prof_begin(b, MF_STAGE_ANCHORS, by_anc, st);
-                MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, u0, nb, lgD, man, w.anchors, w.anchors4, st));
+                MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, u0, nb, lgD, man, w.anchors + aoff, w.anchors4 + aoff,
+                                       st));
                 prof_end(b, pi, st);
                 count_launches(1);
+            } else if (overlap) {
+                MF_CUDA(cudaStreamWaitEvent(st, b->ev_anc, 0));
             }
             pi = prof_begin(b, MF_STAGE_PASS1, by_band + by_anc + exch_bytes, st);
-            MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors, w.anchors4, w.exch,
+            MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors + aoff, w.anchors4 + aoff, w.exch,
                                  b->params.phase_mode, b->d_tmpl, st));
             prof_end(b, pi, st);
+            if (overlap && u0 + batch < n_t) {
+                const int u1 = u0 + (int)batch;
+                const int nb1 = (int)std::min<int64_t>(batch, n_t - u1);
+                const int64_t aoff1 = ((bi + 1) & 1) * slot_elems;
+                MF_CUDA(cudaEventRecord(b->ev_p1, st));
+                MF_CUDA(cudaStreamWaitEvent(b->side, b->ev_p1, 0));
+                MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, u1, nb1, lgD, man, w.anchors + aoff1,
+                                       w.anchors4 + aoff1, b->side));
+                MF_CUDA(cudaEventRecord(b->ev_anc, b->side));
+                count_launches(1);
+            }
             pi = prof_begin(b, MF_STAGE_PASS2, exch_bytes, st);
             MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                  std::max<int64_t>(trig_cap, 0), st));

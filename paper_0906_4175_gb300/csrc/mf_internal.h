@@ -102,8 +102,9 @@ cudaError_t launch_psd_weights(const float2 *X, const double *psd, double psd_f0
                                int64_t N, double fs, double *q, cudaStream_t st);
 cudaError_t launch_prefix_f64(const double *q, int64_t n, double *P, double *block_tmp, cudaStream_t st);
 cudaError_t launch_weight_data(const float2 *X, const double *psd, double psd_f0, double psd_S0,
-                               int64_t N, double fs, const double *P, SegConsts *consts, float2 *W,
+                               int64_t N, double fs, const double *P, SegConsts *consts, float2 *W, float *fac,
                                cudaStream_t st);
+cudaError_t launch_apply_weights(const float2 *X, const float *fac, int64_t N, float2 *W, cudaStream_t st);
 int64_t prefix_block_tmp_count(int64_t n);
 
 // synthesis (mf_synth.cu)

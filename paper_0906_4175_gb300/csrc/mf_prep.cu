@@ -225,10 +225,12 @@ cudaError_t launch_prefix_f64(const double *q, int64_t n, double *P, double *blo
     return cudaGetLastError();
 }
 
-// W_k = alpha f^(-7/6) dt conj(X_k)/S_k for 1 <= k < N/2, W_0 = 0
+// W_k = alpha f^(-7/6) dt conj(X_k)/S_k for 1 <= k < N/2, W_0 = 0; the real
+// factor a_k = alpha f^(-7/6) dt / S_k depends on the PSD only and is kept
+// in fac (when not NULL) so that new samples need only W_k = a_k conj(X_k)
 __global__ void k_weight_data(const float2 *__restrict__ X, const double *__restrict__ psd, double f0, double S0,
                               int64_t N, double fs, const double *__restrict__ P, SegConsts *consts,
-                              float2 *__restrict__ W) {
+                              float2 *__restrict__ W, float *__restrict__ fac) {
     const int64_t half = N / 2;
     const double df = fs / (double)N, dt = 1.0 / fs;
     const double Ptot = P[half];
@@ -239,21 +241,45 @@ __global__ void k_weight_data(const float2 *__restrict__ X, const double *__rest
     }
     const float a_eq2 = (float)(alpha * dt / S0);
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half; k += (int64_t)gridDim.x * blockDim.x) {
-        if (k == 0) { W[0] = make_float2(0.f, 0.f); continue; }
+        if (k == 0) {
+            W[0] = make_float2(0.f, 0.f);
+            if (fac) fac[0] = 0.f;
+            continue;
+        }
         const float f = (float)((double)k * df);
         const float p76 = powf(f, -7.0f / 6.0f);
         const float a = psd ? (float)(alpha * dt / psd[k]) * p76 : a_eq2 * (p76 / psd_eq2_bracket(f, (float)f0));
         const float2 x = X[k];
         W[k] = make_float2(a * x.x, -a * x.y);
+        if (fac) fac[k] = a;
     }
 }
 
 cudaError_t launch_weight_data(const float2 *X, const double *psd, double psd_f0, double psd_S0, int64_t N,
-                               double fs, const double *P, SegConsts *consts, float2 *W, cudaStream_t st) {
+                               double fs, const double *P, SegConsts *consts, float2 *W, float *fac,
+                               cudaStream_t st) {
     const int64_t half = N / 2;
     int blocks = (int)((half + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_weight_data<<<blocks, 256, 0, st>>>(X, psd, psd_f0, psd_S0, N, fs, P, consts, W);
+    k_weight_data<<<blocks, 256, 0, st>>>(X, psd, psd_f0, psd_S0, N, fs, P, consts, W, fac);
+    return cudaGetLastError();
+}
+
+// W_k = a_k conj(X_k) with the segment's kept factors (new samples, same PSD)
+__global__ void k_apply_weights(const float2 *__restrict__ X, const float *__restrict__ fac, int64_t half,
+                                float2 *__restrict__ W) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half; k += (int64_t)gridDim.x * blockDim.x) {
+        const float a = fac[k];
+        const float2 x = X[k];
+        W[k] = make_float2(a * x.x, -a * x.y);
+    }
+}
+
+cudaError_t launch_apply_weights(const float2 *X, const float *fac, int64_t N, float2 *W, cudaStream_t st) {
+    const int64_t half = N / 2;
+    int blocks = (int)((half + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_apply_weights<<<blocks, 256, 0, st>>>(X, fac, half, W);
     return cudaGetLastError();
 }
 
