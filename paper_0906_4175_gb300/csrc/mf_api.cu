@@ -21,6 +21,7 @@ cudaError_t prep_kernel_attributes();
 cudaError_t synth_kernel_attributes();
 cudaError_t refine_kernel_attributes();
 cudaError_t chisq_kernel_attributes();
+cudaError_t rows_kernel_attributes();
 cudaError_t persist_kernel_attributes();
 }  // namespace mf
 
@@ -76,6 +77,7 @@ static int ensure_device_init() {
     MF_CUDA(synth_kernel_attributes());
     MF_CUDA(refine_kernel_attributes());
     MF_CUDA(chisq_kernel_attributes());
+    MF_CUDA(rows_kernel_attributes());
     done.push_back(dev);
     return MF_OK;
 }
@@ -494,6 +496,14 @@ static int ensure_workspace(mf_bank_s *b, int64_t exch_elems, int64_t cap, int64
 constexpr int kLA = 4, kS = 8, kSA = kLA + 4;
 constexpr double kSplit = 0.60;
 
+// Pass 2 as whole rows per warp (row length 1024) unless MFGB_P2ROWS=0.
+static bool use_rows(const mf_bank_s *b, const mf_segment_s *g) {
+    (void)b;
+    if (!pass2_rows_applies(g->log2N)) return false;
+    const char *e = getenv("MFGB_P2ROWS");
+    return !(e && strcmp(e, "0") == 0);
+}
+
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
     if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32) return false;
     if (const char *e = getenv("MFGB_SCHED")) {
@@ -598,6 +608,8 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         exch_elems = std::max(exch_elems, bt * segs[s]->N);
         anc_elems = std::max(anc_elems, 2 * bt * (((segs[s]->N / 2) >> lgD) + 2));   // two batches in flight
         nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
+        if (!use_persistent(b, segs[s]) && use_rows(b, segs[s]))   // one partial per row (N2 rows)
+            nblk = std::max(nblk, (int64_t)1 << (segs[s]->log2N / 2));
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool capturing = stream_capturing(st);
@@ -612,7 +624,8 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const SegDev sd = seg_dev(segs[s]);
         const int lgD = choose_log2D(b, segs[s]);
         const int man = (int)(((segs[s]->N / 2) >> lgD) + 2);
-        const int nbk = pass2_blocks(sd.log2N);
+        const bool rows = !use_persistent(b, segs[s]) && use_rows(b, segs[s]);
+        const int nbk = rows ? (1 << sd.log2N2) : pass2_blocks(sd.log2N);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
         // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
         std::vector<double> band_bytes, anc_bytes;
@@ -749,8 +762,12 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
                 count_launches(1);
             }
             pi = prof_begin(b, MF_STAGE_PASS2, exch_bytes, st);
-            MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
-                                 std::max<int64_t>(trig_cap, 0), st));
+            if (rows)
+                MF_CUDA(launch_pass2_rows(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
+                                          std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, sm_count(), st));
+            else
+                MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
+                                     std::max<int64_t>(trig_cap, 0), st));
             prof_end(b, pi, st);
             count_launches(2);
         }

@@ -247,6 +247,14 @@ __device__ __forceinline__ void fill_twiddles(float2 *tw) {
     }
 }
 
+// Sinks may define after_loads(): called by the last stage once this thread's
+// shared-memory reads are issued and before its arithmetic (a warp-owned
+// region can be refilled from there on).
+template <class T, class = void>
+struct has_after_loads { static constexpr bool value = false; };
+template <class T>
+struct has_after_loads<T, decltype((void)&T::after_loads, void())> { static constexpr bool value = true; };
+
 // One Stockham stage reading from and (unless LAST) writing to shared memory.
 // Ns = product of earlier radices; each thread runs 32/R butterflies b = t + i*T.
 template <int L, int R, int Ns, int SIGN, bool LAST, class Snk>
@@ -262,6 +270,7 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int
         for (int r = 0; r < R; ++r) v[i * R + r] = sq[spad(b + r * SPAN)];
     }
     if constexpr (!LAST) __syncthreads();
+    if constexpr (LAST && has_after_loads<Snk>::value) snk.after_loads();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int b = t + i * T;

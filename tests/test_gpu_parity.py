@@ -56,7 +56,7 @@ def test_tiny_workload_full_series(mf):
 
 
 @pytest.mark.parametrize("lg,fs", [(10, 4096.0), (11, 4096.0), (12, 4096.0), (13, 2048.0), (14, 4096.0),
-                                   (15, 4096.0), (17, 4096.0), (18, 4096.0)])
+                                   (15, 4096.0), (17, 4096.0), (18, 4096.0), (19, 4096.0), (20, 4096.0)])
 def test_sizes_full_series(mf, lg, fs):
     """Every supported FFT split from 32x32 up to 512x512 (ragged tails: the
     heaviest templates cut at f_isco far below Nyquist)."""
@@ -314,6 +314,28 @@ def test_persistent_and_batch_schedulers_agree(mf, monkeypatch):
     b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 18)]
     assert int(a[2][0]) == int(b[2][0]) > 0
     n = int(a[2][0])
+    assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8))
+    assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
+
+
+@pytest.mark.parametrize("lg", [19, 20])
+def test_pass2_rows_and_tiles_agree(mf, monkeypatch, lg):
+    """Pass 2 with whole rows per warp (bulk-copy prefetch, row length 1024)
+    and the per-tile pass 2 give bit-identical peaks and triggers."""
+    import torch
+    wl = workloads.small(seed=40 + lg, N=1 << lg, fs=4096.0, n_templates=11, m_lo=1.1, m_hi=9.0)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    monkeypatch.setenv("MFGB_BATCH", "4")          # ragged batches: 4 + 4 + 3
+    a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 20)]
+    monkeypatch.setenv("MFGB_P2ROWS", "0")
+    b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 20)]
+    assert bank.check() == 0
+    n = int(a[2][0])
+    assert int(b[2][0]) == n > 0
     assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8))
     assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
 
