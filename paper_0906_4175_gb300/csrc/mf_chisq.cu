@@ -192,6 +192,10 @@ cudaError_t launch_chisq_pass2(const SegDev &seg, const UnitInfo *units, int uni
 }
 
 cudaError_t chisq_kernel_attributes() {
+    {
+        cudaError_t e0 = init_twiddle_tables();
+        if (e0 != cudaSuccess) return e0;
+    }
     for (int lg = 10; lg <= 22; ++lg) {
         ChiAttrOp op;
         cudaError_t e = dispatch_split(lg, op);

@@ -226,10 +226,9 @@ struct TwTable {
     static constexpr int SIZE = (FftShape<L>::NST == 1) ? 0 : S1 + S2;
 };
 
-// Fill the table of an L-point FFT (all threads of the block; callers
-// synchronise before first use).
+// Compute the table of an L-point FFT (all threads of the block).
 template <int L>
-__device__ __forceinline__ void fill_twiddles(float2 *tw) {
+__device__ __forceinline__ void compute_twiddles(float2 *tw) {
     using S = FftShape<L>;
     if constexpr (S::NST >= 2) {
         constexpr int LG1 = cx_ilog2(32 * S::R1);
@@ -254,6 +253,42 @@ template <class T, class = void>
 struct has_after_loads { static constexpr bool value = false; };
 template <class T>
 struct has_after_loads<T, decltype((void)&T::after_loads, void())> { static constexpr bool value = true; };
+
+// The tables of every length, computed once per device by init_twiddle_tables()
+// (one copy per translation unit that launches FFT kernels), so that a CTA
+// only copies its table into shared memory instead of evaluating it.
+template <int L>
+__host__ __device__ constexpr int tw_offset() {
+    if constexpr (L <= 32) return 0;
+    else return tw_offset<L / 2>() + TwTable<L / 2>::SIZE;
+}
+constexpr int kTwTotal = tw_offset<4096>();
+static __device__ float2 g_tw_tables[kTwTotal];
+
+template <int L>
+__global__ void k_init_twiddles() {
+    compute_twiddles<L>(g_tw_tables + tw_offset<L>());
+}
+
+static inline cudaError_t init_twiddle_tables() {
+    k_init_twiddles<64><<<1, 256>>>();
+    k_init_twiddles<128><<<1, 256>>>();
+    k_init_twiddles<256><<<1, 256>>>();
+    k_init_twiddles<512><<<1, 256>>>();
+    k_init_twiddles<1024><<<1, 256>>>();
+    k_init_twiddles<2048><<<1, 256>>>();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaDeviceSynchronize();
+}
+
+// Copy the table of an L-point FFT into shared memory (all threads of the
+// block; callers synchronise before first use).
+template <int L>
+__device__ __forceinline__ void fill_twiddles(float2 *tw) {
+    const float2 *src = g_tw_tables + tw_offset<L>();
+    for (int m = threadIdx.x; m < TwTable<L>::SIZE; m += blockDim.x) tw[m] = __ldg(&src[m]);
+}
 
 // One Stockham stage reading from and (unless LAST) writing to shared memory.
 // Ns = product of earlier radices; each thread runs 32/R butterflies b = t + i*T.

@@ -175,6 +175,10 @@ int pass2_blocks(int log2N) {
 }
 
 cudaError_t filter_kernel_attributes() {
+    {
+        cudaError_t e0 = init_twiddle_tables();
+        if (e0 != cudaSuccess) return e0;
+    }
     for (int lg = 10; lg <= 22; ++lg) {
         AttrOp op;
         cudaError_t e = dispatch_split(lg, op);

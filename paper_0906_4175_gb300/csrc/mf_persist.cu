@@ -357,6 +357,10 @@ int g_blocks_per_sm[32];
 }  // namespace
 
 cudaError_t persist_kernel_attributes() {
+    {
+        cudaError_t e0 = init_twiddle_tables();
+        if (e0 != cudaSuccess) return e0;
+    }
     for (int lg = 13; lg <= 22; ++lg) {
         PersistAttrOp op{lg, g_blocks_per_sm};
         cudaError_t e = dispatch_split(lg, op);

@@ -255,6 +255,10 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
 }
 
 cudaError_t rows_kernel_attributes() {
+    {
+        cudaError_t e0 = init_twiddle_tables();
+        if (e0 != cudaSuccess) return e0;
+    }
     return cudaFuncSetAttribute(k_pass2_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass2_rows_smem());
 }
 

@@ -112,6 +112,10 @@ cudaError_t launch_inverse_real_fft(const float2 *Y, int64_t N, double scale, fl
 }
 
 cudaError_t synth_kernel_attributes() {
+    {
+        cudaError_t e0 = init_twiddle_tables();
+        if (e0 != cudaSuccess) return e0;
+    }
     for (int lg = 10; lg <= 22; ++lg) {
         InvAttrOp op;
         cudaError_t e = dispatch_split(lg, op);
