@@ -219,7 +219,8 @@ def cpu_baseline(wl, cpu_seconds: float, gpu_check=None):
     dt = time.perf_counter() - t0
     res = {"value": n_s / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
            "sample": "%d of %d templates (seeded), full N=2^20 segment, FP64 radix-2 FFT, %.1f s wall on %d threads"
-                     % (n_s, wl.n_templates, dt, used)}
+                     % (n_s, wl.n_templates, dt, used),
+           "single_thread_value": 1.0 / max(t1, 1e-9)}
     acc = None
     if gpu_check is not None:
         acc = gpu_check(s, sel, peaks)
@@ -888,6 +889,8 @@ def main():
         assert bank.check() == 0
         assert int(outb[2].item()) == n_trig
 
+    step_medians = []
+
     def timed(run, profile):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
@@ -910,7 +913,9 @@ def main():
         if profile:
             pr = bank.profile_read()
             bank.profile(False)
-        return sum(a.elapsed_time(b) for a, b in ev), w, n_l, pr
+        per = [a.elapsed_time(b) for a, b in ev]
+        step_medians.append(statistics.median(per))
+        return sum(per), w, n_l, pr
 
     sampler = ClockSampler(local)
     sampler.mark_begin()
@@ -940,6 +945,7 @@ def main():
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
             "timed_on": "the eager steps (same workload, per-stage CUDA events on the launching stream)",
+            "effective": bool(traffic is not None and traffic < d_bytes / max(1, d_n)),
             "algorithmic_bytes_per_launch": d_bytes / max(1, d_n), "launches": d_n,
             "avg_launch_ms": d_ms / max(1, d_n), "templates_per_launch": tmpl_per_launch,
             "stage_share": {k: v[0] / sum(x[0] for x in stages.values()) for k, v in stages.items()}}
@@ -1006,6 +1012,7 @@ def main():
         cpu, acc = cpu_baseline(wl, args.cpu_seconds, gpu_check)
 
     launch_mode = {"mode": "eager" if graph is None else "cuda_graph",
+                   "median_ms_per_step": step_medians[-1],
                    "eager_ms_per_step": eager_ms / args.steps,
                    "graph_ms_per_step": tot_ms / args.steps if graph is not None else None,
                    "launches_per_step": launches / args.steps}
