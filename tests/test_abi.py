@@ -64,6 +64,37 @@ def test_invalid_arguments_without_device(L):
     assert L.mf_bank_destroy(None) == 0 and L.mf_segment_destroy(None) == 0
 
 
+def test_invalid_arguments_of_the_later_entry_points(L):
+    """chi^2, events, batched FFT, multi-row refinement and segment refresh
+    reject bad arguments before any device work."""
+    from paper_0906_4175_gb300 import _native
+    EINVAL = _native.MF_EINVAL
+    x = np.zeros(8, dtype=np.float32)
+    n = np.zeros(1, dtype=np.int64)
+    # mf_chisq_series: NULL bank / segment / outputs
+    assert L.mf_chisq_series(None, None, None, 1, 16, None, None, None) == EINVAL
+    # mf_chisq_points: NULL bank, bad stride
+    assert L.mf_chisq_points(None, None, 1, None, 6, 1, 16, None, None) == EINVAL
+    # mf_cluster_triggers: NULLs, negative window, bad capacity
+    assert L.mf_cluster_triggers(None, None, 16, 4, 1, 1024, 8, None, 16, None, None) == EINVAL
+    assert L.mf_cluster_triggers(x.ctypes.data, n.ctypes.data, 16, 4, 1, 1024, -1, x.ctypes.data, 16,
+                                 n.ctypes.data, None) == EINVAL
+    assert L.mf_cluster_triggers(x.ctypes.data, n.ctypes.data, 0, 4, 1, 1024, 8, x.ctypes.data, 16,
+                                 n.ctypes.data, None) == EINVAL
+    # mf_fft_c2c: length, sign, alignment
+    assert L.mf_fft_c2c(x.ctypes.data, x.ctypes.data, 1000, 1, -1, None) == EINVAL
+    assert b"power of two" in L.mf_last_error()
+    assert L.mf_fft_c2c(x.ctypes.data, x.ctypes.data, 1024, 1, 2, None) == EINVAL
+    assert L.mf_fft_c2c(x.ctypes.data + 4, x.ctypes.data, 1024, 1, 1, None) == EINVAL
+    assert L.mf_fft_c2c(x.ctypes.data, x.ctypes.data, 1024, 0, 1, None) == EINVAL
+    # mf_refine_triggers_multi: NULL row map, too many segments
+    assert L.mf_refine_triggers_multi(None, 1, None, None, None, 1, None, None, None, None) == EINVAL
+    assert L.mf_refine_triggers_multi(x.ctypes.data, 257, x.ctypes.data, None, x.ctypes.data, 1, None,
+                                      x.ctypes.data, x.ctypes.data, None) == EINVAL
+    # mf_segment_refresh: NULL segment
+    assert L.mf_segment_refresh(None, x.ctypes.data, 1, None) == EINVAL
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     """No CPU fallback: a missing library is an ImportError, not a silent substitute."""
     from paper_0906_4175_gb300 import _native
