@@ -78,7 +78,7 @@ struct TemplateSrc {
         for (int r = 0; r < 16; ++r) {
             const int k = k0 + ((r * T) << LG1);
             in[r] = (k >= u.k_lo) && (k < u.k_hi);
-            w[r] = __ldg(&p.W[in[r] ? k : u.k_lo]);
+            w[r] = in[r] ? __ldg(&p.W[k]) : czero();   // no load outside the band
         }
         if (D >= C && p.log2D <= LG1) {
             // Every column of this tile falls in the same anchor group on a
