@@ -608,8 +608,8 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         exch_elems = std::max(exch_elems, bt * segs[s]->N);
         anc_elems = std::max(anc_elems, 2 * bt * (((segs[s]->N / 2) >> lgD) + 2));   // two batches in flight
         nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
-        if (!use_persistent(b, segs[s]) && use_rows(b, segs[s]))   // one partial per row (N2 rows)
-            nblk = std::max(nblk, (int64_t)1 << (segs[s]->log2N / 2));
+        if (!use_persistent(b, segs[s]) && use_rows(b, segs[s]))   // one partial per row and warp
+            nblk = std::max(nblk, (int64_t)pass2_rows_partials(segs[s]->log2N));
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool capturing = stream_capturing(st);
@@ -625,7 +625,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const int lgD = choose_log2D(b, segs[s]);
         const int man = (int)(((segs[s]->N / 2) >> lgD) + 2);
         const bool rows = !use_persistent(b, segs[s]) && use_rows(b, segs[s]);
-        const int nbk = rows ? (1 << sd.log2N2) : pass2_blocks(sd.log2N);
+        const int nbk = rows ? pass2_rows_partials(sd.log2N) : pass2_blocks(sd.log2N);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
         // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
         std::vector<double> band_bytes, anc_bytes;

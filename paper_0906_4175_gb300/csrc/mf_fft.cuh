@@ -290,9 +290,15 @@ __device__ __forceinline__ void fill_twiddles(float2 *tw) {
     for (int m = threadIdx.x; m < TwTable<L>::SIZE; m += blockDim.x) tw[m] = __ldg(&src[m]);
 }
 
+// Barrier between the stages of one FFT: the whole CTA by default; kernels in
+// which a smaller group of threads owns a sequence pass their own.
+struct CtaSync {
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
 // One Stockham stage reading from and (unless LAST) writing to shared memory.
 // Ns = product of earlier radices; each thread runs 32/R butterflies b = t + i*T.
-template <int L, int R, int Ns, int SIGN, bool LAST, class Snk>
+template <int L, int R, int Ns, int SIGN, bool LAST, class Snk, class Sync = CtaSync>
 __device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int seq, int t, Snk &snk) {
     constexpr int T = L / 32;
     constexpr int NB = 32 / R;
@@ -304,7 +310,7 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i * R + r] = sq[spad(b + r * SPAN)];
     }
-    if constexpr (!LAST) __syncthreads();
+    if constexpr (!LAST) Sync::sync();
     if constexpr (LAST && has_after_loads<Snk>::value) snk.after_loads();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
@@ -327,7 +333,7 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int
             for (int r = 0; r < R; ++r) sq[spad(idxD + r * Ns)] = v[i * R + r];
         }
     }
-    if constexpr (!LAST) __syncthreads();
+    if constexpr (!LAST) Sync::sync();
 }
 
 // Full CTA FFT.  tw: the TwTable<L> twiddles in shared memory, filled and

@@ -130,6 +130,7 @@ cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, in
 int pass2_blocks(int log2N);
 // pass 2 with whole rows per warp and bulk-copy prefetch (row length 1024 only)
 bool pass2_rows_applies(int log2N);
+int pass2_rows_partials(int log2N);
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,

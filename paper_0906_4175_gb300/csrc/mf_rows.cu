@@ -1,21 +1,22 @@
 // mf_rows.cu -- pass 2 of the filter (row IFFTs + rho epilogue) as a
-// persistent kernel in which every warp owns whole rows, for row length
-// N1 = 1024 (N = 2^19, 2^20).
+// persistent kernel in which a group of G warps owns whole rows: one warp for
+// row length N1 = 1024 (N = 2^19, 2^20), two for N1 = 2048 (N = 2^21, 2^22).
 //
-// Row j2 of batch entry b is E[b N + j2 N1 .. + N1), 8 KiB contiguous.  Each
-// warp works through rows w, w + W, w + 2W, ... (W = warps in the grid) in
-// its own shared-memory region:
+// Row j2 of batch entry b is E[b N + j2 N1 .. + N1), contiguous.  Each group
+// works through rows g, g + W, g + 2W, ... (W = groups in the grid) in its
+// own shared-memory region:
 //   1. wait for the row's bulk copy (cp.async.bulk, completion counted on the
-//      warp's mbarrier; bounded wait, status bit 1 and stop on expiry);
+//      group's mbarrier; bounded wait, status bit 1 and stop on expiry);
 //   2. stage 0 (radix 32) from the staged row, written back in the padded
-//      Stockham layout over the same region;
-//   3. stage 1 reads the region, then -- before its arithmetic -- lane 0
-//      starts the bulk copy of the warp's next row into the region, so the
-//      copy runs under the last stage and the rho epilogue;
+//      Stockham layout over the same region (then the middle stage, N1 = 2048);
+//   3. the last stage reads the region, then -- before its arithmetic -- the
+//      group's first thread starts the bulk copy of the group's next row into
+//      the region, so the copy runs under the last stage and the epilogue;
 //   4. epilogue as in the per-tile pass 2 (argmax with the lowest-j rule,
-//      warp-aggregated trigger append), the row's argmax to partials[unit][j2].
-// The twiddle table is filled once per CTA; after start-up no CTA barrier is
-// needed, since a row never leaves its warp.
+//      warp-aggregated trigger append), each warp's argmax of the row to
+//      partials[unit][j2][warp of the group].
+// The twiddle table is filled once per CTA; the stages of a row synchronise
+// only its group (__syncwarp, or a named barrier for a pair of warps).
 #include "mf_filter.cuh"
 
 namespace mf {
@@ -52,9 +53,20 @@ __device__ __forceinline__ void bulk_row_copy(void *dst, const void *src, uint32
 // later async-proxy ones (the bulk copy refilling the region)
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr int kL = 1024;                      // row length N1
-constexpr int kWarps = 8;                     // warps (rows in flight) per CTA
-using RowShape = FftShape<kL>;
+constexpr int kWarps = 8;                     // warps per CTA
+
+// barrier of the G warps that own one row
+template <int G>
+struct GroupSync {
+    static __device__ __forceinline__ void sync() {
+        if constexpr (G == 1) {
+            __syncwarp();
+        } else {
+            const unsigned id = 1u + (threadIdx.x >> 5) / G;   // named barriers 1.. (0 is __syncthreads)
+            asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(32 * G) : "memory");
+        }
+    }
+};
 
 struct RowsParams {
     const float2 *exch;
@@ -72,7 +84,8 @@ struct RowsParams {
 };
 
 // epilogue of one row: per-butterfly argmax (lowest j on ties), triggers
-struct WarpRhoSink {
+template <int L, int G>
+struct GroupRhoSink {
     const RowsParams &p;
     const UnitInfo &u;
     const int j2;
@@ -81,17 +94,17 @@ struct WarpRhoSink {
     float2 bz = make_float2(0.f, 0.f);
     float2 *region;
     uint64_t *bar;
-    const float2 *next_src;     // next row of this warp, or NULL
-    __device__ WarpRhoSink(const RowsParams &pp, const UnitInfo &uu, int jj, float2 *rg, uint64_t *br,
-                           const float2 *nx)
+    const float2 *next_src;     // next row of this group, or NULL
+    __device__ GroupRhoSink(const RowsParams &pp, const UnitInfo &uu, int jj, float2 *rg, uint64_t *br,
+                            const float2 *nx)
         : p(pp), u(uu), j2(jj), region(rg), bar(br), next_src(nx) {}
-    // the last stage has read this warp's region: refill it with the next row
+    // the last stage has read the group's region: refill it with the next row
     __device__ __forceinline__ void after_loads() {
-        __syncwarp();
+        GroupSync<G>::sync();
         fence_proxy_async();
-        if (next_src != nullptr && (threadIdx.x & 31) == 0) {
-            mbar_expect_tx(bar, kL * sizeof(float2));
-            bulk_row_copy(region, next_src, kL * sizeof(float2), bar);
+        if (next_src != nullptr && (threadIdx.x & (32 * G - 1)) == 0) {
+            mbar_expect_tx(bar, L * sizeof(float2));
+            bulk_row_copy(region, next_src, L * sizeof(float2), bar);
         }
     }
     template <int R>
@@ -160,71 +173,104 @@ struct WarpRhoSink {
     }
 };
 
+template <int L>
 __device__ __forceinline__ const float2 *row_src(const RowsParams &p, int64_t r) {
     const int64_t n2 = (int64_t)1 << p.log2N2;
     const int64_t slot = r >> p.log2N2, j2 = r & (n2 - 1);
-    return p.exch + (slot << p.log2N) + j2 * kL;
+    return p.exch + (slot << p.log2N) + j2 * L;
 }
 
 }  // namespace
 
+template <int L>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
+    using S = FftShape<L>;
+    constexpr int G = L / 1024;               // warps per row
+    constexpr int NG = kWarps / G;            // rows in flight per CTA
+    constexpr int T = L / 32;                 // threads per row (= 32 G)
+    static_assert(G >= 1 && kWarps % G == 0 && T == 32 * G, "1024- or 2048-point rows");
     extern __shared__ __align__(16) float2 rows_smem[];
-    float2 *tw = rows_smem + kWarps * RowShape::STRIDE;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tw + TwTable<kL>::SIZE);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *region = rows_smem + warp * RowShape::STRIDE;
-    fill_twiddles<kL>(tw);
-    if (lane == 0) mbar_init(&bars[warp], 1);
+    __shared__ int gfail[NG];                 // a warp of the group gave up waiting
+    float2 *tw = rows_smem + NG * S::STRIDE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tw + TwTable<L>::SIZE);
+    const int grp = (threadIdx.x >> 5) / G, t = threadIdx.x & (T - 1), lane = threadIdx.x & 31;
+    const int wig = (threadIdx.x >> 5) % G;   // warp within the group
+    float2 *region = rows_smem + grp * S::STRIDE;
+    fill_twiddles<L>(tw);
+    if (t == 0) {
+        mbar_init(&bars[grp], 1);
+        gfail[grp] = 0;
+    }
     mbar_fence_init();
     __syncthreads();
     const int64_t total = (int64_t)p.n_units << p.log2N2;
-    const int64_t step = (int64_t)gridDim.x * kWarps;
-    int64_t r = (int64_t)blockIdx.x * kWarps + warp;
-    if (r < total && lane == 0) {
-        mbar_expect_tx(&bars[warp], kL * sizeof(float2));
-        bulk_row_copy(region, row_src(p, r), kL * sizeof(float2), &bars[warp]);
+    const int64_t step = (int64_t)gridDim.x * NG;
+    int64_t r = (int64_t)blockIdx.x * NG + grp;
+    if (r < total && t == 0) {
+        mbar_expect_tx(&bars[grp], L * sizeof(float2));
+        bulk_row_copy(region, row_src<L>(p, r), L * sizeof(float2), &bars[grp]);
     }
     uint32_t parity = 0;
     for (; r < total; r += step) {
-        // 1. the row has landed (bounded wait)
+        // 1. the row has landed (bounded wait; every warp of the group waits on the same barrier)
         long long it = 0;
         bool ok = true;
-        while (!mbar_try_wait(&bars[warp], parity)) {
+        while (!mbar_try_wait(&bars[grp], parity)) {
             if (++it > p.spin_limit) { ok = false; break; }
         }
-        if (!__all_sync(0xffffffffu, ok)) {
+        ok = __all_sync(0xffffffffu, ok);
+        if constexpr (G > 1) {   // the group leaves together: no warp may wait at a group barrier alone
+            if (!ok && lane == 0) atomicOr(&gfail[grp], 1);
+            GroupSync<G>::sync();
+            ok = *(volatile int *)&gfail[grp] == 0;
+        }
+        if (!ok) {
             if (lane == 0) atomicOr(p.status, 2);
-            return;   // the copy into this warp's region never completed; nothing else is in flight
+            return;   // the copy into this group's region never completed; nothing else is in flight
         }
         parity ^= 1u;
         const int slot = (int)(r >> p.log2N2);
         const int j2 = (int)(r & (((int64_t)1 << p.log2N2) - 1));
         const int unit = p.unit0 + slot;
         const UnitInfo u = p.units[unit];
-        // 2. stage 0 from the staged row (element t + 32 q of the row at t + 32 q)
+        // 2. stage 0 from the staged row (element t + T q of the row at t + T q)
         float2 v[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = region[lane + 32 * q];
+        for (int q = 0; q < 32; ++q) v[q] = region[t + T * q];
         Dft<32, +1>::run(v);
-        __syncwarp();
+        GroupSync<G>::sync();
 #pragma unroll
-        for (int q = 0; q < 32; ++q) region[spad(32 * lane + q)] = v[q];
-        __syncwarp();
-        // 3./4. last stage, next-row copy, epilogue
+        for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
+        GroupSync<G>::sync();
+        // 3./4. the remaining stages, next-row copy, epilogue
         const int64_t rn = r + step;
-        WarpRhoSink snk(p, u, j2, region, &bars[warp], rn < total ? row_src(p, rn) : nullptr);
-        stockham_stage<kL, RowShape::R1, 32, +1, true>(region, tw, 0, lane, snk);
-        snk.finish(&p.partials[((int64_t)unit << p.log2N2) + j2]);
+        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp], rn < total ? row_src<L>(p, rn) : nullptr);
+        if constexpr (S::NST == 2) {
+            stockham_stage<L, S::R1, 32, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
+        } else {
+            stockham_stage<L, S::R1, 32, +1, false, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
+            stockham_stage<L, S::R2, 32 * S::R1, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(
+                region, tw + TwTable<L>::S1, 0, t, snk);
+        }
+        snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + wig]);
     }
 }
 
-size_t pass2_rows_smem() {
-    return (size_t)kWarps * RowShape::STRIDE * sizeof(float2) + (size_t)TwTable<kL>::SIZE * sizeof(float2) +
-           kWarps * sizeof(uint64_t);
+template <int L>
+static size_t rows_smem() {
+    return (size_t)(kWarps / (L / 1024)) * FftShape<L>::STRIDE * sizeof(float2) +
+           (size_t)TwTable<L>::SIZE * sizeof(float2) + kWarps * sizeof(uint64_t);
 }
 
-bool pass2_rows_applies(int log2N) { return log2N - log2_n2(log2N) == 10; }
+bool pass2_rows_applies(int log2N) {
+    const int lg1 = log2N - log2_n2(log2N);
+    return lg1 == 10 || lg1 == 11;
+}
+
+int pass2_rows_partials(int log2N) {   // partials per unit: one per row and warp
+    const int lg1 = log2N - log2_n2(log2N);
+    return (1 << log2_n2(log2N)) * (lg1 == 11 ? 2 : 1);
+}
 
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
@@ -248,9 +294,13 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
     p.status = status;
     p.spin_limit = spin_limit;
     const int64_t rows = (int64_t)n_units << seg.log2N2;
-    int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps - 1) / kWarps);
-    if (grid < 1) grid = 1;
-    k_pass2_rows<<<(unsigned)grid, kWarps * 32, pass2_rows_smem(), st>>>(p);
+    if (seg.log2N1 == 10) {
+        int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps - 1) / kWarps);
+        k_pass2_rows<1024><<<(unsigned)std::max<int64_t>(grid, 1), kWarps * 32, rows_smem<1024>(), st>>>(p);
+    } else {
+        int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 2 - 1) / (kWarps / 2));
+        k_pass2_rows<2048><<<(unsigned)std::max<int64_t>(grid, 1), kWarps * 32, rows_smem<2048>(), st>>>(p);
+    }
     return cudaGetLastError();
 }
 
@@ -259,7 +309,11 @@ cudaError_t rows_kernel_attributes() {
         cudaError_t e0 = init_twiddle_tables();
         if (e0 != cudaSuccess) return e0;
     }
-    return cudaFuncSetAttribute(k_pass2_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass2_rows_smem());
+    cudaError_t e = cudaFuncSetAttribute(k_pass2_rows<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rows_smem<1024>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pass2_rows<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rows_smem<2048>());
 }
 
 }  // namespace mf

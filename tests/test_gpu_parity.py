@@ -318,10 +318,11 @@ def test_persistent_and_batch_schedulers_agree(mf, monkeypatch):
     assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
 
 
-@pytest.mark.parametrize("lg", [19, 20])
+@pytest.mark.parametrize("lg", [19, 20, 21, 22])
 def test_pass2_rows_and_tiles_agree(mf, monkeypatch, lg):
-    """Pass 2 with whole rows per warp (bulk-copy prefetch, row length 1024)
-    and the per-tile pass 2 give bit-identical peaks and triggers."""
+    """Pass 2 with whole rows per warp group (bulk-copy prefetch; rows of 1024
+    points on one warp, 2048 on a pair) and the per-tile pass 2 give
+    bit-identical peaks and triggers."""
     import torch
     wl = workloads.small(seed=40 + lg, N=1 << lg, fs=4096.0, n_templates=11, m_lo=1.1, m_hi=9.0)
     spec = wl.segments[0]
