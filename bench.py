@@ -39,7 +39,7 @@ UNIT = "templates/s"
 WORKLOAD = "1024 templates (32x32 lattice, m1,m2 in [1,3] Msun), 1 segment N=2^20 at 4096 Hz, 8 injections, thr 6"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu", "mf_rows.cu", "mf_internal.h"]
+KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu", "mf_rows.cu", "mf_pass1.cu", "mf_internal.h"]
 
 
 def _args():

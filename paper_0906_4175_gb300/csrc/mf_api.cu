@@ -78,6 +78,7 @@ static int ensure_device_init() {
     MF_CUDA(refine_kernel_attributes());
     MF_CUDA(chisq_kernel_attributes());
     MF_CUDA(rows_kernel_attributes());
+    MF_CUDA(pass1_pf_kernel_attributes());
     done.push_back(dev);
     return MF_OK;
 }

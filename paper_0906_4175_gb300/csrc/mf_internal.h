@@ -128,6 +128,13 @@ cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, in
                          mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
                          cudaStream_t st);
 int pass2_blocks(int log2N);
+// pass 1 as a persistent kernel with cp.async staging of the next tile (mf_pass1.cu);
+// launch_pass1 takes it where it applies
+bool pass1_pf_applies(int log2N, int log2D, int phase_mode);
+cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
+                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
+                            cudaStream_t st);
+cudaError_t pass1_pf_kernel_attributes();
 // pass 2 with whole rows per warp and bulk-copy prefetch (row length 1024 only)
 bool pass2_rows_applies(int log2N);
 int pass2_rows_partials(int log2N);
