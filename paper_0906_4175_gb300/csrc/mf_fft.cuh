@@ -336,6 +336,38 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int
     if constexpr (!LAST) Sync::sync();
 }
 
+// Last Stockham stage of a 1024-point sequence (radix 32 over Ns = 32) with
+// the twiddles exp(SIGN 2 pi i r t / 1024) of rows r > 16 formed as
+// w[r - 16] w[16]: only rows r <= 16 of the table are read, so a kernel short
+// of shared memory can keep just those 17 rows.  Thread t reads elements
+// t + 32 r and hands the 32-point DFT to the sink (outputs t + 32 r).
+template <int SIGN, class Snk>
+__device__ __forceinline__ void last_stage_1024_split(const float2 *sq, const float2 *tw, int seq, int t, Snk &snk) {
+    float2 v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = sq[spad(t + 32 * r)];
+    float2 w16 = tw[16 * 32 + t];
+    if (SIGN < 0) w16.y = -w16.y;
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+        float2 w = tw[r * 32 + t];
+        if (SIGN < 0) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+        v[r + 16] = cmul(v[r + 16], cmul(w, w16));
+    }
+    v[16] = cmul(v[16], w16);
+    Dft<32, SIGN>::run(v);
+    snk.template store<32>(seq, t, 32, v);
+}
+
+// Sources that define kSplitTw = true have their 1024-point transforms end
+// with last_stage_1024_split, so that every kernel generating templates
+// (whatever its shared-memory budget) rounds the same way.
+template <class T, class = void>
+struct uses_split_tw { static constexpr bool value = false; };
+template <class T>
+struct uses_split_tw<T, decltype((void)T::kSplitTw, void())> { static constexpr bool value = T::kSplitTw; };
+
 // Full CTA FFT.  tw: the TwTable<L> twiddles in shared memory, filled and
 // made visible before the call (or filled before it with no intervening
 // shared-memory write, the first stage barrier publishes them).
@@ -369,7 +401,8 @@ __device__ __forceinline__ void cta_fft(float2 *smem, const float2 *tw, Src &src
     }
     __syncthreads();
     if constexpr (S::NST == 2) {
-        stockham_stage<L, S::R1, 32, SIGN, true>(sq, tw, seq, t, snk);
+        if constexpr (L == 1024 && uses_split_tw<Src>::value) last_stage_1024_split<SIGN>(sq, tw, seq, t, snk);
+        else stockham_stage<L, S::R1, 32, SIGN, true>(sq, tw, seq, t, snk);
     } else if constexpr (S::NST == 3) {
         stockham_stage<L, S::R1, 32, SIGN, false>(sq, tw, seq, t, snk);
         stockham_stage<L, S::R2, 32 * S::R1, SIGN, true>(sq, tw + TwTable<L>::S1, seq, t, snk);

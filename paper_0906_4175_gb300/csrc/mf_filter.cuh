@@ -47,6 +47,7 @@ __device__ __forceinline__ void anchor_record(double c1, double c2, double c3, d
 template <int L, int C, int LG1>
 struct TemplateSrc {
     static constexpr bool kHalfZero = true;
+    static constexpr bool kSplitTw = true;   // same rounding as the persistent pass 1
     // one anchor record (float4 + float) per non-zero column row, staged per tile
     static constexpr size_t kScratchBytes = (size_t)(L / 2) * (sizeof(float4) + sizeof(float));
     struct Params {
@@ -140,6 +141,7 @@ struct TemplateSrc {
 template <int L, int C, int LG1>
 struct TemplateSrcF32 {
     static constexpr bool kHalfZero = true;
+    static constexpr bool kSplitTw = true;
     struct Params {
         const float2 *W;
         const UnitInfo *units;

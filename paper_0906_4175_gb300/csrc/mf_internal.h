@@ -42,6 +42,7 @@ struct UnitInfo {
     float z_scale;        // z = raw * z_scale (Eq. 1 with A = Mc^(5/6))
     int32_t tmpl;         // template index
 };
+static_assert(sizeof(UnitInfo) == 32, "the persistent pass 1 reads the band fields as one int4");
 
 // Stable trigger keys: (tmpl, seg, j) packed into 64 bits.
 struct KeyLayout {

@@ -18,7 +18,9 @@
 //   W staging     L/2 rows x C columns complex64 (32 KB; the upper half of
 //                 every column is outside the one-sided spectrum)
 //   anchors       L/2 float4 + L/2 float          (one record per row: D >= C)
-// The Stockham twiddle table is read from the device copy through L1.
+//   twiddles     the second stage's table w[r * 32 + k] = exp(2 pi i r k / L)
+//                 for L <= 512; for L = 1024 (no room for all 32 rows) rows
+//                 r <= 16 only, and w[r] = w[r - 16] w[16] for r > 16
 //
 // Applies to the FP64-anchor phase when the anchor spacing D is at least the
 // tile width C and at most N1, for N = 2^16 .. 2^21 (L = 256 .. 1024); every
@@ -54,39 +56,49 @@ struct Pass1PfParams {
 template <int L, int C>
 __host__ __device__ constexpr size_t pf_wbuf_elems() { return (size_t)(L / 2) * C; }
 
+// twiddle entries kept in shared memory (see the layout above)
+template <int L>
+__host__ __device__ constexpr int pf_tw_elems() { return L == 1024 ? 17 * 32 : TwTable<L>::S1; }
+
 template <int L, int C>
 __host__ __device__ constexpr size_t pf_smem_bytes() {
     return pass_data_bytes<L, C>() + pf_wbuf_elems<L, C>() * sizeof(float2) +
-           (size_t)(L / 2) * (sizeof(float4) + sizeof(float));
+           (size_t)(L / 2) * (sizeof(float4) + sizeof(float)) + (size_t)pf_tw_elems<L>() * sizeof(float2);
 }
 
 // Issue the copies of one item's inputs: W rows n < L/2 (C consecutive
 // columns each, 16-byte chunks, skipped when both columns of a chunk are
 // outside the template's band) and the anchor record of every row that has an
 // anchor.  Every thread commits one group.
+// The band fields of a unit (k_lo, k_hi, g_lo, n_anc: the first 16 bytes of
+// its 32-byte-aligned UnitInfo), loaded a full item ahead of their use.
+__device__ __forceinline__ int4 pf_band(const Pass1PfParams &p, int slot) {
+    return __ldg(reinterpret_cast<const int4 *>(p.units + p.unit0 + slot));
+}
+
 template <int L, int C, int LG1>
-__device__ __forceinline__ void pf_issue(const Pass1PfParams &p, int item, float2 *wbuf, float4 *abuf,
+__device__ __forceinline__ void pf_issue(const Pass1PfParams &p, int item, int4 band, float2 *wbuf, float4 *abuf,
                                          float *abuf4) {
     constexpr int NT = C * (L / 32);
     constexpr int TILES = (1 << LG1) / C;
     constexpr int CH = C / 2;   // 16-byte chunks per row
     const int slot = item / TILES, tile = item - slot * TILES;
-    const UnitInfo u = p.units[p.unit0 + slot];
+    const int k_lo = band.x, k_hi = band.y, g_lo = band.z, n_anc = band.w;
     const int kc = tile * C;
 #pragma unroll
     for (int i = 0; i < (L / 2) * CH / NT; ++i) {
         const int c = threadIdx.x + i * NT;
         const int n = c / CH, j = c - n * CH;
         const int k = kc + 2 * j + (n << LG1);
-        if (k + 1 >= u.k_lo && k < u.k_hi) cp_async16(wbuf + n * C + 2 * j, p.W + k);
+        if (k + 1 >= k_lo && k < k_hi) cp_async16(wbuf + n * C + 2 * j, p.W + k);
     }
     const float4 *anc0 = p.anchors + (int64_t)slot * p.anc_stride;
     const float *anc40 = p.anchors4 + (int64_t)slot * p.anc_stride;
     const int gstep = 1 << (LG1 - p.log2D);
-    const int gbase = (kc >> p.log2D) - u.g_lo;
+    const int gbase = (kc >> p.log2D) - g_lo;
     for (int n = threadIdx.x; n < L / 2; n += NT) {
         const int a = gbase + n * gstep;
-        if (a >= 0 && a < u.n_anc) {
+        if (a >= 0 && a < n_anc) {
             cp_async16(abuf + n, anc0 + a);
             cp_async4(abuf4 + n, anc40 + a);
         }
@@ -105,17 +117,27 @@ __global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams
     float2 *wbuf = smem + pass_data_bytes<L, C>() / sizeof(float2);
     float4 *abuf = (float4 *)(wbuf + pf_wbuf_elems<L, C>());
     float *abuf4 = (float *)(abuf + L / 2);
+    float2 *tw = (float2 *)(abuf4 + L / 2);
     const int seq = threadIdx.x % C, t = threadIdx.x / C;
     float2 *sq = smem + seq * S::STRIDE;
-    const float2 *tw = g_tw_tables + tw_offset<L>();
+    {   // published by the first item's barrier
+        const float2 *src = g_tw_tables + tw_offset<L>();
+        for (int m = threadIdx.x; m < pf_tw_elems<L>(); m += NT) tw[m] = __ldg(&src[m]);
+    }
     const int D = 1 << p.log2D;
     const typename ExchSink<L, C, +1, LG1>::Params kp{p.E, LG1, p.log2N};
 
     int item = blockIdx.x;
-    if (item < p.n_items) pf_issue<L, C, LG1>(p, item, wbuf, abuf, abuf4);
+    int4 band = make_int4(0, 0, 0, 0);
+    if (item < p.n_items) {
+        band = pf_band(p, item / TILES);
+        pf_issue<L, C, LG1>(p, item, band, wbuf, abuf, abuf4);
+    }
     for (; item < p.n_items; item += gridDim.x) {
         const int slot = item / TILES, tile = item - slot * TILES;
-        const UnitInfo u = p.units[p.unit0 + slot];
+        const int next = item + (int)gridDim.x;
+        const int4 nband = next < p.n_items ? pf_band(p, next / TILES) : make_int4(0, 0, 0, 0);
+        const int k_lo = band.x, k_hi = band.y;
         cp_async_wait_all();
         __syncthreads();   // staged inputs visible; the previous item's last stage has read the column data
         float2 v[32];
@@ -129,7 +151,7 @@ __global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams
                 const int n = t + r * T;
                 const int k = k0 + ((r * T) << LG1);
                 float2 x = czero();
-                if (k >= u.k_lo && k < u.k_hi) {
+                if (k >= k_lo && k < k_hi) {
                     const float2 w = wbuf[n * C + seq];
                     const float4 a = abuf[n];
                     const float a4 = abuf4[n];
@@ -146,9 +168,11 @@ __global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams
 #pragma unroll
         for (int r = 0; r < 32; ++r) sq[spad(32 * t + r)] = v[r];
         __syncthreads();   // column data complete; every thread has consumed the staged inputs
-        if (item + (int)gridDim.x < p.n_items) pf_issue<L, C, LG1>(p, item + gridDim.x, wbuf, abuf, abuf4);
+        if (next < p.n_items) pf_issue<L, C, LG1>(p, next, nband, wbuf, abuf, abuf4);
         ExchSink<L, C, +1, LG1> snk(kp, tile, p.unit0 + slot, slot);
-        stockham_stage<L, S::R1, 32, +1, true>(sq, tw, seq, t, snk);
+        if constexpr (L == 1024) last_stage_1024_split<+1>(sq, tw, seq, t, snk);
+        else stockham_stage<L, S::R1, 32, +1, true>(sq, tw, seq, t, snk);
+        band = nband;
     }
 }
 
