@@ -325,12 +325,25 @@ __device__ __forceinline__ void stockham_stage(float2 *sq, const float2 *tw, int
             }
         }
         Dft<R, SIGN>::run(v + i * R);
-        if constexpr (LAST) {
-            snk.template store<R>(seq, b, Ns, v + i * R);    // outputs b + r * Ns
-        } else {
+        if constexpr (!LAST) {
             const int idxD = (b / Ns) * Ns * R + k;
 #pragma unroll
             for (int r = 0; r < R; ++r) sq[spad(idxD + r * Ns)] = v[i * R + r];
+        }
+    }
+    if constexpr (LAST) {
+        // In the last stage Ns R = L, so output r of butterfly i is element
+        // t + i T + r L/R = t + T (i + r NB): all 32 outputs of the thread go to
+        // the sink in one call (outputs t + q T), whatever the radix.
+        if constexpr (NB == 1) {
+            snk.template store<32>(seq, t, T, v);
+        } else {
+            float2 o[32];
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[i + r * NB] = v[i * R + r];
+            snk.template store<32>(seq, t, T, o);
         }
     }
     if constexpr (!LAST) Sync::sync();
@@ -373,7 +386,8 @@ struct uses_split_tw<T, decltype((void)T::kSplitTw, void())> { static constexpr 
 // shared-memory write, the first stage barrier publishes them).
 // Src::load(seq, t, v) fills v[r] = x[t + r*T], r < 32
 // (Src::kHalfZero: v[16..31] are zero and are not read).
-// Snk::store<R>(seq, b, stride, v) receives outputs b + r*stride, r < R.
+// Snk::store<R>(seq, b, stride, v) receives outputs b + r*stride, r < R
+// (the Stockham stages call it once per thread with R = 32, b = t, stride = T).
 // The last stage does not synchronise: a sink that reuses shared memory
 // afterwards must __syncthreads() first.
 // smem: C * FftShape<L>::STRIDE float2.  Must be called by all C*T threads.
