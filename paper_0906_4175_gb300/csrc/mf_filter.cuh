@@ -181,6 +181,21 @@ struct TemplateSrcF32 {
 // rho_j = |raw_j| rho_scale.  Tracks the argmax (lowest j on ties) and
 // appends every j with |raw_j|^2 > thr2.
 // ---------------------------------------------------------------------------
+// max(0, a[0], ..., a[R-1]) (NaNs ignored, as by fmaxf) by pairwise halving:
+// a dependency chain of log2 R instead of R.
+template <int R>
+__device__ __forceinline__ float tree_max0(const float *a) {
+    if constexpr (R == 1) {
+        return fmaxf(0.f, a[0]);
+    } else {
+        float h[(R + 1) / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) h[i] = fmaxf(a[i], a[i + R / 2]);
+        if constexpr (R % 2) h[R / 2] = a[R - 1];
+        return tree_max0<(R + 1) / 2>(h);
+    }
+}
+
 template <int L, int C>
 struct RhoSink {
     struct Params {
@@ -207,12 +222,9 @@ struct RhoSink {
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) {
         const int j2 = tile * C + seq;
         float pw[R];
-        float m = 0.f;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
-            m = fmaxf(m, pw[r]);
-        }
+        for (int r = 0; r < R; ++r) pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+        const float m = tree_max0<R>(pw);
         // The butterfly's outputs j2 + N2 (b + r stride) increase with r, so its
         // argmax with the lowest-j tie rule is the first r with pw[r] == m.
         if (m >= bp) {

@@ -110,12 +110,9 @@ struct GroupRhoSink {
     template <int R>
     __device__ __forceinline__ void store(int, int b, int stride, const float2 *v) {
         float pw[R];
-        float m = 0.f;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
-            m = fmaxf(m, pw[r]);
-        }
+        for (int r = 0; r < R; ++r) pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+        const float m = tree_max0<R>(pw);
         if (m >= bp) {
             int rs = R - 1;
 #pragma unroll
