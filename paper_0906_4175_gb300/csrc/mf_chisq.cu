@@ -74,7 +74,7 @@ __global__ void k_chisq_units(SegDev seg, const UnitInfo *__restrict__ all, int 
 template <int L, int C>
 __device__ __forceinline__ float *chi_tile_row(int seq) {
     extern __shared__ float2 chi_smem[];
-    return reinterpret_cast<float *>(chi_smem + seq * FftShape<L>::STRIDE);
+    return reinterpret_cast<float *>(chi_smem + seq * SeqStride<L, C>::value);
 }
 
 template <int L, int C>

@@ -215,6 +215,19 @@ struct FftShape {
 
 __device__ __forceinline__ int spad(int m) { return m + (m >> 5); }
 
+// Stride (float2 units) between the C sequences of a CTA: the padded length
+// rounded up to 16/C (mod 16), or to 1 (mod 16) for C >= 16.  A half-warp of
+// a column pass holds C sequences x 16/C positions (sequence fastest), so its
+// 8-byte accesses land on 16 different bank pairs; the same holds for the
+// sinks' tile flushes (sequence fastest).  For C = 8 this is the 2 (mod 16)
+// of FftShape::STRIDE.
+template <int L, int C>
+struct SeqStride {
+    static constexpr int PADDED = FftShape<L>::PADDED;
+    static constexpr int RES = C >= 16 ? 1 : 16 / C;
+    static constexpr int value = PADDED + ((RES - PADDED % 16) + 16) % 16;
+};
+
 // Twiddle tables of the Stockham stages after stage 0, in shared memory:
 // for a stage (Ns, R) the entries w[r * Ns + k] = exp(+2 pi i r k / (Ns R)),
 // r < R, k < Ns (k fastest, so a warp reading one r hits consecutive words).
@@ -390,7 +403,7 @@ struct uses_split_tw<T, decltype((void)T::kSplitTw, void())> { static constexpr 
 // (the Stockham stages call it once per thread with R = 32, b = t, stride = T).
 // The last stage does not synchronise: a sink that reuses shared memory
 // afterwards must __syncthreads() first.
-// smem: C * FftShape<L>::STRIDE float2.  Must be called by all C*T threads.
+// smem: C * SeqStride<L, C>::value float2.  Must be called by all C*T threads.
 template <int L, int C, bool SEQ_FAST, int SIGN, class Src, class Snk>
 __device__ __forceinline__ void cta_fft(float2 *smem, const float2 *tw, Src &src, Snk &snk) {
     using S = FftShape<L>;
@@ -398,7 +411,7 @@ __device__ __forceinline__ void cta_fft(float2 *smem, const float2 *tw, Src &src
     const int tid = threadIdx.x;
     const int seq = SEQ_FAST ? (tid % C) : (tid / T);
     const int t = SEQ_FAST ? (tid / C) : (tid % T);
-    float2 *sq = smem + seq * S::STRIDE;
+    float2 *sq = smem + seq * SeqStride<L, C>::value;
 
     {
         float2 v[32];

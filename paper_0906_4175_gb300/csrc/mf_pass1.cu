@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams
     float *abuf4 = (float *)(abuf + L / 2);
     float2 *tw = (float2 *)(abuf4 + L / 2);
     const int seq = threadIdx.x % C, t = threadIdx.x / C;
-    float2 *sq = smem + seq * S::STRIDE;
+    float2 *sq = smem + seq * SeqStride<L, C>::value;
     {   // published by the first item's barrier
         const float2 *src = g_tw_tables + tw_offset<L>();
         for (int m = threadIdx.x; m < pf_tw_elems<L>(); m += NT) tw[m] = __ldg(&src[m]);

@@ -17,7 +17,7 @@ __host__ __device__ constexpr int seqs_per_cta(int other) {
 
 template <int L, int C>
 __host__ __device__ constexpr size_t pass_data_bytes() {
-    return (size_t)C * FftShape<L>::STRIDE * sizeof(float2);
+    return (size_t)C * SeqStride<L, C>::value * sizeof(float2);
 }
 // data area, then the twiddle table, then the source's scratch
 template <int L, int C, class Src>
@@ -213,7 +213,7 @@ struct RowTileOut {
     __device__ RowTileOut(const Params &pp, int tl, int, int sl) : p(pp), tile(tl), slot(sl) {}
     __device__ __forceinline__ float2 *row(int seq) const {
         extern __shared__ float2 rto_smem[];
-        return rto_smem + seq * FftShape<L>::STRIDE;
+        return rto_smem + seq * SeqStride<L, C>::value;
     }
     template <int R>
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
