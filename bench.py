@@ -358,10 +358,12 @@ def run_uneven(args, mf, torch, dev):
 
 
 def run_precision(args, mf, torch, dev):
-    """The phase forms on the 1024-template, N = 2^20 workload: speed of each
-    (one CUDA-graph replay per step) and, in the CPU-baseline leg, its rho
-    error against the FP64 oracle on a seeded sample of templates (full
-    series, oracle-synthesised input)."""
+    """The phase forms and the FFT forms (FP32 butterflies, or the first
+    radix-32 stage of pass 2's rows as split FP16 / BF16 tensor-core products)
+    on the 1024-template, N = 2^20 workload: speed of each (one CUDA-graph
+    replay per step) and, in the CPU-baseline leg, its rho error against the
+    FP64 oracle on a seeded sample of templates (full series,
+    oracle-synthesised input)."""
     import numpy as np
     import workloads
     wl = workloads.scale(0)
@@ -371,10 +373,13 @@ def run_precision(args, mf, torch, dev):
     stream = torch.cuda.current_stream()
     forms = {}
     cap = 1 << 22
-    modes = (("fp64_anchors_fp32_taylor", mf.MF_PHASE_ANCHOR), ("fp64_per_bin", mf.MF_PHASE_FP64),
-             ("fp32_only", mf.MF_PHASE_FP32))
-    for name, mode in modes:
-        bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low, phase_mode=mode)
+    modes = (("fp64_anchors_fp32_taylor", mf.MF_PHASE_ANCHOR, mf.MF_FFT_FP32),
+             ("fp64_per_bin", mf.MF_PHASE_FP64, mf.MF_FFT_FP32),
+             ("fp32_only", mf.MF_PHASE_FP32, mf.MF_FFT_FP32),
+             ("tc_fp16_split_stage", mf.MF_PHASE_ANCHOR, mf.MF_FFT_TC_FP16),
+             ("tc_bf16_split_stage", mf.MF_PHASE_ANCHOR, mf.MF_FFT_TC_BF16))
+    for name, mode, fmode in modes:
+        bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low, phase_mode=mode, fft_mode=fmode)
         out = (torch.empty((wl.n_templates, 4), dtype=torch.float32, device=dev),
                torch.empty((cap, 6), dtype=torch.float32, device=dev),
                torch.zeros(1, dtype=torch.int64, device=dev))
@@ -392,13 +397,16 @@ def run_precision(args, mf, torch, dev):
         acc = _precision_cpu_baseline(mf, torch, dev, wl, modes)
         for name in forms:
             forms[name].update(acc["forms"][name])
-    line = {"workload": "precision", "metric": "templates/s and max rho rel err vs FP64 per phase form",
+    line = {"workload": "precision", "metric": "templates/s and max rho rel err vs FP64 per phase and FFT form",
             "value": forms["fp64_anchors_fp32_taylor"]["templates_per_s"], "unit": "templates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections)",
             "config": {"workload": WORKLOAD, "error_sample": acc["sample"] if acc else None,
                        "l2": "flushed before every timed step (256 MiB write)",
-                       "fft": "FP32 in every form (no tensor-core DFT stage is built)"},
+                       "phase_forms": "FFT in FP32; phase from FP64 anchors + FP32 Taylor, FP64 per bin, FP32 only",
+                       "fft_forms": "tc_*: FP64-anchor phase; first radix-32 stage of pass 2's 1024-point rows as "
+                                    "tcgen05 products of hi + lo FP16 / BF16 splits (hi*hi + hi*lo + lo*hi), FP32 "
+                                    "accumulate; all other stages FP32"},
             "forms": forms, "cpu_baseline": acc["cpu_baseline"] if acc else None}
     print(json.dumps(line))
     return 0
@@ -425,8 +433,8 @@ def _precision_cpu_baseline(mf, torch, dev, wl, modes):
                                                            spec.fs, wl.f_low)["rho"], sample))
     cpu_s = time.perf_counter() - t0
     forms = {}
-    for name, mode in modes:
-        b2 = mf.Bank(wl.m1[sample], wl.m2[sample], f_low=wl.f_low, phase_mode=mode)
+    for name, mode, fmode in modes:
+        b2 = mf.Bank(wl.m1[sample], wl.m2[sample], f_low=wl.f_low, phase_mode=mode, fft_mode=fmode)
         p, t, n = mf.filter_bank(b2, [seg], 0.0, trig_cap=len(sample) * spec.N)
         tr = mf.triggers_to_numpy(t, n)
         rho = tr["rho"].reshape(len(sample), spec.N).astype(np.float64)

@@ -50,13 +50,20 @@ typedef struct {
     int pn_order;     /* phase order in half-PN steps; only 4 (= 2PN, the paper's choice) */
     int amp_order;    /* amplitude order; only 0 (Newtonian, the paper's choice) */
     int phase_mode;   /* MF_PHASE_* below */
-    int fft_mode;     /* MF_FFT_FP32 (only mode in this build) */
+    int fft_mode;     /* MF_FFT_* below */
 } mf_bank_params;
 
 #define MF_PHASE_ANCHOR 0  /* default: Psi in FP64 at anchor bins, reduced mod 2 pi, FP32 cubic Taylor between them */
 #define MF_PHASE_FP64   1  /* Psi in FP64 at every bin (anchor spacing 1) */
 #define MF_PHASE_FP32   2  /* Psi in FP32 only, no FP64 reduction (precision-sweep reference; loses accuracy) */
-#define MF_FFT_FP32     0
+#define MF_FFT_FP32     0  /* default: every FFT stage in FP32 on the CUDA cores */
+/* Precision-sweep forms (config "FFT in FP32 vs a tensor-core DFT-GEMM radix stage"): the first radix-32
+   stage of the 1024-point rows of pass 2 runs as a tensor-core GEMM (tcgen05.mma, FP32 accumulate in tensor
+   memory) on hi + lo 16-bit splits of its inputs and of the DFT matrix (three products: hi*hi + hi*lo +
+   lo*hi); everything else stays FP32.  Only segments with N = 2^19 or 2^20 (1024-point rows);
+   mf_filter_bank returns MF_ENOTSUP for other N.  chi^2 (mf_chisq_*) always runs in FP32. */
+#define MF_FFT_TC_FP16  1  /* FP16 splits (rows scaled by a power of two into the FP16 range) */
+#define MF_FFT_TC_BF16  2  /* BF16 splits */
 
 /* Per-(template, segment) peak: the argmax over j of rho_j (lowest j on ties). */
 typedef struct {
@@ -101,7 +108,8 @@ const char *mf_version(void);
 
 /* mf_bank_create -- per-template constants for Sec. 1.1's templates.
  * m1, m2: host arrays of n > 0 component masses in solar masses (> 0, finite).
- * params: host; NULL means f_low = 40, 2PN, Newtonian, MF_PHASE_ANCHOR, MF_FFT_FP32.
+ * params: host; NULL means f_low = 40, 2PN, Newtonian, MF_PHASE_ANCHOR, MF_FFT_FP32.  fft_mode outside
+ * MF_FFT_FP32 .. MF_FFT_TC_BF16 returns MF_ENOTSUP.
  * Computes in FP64 on the host the 2PN phase coefficients, f_isco and the
  * amplitude constant of each template and copies them to the device.
  * *out receives the handle (free with mf_bank_destroy).

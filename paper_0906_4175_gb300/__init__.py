@@ -15,12 +15,14 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (EVENT_DTYPE, INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_OK, MF_PHASE_ANCHOR,
+from ._native import (EVENT_DTYPE, INJ_DTYPE, MF_EINVAL, MF_EOVERFLOW, MF_ETIMEOUT, MF_FFT_FP32, MF_FFT_TC_BF16,
+                      MF_FFT_TC_FP16, MF_OK, MF_PHASE_ANCHOR,
                       MF_PHASE_FP32, MF_PHASE_FP64, PEAK_DTYPE, TRIG_DTYPE, BankParams, MFError, check)
 
 __all__ = ["Bank", "Segment", "filter_bank", "chisq_series", "chisq_points", "cluster_triggers",
            "events_to_numpy", "EVENT_DTYPE", "fft", "autotune", "synth_segment", "refine", "RefineFn", "MFError",
            "PEAK_DTYPE", "TRIG_DTYPE", "INJ_DTYPE", "MF_PHASE_ANCHOR", "MF_PHASE_FP64", "MF_PHASE_FP32",
+           "MF_FFT_FP32", "MF_FFT_TC_FP16", "MF_FFT_TC_BF16",
            "peaks_to_numpy", "triggers_to_numpy", "version"]
 
 
@@ -47,12 +49,12 @@ def params(f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR, pn_order: int
 class Bank:
     """mf_bank_create: template constants for masses m1, m2 (solar masses)."""
 
-    def __init__(self, m1, m2, f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR):
+    def __init__(self, m1, m2, f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR, fft_mode: int = MF_FFT_FP32):
         m1 = np.ascontiguousarray(m1, dtype=np.float64)
         m2 = np.ascontiguousarray(m2, dtype=np.float64)
         if m1.shape != m2.shape or m1.ndim != 1:
             raise ValueError("m1 and m2 must be 1-D arrays of the same length")
-        self.params = params(f_low, phase_mode)
+        self.params = params(f_low, phase_mode, fft_mode=fft_mode)
         h = ctypes.c_void_p()
         L = _native.lib()
         check(L.mf_bank_create(m1.ctypes.data, m2.ctypes.data, m1.size, ctypes.byref(self.params),

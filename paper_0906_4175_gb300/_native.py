@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libmfgb.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ETIMEOUT, MF_ENOTSUP = range(7)
 MF_PHASE_ANCHOR, MF_PHASE_FP64, MF_PHASE_FP32 = 0, 1, 2
-MF_FFT_FP32 = 0
+MF_FFT_FP32, MF_FFT_TC_FP16, MF_FFT_TC_BF16 = 0, 1, 2
 _NAMES = {0: "MF_OK", 1: "MF_EINVAL", 2: "MF_ENOMEM", 3: "MF_ECUDA", 4: "MF_EOVERFLOW",
           5: "MF_ETIMEOUT", 6: "MF_ENOTSUP"}
 

@@ -231,7 +231,8 @@ static int check_params(const mf_bank_params &p) {
     if (p.pn_order != 4) return set_err(MF_ENOTSUP, "pn_order %d: only 4 (2PN) is implemented", p.pn_order);
     if (p.amp_order != 0) return set_err(MF_ENOTSUP, "amp_order %d: only 0 (Newtonian) is implemented", p.amp_order);
     if (p.phase_mode < 0 || p.phase_mode > 2) return set_err(MF_EINVAL, "phase_mode %d", p.phase_mode);
-    if (p.fft_mode != MF_FFT_FP32) return set_err(MF_ENOTSUP, "fft_mode %d: only MF_FFT_FP32", p.fft_mode);
+    if (p.fft_mode < MF_FFT_FP32 || p.fft_mode > MF_FFT_TC_BF16)
+        return set_err(MF_ENOTSUP, "fft_mode %d: MF_FFT_FP32, MF_FFT_TC_FP16 or MF_FFT_TC_BF16", p.fft_mode);
     return MF_OK;
 }
 
@@ -499,14 +500,14 @@ constexpr double kSplit = 0.60;
 
 // Pass 2 as whole rows per warp (row length 1024) unless MFGB_P2ROWS=0.
 static bool use_rows(const mf_bank_s *b, const mf_segment_s *g) {
-    (void)b;
     if (!pass2_rows_applies(g->log2N)) return false;
+    if (b->params.fft_mode != MF_FFT_FP32) return true;   // the tensor-core stage lives in the rows kernel
     const char *e = getenv("MFGB_P2ROWS");
     return !(e && strcmp(e, "0") == 0);
 }
 
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
-    if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32) return false;
+    if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32 || b->params.fft_mode != MF_FFT_FP32) return false;
     if (const char *e = getenv("MFGB_SCHED")) {
         if (strcmp(e, "batch") == 0) return false;
         if (strcmp(e, "persistent") == 0) return true;
@@ -581,6 +582,8 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const mf_segment_s *g = segs[s];
         if (!g) return set_err(MF_EINVAL, "segs[%d] is NULL", s);
         if (g->device != cur) return set_err(MF_EINVAL, "segs[%d] lives on device %d", s, g->device);
+        if (b->params.fft_mode != MF_FFT_FP32 && g->log2N != 19 && g->log2N != 20)
+            return set_err(MF_ENOTSUP, "segs[%d]: the tensor-core FFT stage needs N = 2^19 or 2^20", s);
         maxN = std::max(maxN, g->N);
         // every template's band must be non-empty: the smallest f_cut decides
         const double fc = std::min(b->fisco_min, 0.5 * g->fs);
@@ -765,7 +768,8 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             pi = prof_begin(b, MF_STAGE_PASS2, exch_bytes, st);
             if (rows)
                 MF_CUDA(launch_pass2_rows(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
-                                          std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, sm_count(), st));
+                                          std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, sm_count(),
+                                          b->params.fft_mode, st));
             else
                 MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                      std::max<int64_t>(trig_cap, 0), st));
@@ -1018,7 +1022,8 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     if (repeats < 1) repeats = 2;
     struct Cand { int sched; int64_t exch; double split; };
     std::vector<Cand> cands;
-    for (double sp : {0.55, 0.60, 0.65}) cands.push_back({0, 0, sp});
+    if (b->params.fft_mode == MF_FFT_FP32)   // the tensor-core stage runs in the per-batch rows kernel only
+        for (double sp : {0.55, 0.60, 0.65}) cands.push_back({0, 0, sp});
     int64_t maxN = 0;
     for (int s = 0; s < n_seg; ++s) maxN = std::max(maxN, segs[s]->N);
     for (int64_t mib : {128, 256, 512, 1024}) cands.push_back({1, mib << 20, 0.60});

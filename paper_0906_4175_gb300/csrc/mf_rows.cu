@@ -17,6 +17,9 @@
 //      partials[unit][j2][warp of the group].
 // The twiddle table is filled once per CTA; the stages of a row synchronise
 // only its group (__syncwarp, or a named barrier for a pair of warps).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "mf_filter.cuh"
 
 namespace mf {
@@ -253,6 +256,261 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form of the 1024-point rows (fft_mode MF_FFT_TC_FP16 /
+// MF_FFT_TC_BF16).  Stage 0 of a row is Y_t[p] = sum_q x[t + 32 q] w^(pq),
+// w = exp(2 pi i / 32), t, p, q < 32: for each row the complex product of the
+// 32 x 32 matrix X[t][q] with the DFT matrix.  The four warps 4g .. 4g + 3 of
+// a CTA form one tile of M = 128 GEMM rows (warp, t), K = 64 (re, im of the
+// 32 inputs), N = 64 (re, im of the 32 outputs), with B the real form of the
+// DFT matrix: B[2q][2p] = B[2q+1][2p+1] = cos, B[2q][2p+1] = -B[2q+1][2p] = sin.
+// A and B are split into 16-bit hi + lo parts and D = A_hi B_hi + A_hi B_lo +
+// A_lo B_hi is accumulated in FP32 in tensor memory (tcgen05.mma kind::f16,
+// 3 x 4 instructions of K = 16 issued by one thread of the tile, completion
+// on an mbarrier); each warp reads its 32 lanes back with tcgen05.ld and goes
+// on with the FP32 second stage and the rho epilogue of the FP32 kernel.
+// FP16 rows are scaled by a power of two (max |x| in [2^14, 2^15)) before the
+// split and unscaled after; BF16 has the FP32 exponent range.
+// Shared-memory operands use the no-swizzle K-major canonical layout: core
+// matrices of 8 rows x 16 bytes, LBO = 128 B between K-adjacent ones, SBO
+// between 8-row groups.  A warp's row region (8448 B) holds, per 8 rows of t,
+// [A_hi 1 KB | A_lo 1 KB | 64 B], so the tile's SBO is 2112 B; B^T is 64 x 64
+// (SBO 1 KB) for hi and lo.
+// ---------------------------------------------------------------------------
+constexpr int kTcRegion = 1056;               // float2 per warp region = 8448 B = 4 x 2112 B
+constexpr uint32_t kTcSboA = 2112, kTcLbo = 128, kTcSboB = 1024, kTcBBytes = 2 * 64 * 64 * 2;
+constexpr int kTcCols = 64;                   // TMEM columns per tile (N = 64 FP32)
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);   // version 1, no swizzle
+}
+
+// 16-bit split of a pair: hi = round(a), lo = round(a - hi) packed as 2 x 16 bits
+template <int TCM>
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    if constexpr (TCM == MF_FFT_TC_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+template <int TCM>
+__device__ __forceinline__ void store16(uint8_t *p, float v) {
+    if constexpr (TCM == MF_FFT_TC_BF16) *reinterpret_cast<__nv_bfloat16 *>(p) = __float2bfloat16_rn(v);
+    else *reinterpret_cast<__half *>(p) = __float2half_rn(v);
+}
+template <int TCM>
+__device__ __forceinline__ float round16(float v) {
+    if constexpr (TCM == MF_FFT_TC_BF16) return __bfloat162float(__float2bfloat16_rn(v));
+    else return __half2float(__float2half_rn(v));
+}
+
+__device__ __forceinline__ void tile_sync(int g) {   // the 4 warps of tile g (named barrier 1 + g)
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+
+template <int TCM>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_tc(RowsParams p) {
+    constexpr int L = 1024;
+    extern __shared__ __align__(16) float2 rows_smem[];
+    __shared__ int gfail[2];
+    __shared__ uint32_t tmem_base;
+    float2 *tw = rows_smem + kWarps * kTcRegion;
+    uint8_t *Bm = reinterpret_cast<uint8_t *>(tw + TwTable<L>::SIZE);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Bm + kTcBBytes);   // kWarps row barriers, 2 tile barriers
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31, g = w >> 2, rl = w & 3;
+    float2 *region = rows_smem + w * kTcRegion;
+    fill_twiddles<L>(tw);
+    // B^T[n][k] of the DFT matrix, hi at Bm, lo at Bm + 8 KB
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int n = e >> 6, k = e & 63, pp = n >> 1, q = k >> 1;
+        double sn, cs;
+        sincospi((double)((pp * q) & 31) / 16.0, &sn, &cs);
+        const float v = (float)((n & 1) == 0 ? ((k & 1) == 0 ? cs : -sn) : ((k & 1) == 0 ? sn : cs));
+        const uint32_t off = (n >> 3) * kTcSboB + (k >> 3) * kTcLbo + (n & 7) * 16 + (k & 7) * 2;
+        store16<TCM>(Bm + off, v);
+        store16<TCM>(Bm + 8192 + off, v - round16<TCM>(v));
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(2 * kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) mbar_init(&bars[w], 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[kWarps], 1);
+        mbar_init(&bars[kWarps + 1], 1);
+        gfail[0] = gfail[1] = 0;
+    }
+    mbar_fence_init();
+    fence_proxy_async();   // B, written by this CTA's threads, is read by the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base + (uint32_t)(kTcCols * g);
+    const int64_t total = (int64_t)p.n_units << p.log2N2;
+    const int64_t step = (int64_t)gridDim.x * kWarps;
+    int64_t r0 = (int64_t)blockIdx.x * kWarps + 4 * g;   // the tile's first row; rows r0 .. r0 + 3 go together
+    if (r0 + rl < total && t == 0) {
+        mbar_expect_tx(&bars[w], L * sizeof(float2));
+        bulk_row_copy(region, row_src<L>(p, r0 + rl), L * sizeof(float2), &bars[w]);
+    }
+    uint32_t parity = 0, tparity = 0;
+    for (; r0 < total; r0 += step) {
+        const int64_t r = r0 + rl;
+        const bool has = r < total;
+        // 1. the row has landed (bounded wait); the tile leaves together on expiry
+        bool ok = true;
+        if (has) {
+            long long it = 0;
+            while (!mbar_try_wait(&bars[w], parity)) {
+                if (++it > p.spin_limit) { ok = false; break; }
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            parity ^= 1u;
+        }
+        if (!ok && t == 0) atomicOr(&gfail[g], 1);
+        tile_sync(g);
+        if (*(volatile int *)&gfail[g] != 0) {
+            if (t == 0 && !ok) atomicOr(p.status, 2);
+            break;
+        }
+        // 2. this warp's 32 GEMM rows: x[t + 32 q], split into hi + lo
+        float2 v[32];
+        float unscale = 1.f;
+        if (has) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = region[t + 32 * q];
+            if constexpr (TCM == MF_FFT_TC_FP16) {
+                float m = 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) m = fmaxf(m, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (m > 0.f && m < 3.0e38f) {
+                    const int e = 14 - ilogbf(m);
+                    const float s = ldexpf(1.f, e);
+                    unscale = ldexpf(1.f, -e);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = make_float2(v[q].x * s, v[q].y * s);
+                }
+            }
+            __syncwarp();   // every lane has read the staged row
+            uint8_t *blk = reinterpret_cast<uint8_t *>(region) + (t >> 3) * kTcSboA + (t & 7) * 16;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {   // inputs q = 4j .. 4j + 3
+                uint4 h, l;
+                split2<TCM>(v[4 * j].x, v[4 * j].y, h.x, l.x);
+                split2<TCM>(v[4 * j + 1].x, v[4 * j + 1].y, h.y, l.y);
+                split2<TCM>(v[4 * j + 2].x, v[4 * j + 2].y, h.z, l.z);
+                split2<TCM>(v[4 * j + 3].x, v[4 * j + 3].y, h.w, l.w);
+                *reinterpret_cast<uint4 *>(blk + j * kTcLbo) = h;
+                *reinterpret_cast<uint4 *>(blk + 1024 + j * kTcLbo) = l;
+            }
+            fence_proxy_async();
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        tile_sync(g);
+        // 3. one thread issues the tile's 12 MMAs
+        if (rl == 0 && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            constexpr uint32_t fmt = TCM == MF_FFT_TC_BF16 ? 1u : 0u;
+            constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+            const uint32_t a0 = smem_addr(rows_smem + 4 * g * kTcRegion), b0 = smem_addr(Bm);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {   // A_hi B_hi, A_hi B_lo, A_lo B_hi
+                const uint32_t ab = a0 + (s == 2 ? 1024u : 0u), bb = b0 + (s == 1 ? 8192u : 0u);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ad = umma_desc(ab + kk * 2 * kTcLbo, kTcLbo, kTcSboA);
+                    const uint64_t bd = umma_desc(bb + kk * 2 * kTcLbo, kTcLbo, kTcSboB);
+                    const uint32_t acc = (s | kk) != 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&bars[kWarps + g]))
+                         : "memory");
+        }
+        // 4. wait for the products (bounded), read this warp's lanes
+        bool mok = true;
+        {
+            long long it = 0;
+            while (!mbar_try_wait(&bars[kWarps + g], tparity)) {
+                if (++it > p.spin_limit) { mok = false; break; }
+            }
+            mok = __all_sync(0xffffffffu, mok);
+            tparity ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!mok) {   // the tile stops at the next row's check
+            if (t == 0) { atomicOr(p.status, 2); atomicOr(&gfail[g], 1); }
+            continue;
+        }
+        {
+            const uint32_t ta = tmem + ((uint32_t)(32 * rl) << 16);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t d[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+                      "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]),
+                      "=r"(d[15])
+                    : "r"(ta + 16 * c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    v[8 * c + i] = make_float2(__uint_as_float(d[2 * i]) * unscale, __uint_as_float(d[2 * i + 1]) * unscale);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (!has) continue;
+        // 5. as the FP32 kernel from the end of stage 0: padded layout, stage 1, epilogue
+        const int slot = (int)(r >> p.log2N2);
+        const int j2 = (int)(r & (((int64_t)1 << p.log2N2) - 1));
+        const int unit = p.unit0 + slot;
+        const UnitInfo u = p.units[unit];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
+        __syncwarp();
+        const int64_t rn = r + step;
+        GroupRhoSink<L, 1> snk(p, u, j2, region, &bars[w], rn < total ? row_src<L>(p, rn) : nullptr);
+        stockham_stage<L, FftShape<L>::R1, 32, +1, true, GroupRhoSink<L, 1>, GroupSync<1>>(region, tw, 0, t, snk);
+        snk.finish(&p.partials[((int64_t)unit << p.log2N2) + j2]);
+    }
+    // every warp is done with tensor memory (a warp that left the loop early
+    // issued no tensor-core work after its last completed wait)
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * kTcCols)
+                     : "memory");
+    }
+}
+
+static size_t rows_smem_tc() {
+    return (size_t)kWarps * kTcRegion * sizeof(float2) + (size_t)TwTable<1024>::SIZE * sizeof(float2) + kTcBBytes +
+           (kWarps + 2) * sizeof(uint64_t);
+}
+
 template <int L>
 static size_t rows_smem() {
     return (size_t)(kWarps / (L / 1024)) * FftShape<L>::STRIDE * sizeof(float2) +
@@ -272,8 +530,9 @@ int pass2_rows_partials(int log2N) {   // partials per unit: one per row and war
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,
-                              cudaStream_t st) {
+                              int fft_mode, cudaStream_t st) {
     if (!pass2_rows_applies(seg.log2N)) return cudaErrorInvalidValue;
+    if (fft_mode != MF_FFT_FP32 && seg.log2N1 != 10) return cudaErrorInvalidValue;
     RowsParams p;
     p.exch = exch;
     p.units = units;
@@ -293,7 +552,13 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
     const int64_t rows = (int64_t)n_units << seg.log2N2;
     if (seg.log2N1 == 10) {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps - 1) / kWarps);
-        k_pass2_rows<1024><<<(unsigned)std::max<int64_t>(grid, 1), kWarps * 32, rows_smem<1024>(), st>>>(p);
+        const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
+        if (fft_mode == MF_FFT_TC_FP16)
+            k_pass2_rows_tc<MF_FFT_TC_FP16><<<gr, kWarps * 32, rows_smem_tc(), st>>>(p);
+        else if (fft_mode == MF_FFT_TC_BF16)
+            k_pass2_rows_tc<MF_FFT_TC_BF16><<<gr, kWarps * 32, rows_smem_tc(), st>>>(p);
+        else
+            k_pass2_rows<1024><<<gr, kWarps * 32, rows_smem<1024>(), st>>>(p);
     } else {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 2 - 1) / (kWarps / 2));
         k_pass2_rows<2048><<<(unsigned)std::max<int64_t>(grid, 1), kWarps * 32, rows_smem<2048>(), st>>>(p);
@@ -308,6 +573,12 @@ cudaError_t rows_kernel_attributes() {
     }
     cudaError_t e = cudaFuncSetAttribute(k_pass2_rows<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rows_smem<1024>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pass2_rows_tc<MF_FFT_TC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rows_smem_tc());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pass2_rows_tc<MF_FFT_TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rows_smem_tc());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_pass2_rows<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)rows_smem<2048>());

@@ -61,6 +61,9 @@ def test_invalid_arguments_without_device(L):
                               g.ctypes.data, None) == EINVAL
     p = _native.BankParams(40.0, 3, 0, 0, 0)
     assert L.mf_bank_create(m.ctypes.data, m.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == _native.MF_ENOTSUP
+    p = _native.BankParams(40.0, 4, 0, 0, 3)   # fft_mode past MF_FFT_TC_BF16
+    assert L.mf_bank_create(m.ctypes.data, m.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == _native.MF_ENOTSUP
+    assert b"fft_mode" in L.mf_last_error()
     assert L.mf_bank_destroy(None) == 0 and L.mf_segment_destroy(None) == 0
 
 
