@@ -55,6 +55,9 @@ def _args():
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
+    ap.add_argument("--fft-mode", default="fp32", choices=["fp32", "tc_fp16", "tc_bf16"],
+                    help="FFT form of the scale workload: FP32 butterflies (the benchmark line) or the tensor-core "
+                         "DFT stage of pass 2 with FP16 / BF16 splits (precision-sweep forms)")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "uneven", "precision", "refine", "chisq", "fft", "events"],
                     help="scale: the benchmark line; the others print their own measurement line "
@@ -854,7 +857,8 @@ def main():
     stream = torch.cuda.current_stream()
     # inputs: seeded coloured noise + injections synthesised on the device by the library
     s_dev = mf.synth_segment(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections)
-    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
+    fft_mode = {"fp32": mf.MF_FFT_FP32, "tc_fp16": mf.MF_FFT_TC_FP16, "tc_bf16": mf.MF_FFT_TC_BF16}[args.fft_mode]
+    bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low, fft_mode=fft_mode)
     cap = 1 << 22
     outb = (torch.empty((wl.n_templates, 4), dtype=torch.float32, device=dev),
             torch.empty((cap, 6), dtype=torch.float32, device=dev),
@@ -996,13 +1000,13 @@ def main():
     acc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def gpu_check(s32, sel, opeaks):
-            b2 = mf.Bank(wl.m1[sel], wl.m2[sel], f_low=wl.f_low)
+            b2 = mf.Bank(wl.m1[sel], wl.m2[sel], f_low=wl.f_low, fft_mode=fft_mode)
             sg = mf.Segment(torch.from_numpy(s32).to(dev), spec.fs)
             p, _, _ = mf.filter_bank(b2, [sg], wl.threshold, trig_cap=1 << 16)
             pk = mf.peaks_to_numpy(p)
             err = np.abs(pk["rho"].astype(np.float64) - opeaks["rho"]) / np.maximum(opeaks["rho"], 1.0)
             # full rho series of two templates (threshold 0 returns every sample)
-            b3 = mf.Bank(wl.m1[sel[:2]], wl.m2[sel[:2]], f_low=wl.f_low)
+            b3 = mf.Bank(wl.m1[sel[:2]], wl.m2[sel[:2]], f_low=wl.f_low, fft_mode=fft_mode)
             p3, t3, n3 = mf.filter_bank(b3, [sg], 0.0, trig_cap=2 * spec.N)
             tr = mf.triggers_to_numpy(t3, n3)
             import oracle
@@ -1035,7 +1039,10 @@ def main():
                                if graph is not None else "mf_segment_refresh (device s) + mf_filter_bank",
                        "launch": launch_mode,
                        "schedule": schedule,
-                       "phase": "FP64 anchors + FP32 Taylor; FFT FP32"},
+                       "phase": "FP64 anchors + FP32 Taylor; FFT " + {
+                           "fp32": "FP32", "tc_fp16": "FP32 but pass 2's first radix-32 stage on the tensor cores "
+                           "(FP16 hi + lo splits)", "tc_bf16": "FP32 but pass 2's first radix-32 stage on the tensor "
+                           "cores (BF16 hi + lo splits)"}[args.fft_mode]},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "path_roofline": path,
             "rho_err": acc, "cpu_baseline": cpu, "wall_s_timed": wall}
     if rank == 0:
