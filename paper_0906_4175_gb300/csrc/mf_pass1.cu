@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams
 
 int g_pf_blocks_per_sm[3] = {0, 0, 0};   // L = 256, 512, 1024
 int g_pf_sms = 0;
-bool g_pf_enabled = true;
 
 template <int L>
 constexpr int pf_index() { return L == 256 ? 0 : (L == 512 ? 1 : 2); }
@@ -219,7 +218,9 @@ struct PfOp {
 }  // namespace
 
 bool pass1_pf_applies(int log2N, int log2D, int phase_mode) {
-    if (!g_pf_enabled || g_pf_sms <= 0 || phase_mode == MF_PHASE_FP32) return false;
+    if (g_pf_sms <= 0 || phase_mode == MF_PHASE_FP32) return false;
+    const char *env = std::getenv("MFGB_P1PF");   // "0": the per-tile kernel (comparisons)
+    if (env && env[0] == '0') return false;
     if (log2N < 16 || log2N > 21) return false;
     const int log2N2 = log2_n2(log2N), log2N1 = log2N - log2N2;
     const int C = (8192 >> log2N2) < (1 << log2N1) ? (8192 >> log2N2) : (1 << log2N1);   // seqs_per_cta
@@ -238,8 +239,6 @@ cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0,
 }
 
 cudaError_t pass1_pf_kernel_attributes() {
-    const char *env = std::getenv("MFGB_P1PF");
-    g_pf_enabled = !(env && env[0] == '0');
     cudaError_t e = init_twiddle_tables();   // this translation unit's copy of the Stockham tables
     if (e != cudaSuccess) return e;
     int dev = 0;

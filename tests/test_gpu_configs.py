@@ -148,6 +148,21 @@ def test_uneven_bank_schedules_and_graph_agree(mf, uneven_data, monkeypatch):
     assert np.array_equal(mf.triggers_to_numpy(out[1], out[2]).view(np.uint8), tr_a.view(np.uint8))
 
 
+def test_uneven_bank_pass1_kernels_agree(mf, uneven_data, monkeypatch):
+    """The persistent pass 1 (next tile staged by cp.async while the current
+    one is transformed) and the per-tile pass 1 give bit-identical peaks and
+    triggers on the uneven call (segments of 2^18 .. 2^21 samples)."""
+    wl, _, segs = uneven_data
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    monkeypatch.setenv("MFGB_P1PF", "0")
+    _, pk_a, tr_a, n_a = _uneven_call(mf, wl, segs)
+    monkeypatch.setenv("MFGB_P1PF", "1")
+    _, pk_b, tr_b, n_b = _uneven_call(mf, wl, segs)
+    assert n_a == n_b
+    assert np.array_equal(pk_a.view(np.uint8), pk_b.view(np.uint8))
+    assert np.array_equal(tr_a.view(np.uint8), tr_b.view(np.uint8))
+
+
 def _mode_errors(mf, wl, sample, s32, ref, phase_mode):
     """Full rho series of the sampled templates in one phase mode, compared
     with the oracle: (max err, median err, peak indices agree, trigger sets
