@@ -66,11 +66,12 @@ __global__ void k_chisq_units(SegDev seg, const UnitInfo *__restrict__ all, int 
 
 // pass-2 sinks.  The CTA owns rows j2 = tile C .. tile C + C - 1, i.e. C
 // consecutive samples out of every N2, so per-element global accesses from
-// the butterflies would touch one 32-byte sector per lane.  Each warp (one
-// sequence per warp in pass 2) therefore parks |raw|^2 of its outputs in its
-// own sequence's shared-memory row (free once the warp has read its last
-// stage), and finish() moves the C x N1 tile to the unit's output row with
-// the C consecutive samples of each j1 on consecutive threads.
+// the butterflies would touch one 32-byte sector per lane.  Each thread
+// therefore parks |raw|^2 of its outputs in its sequence's shared-memory row
+// (free once every thread of the sequence has read its last stage: the warp
+// for rows of up to 1024 points, the CTA for 2048), and finish() moves the
+// C x N1 tile to the unit's output row with the C consecutive samples of each
+// j1 on consecutive threads.
 template <int L, int C>
 __device__ __forceinline__ float *chi_tile_row(int seq) {
     extern __shared__ float2 chi_smem[];
@@ -80,18 +81,18 @@ __device__ __forceinline__ float *chi_tile_row(int seq) {
 template <int L, int C>
 __device__ __forceinline__ void chi_park(int seq, int b, int stride, const float2 *v, int R) {
     float *row = chi_tile_row<L, C>(seq);
-    __syncwarp();   // every lane of this warp has read its last-stage inputs
+    if constexpr (L / 32 <= 32) __syncwarp();   // the sequence's threads have read their last-stage inputs
+    else __syncthreads();                        // (a 2048-point sequence spans two warps; every thread gets here once)
 #pragma unroll 32
     for (int r = 0; r < R; ++r) row[b + r * stride] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
 }
 
 // mode 0: acc = |raw|^2, 1: acc += |raw|^2, 2: acc = rs2 (p acc - |raw|^2).
-// The shared-memory tile needs every sequence inside one warp (L / 32 <= 32
-// threads per sequence, L <= 1024); longer rows (N >= 2^21) update the output
-// element by element from the butterflies.
+// Rows of up to 2048 points go through the shared-memory tile; longer rows
+// would update the output element by element from the butterflies.
 template <int L, int C>
 struct ChiSink {
-    static constexpr bool kTile = (L / 32) <= 32;
+    static constexpr bool kTile = (L / 32) <= 64;
     struct Params { float *acc; const UnitInfo *units; int log2N2, log2N, mode; float pf; };
     const Params &p;
     const int tile, unit;

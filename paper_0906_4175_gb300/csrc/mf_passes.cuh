@@ -199,14 +199,15 @@ struct RowComplexOut {
 };
 
 // out[slot * out_stride + j2 + N2 j1] = v for every j.  The CTA owns C
-// consecutive rows j2, so each j1 is C consecutive outputs; when a sequence
-// fits one warp (L <= 1024) every warp parks its outputs in its own
-// sequence's shared-memory row (free once the warp has read its last stage)
-// and finish() writes the C x L tile with consecutive threads on consecutive
-// outputs.  Longer rows store element by element.
+// consecutive rows j2, so each j1 is C consecutive outputs; every thread
+// parks its outputs in its sequence's shared-memory row (free once every
+// thread of the sequence has read its last stage: the warp for rows of up to
+// 1024 points, the CTA for 2048) and finish() writes the C x L tile with
+// consecutive threads on consecutive outputs.  Longer rows would store
+// element by element.
 template <int L, int C>
 struct RowTileOut {
-    static constexpr bool kTile = (L / 32) <= 32;
+    static constexpr bool kTile = (L / 32) <= 64;
     struct Params { float2 *out; int log2N2; int64_t out_stride; };
     const Params &p;
     const int tile, slot;
@@ -219,7 +220,8 @@ struct RowTileOut {
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
         if constexpr (kTile) {
             float2 *r0 = row(seq);
-            __syncwarp();   // every lane of this warp has read its last-stage inputs
+            if constexpr (L / 32 <= 32) __syncwarp();   // the sequence's threads have read their last stage
+            else __syncthreads();                        // (two warps per 2048-point sequence; all threads get here once)
 #pragma unroll
             for (int r = 0; r < R; ++r) r0[b + r * stride] = v[r];
         } else {

@@ -95,10 +95,10 @@ def test_chisq_tiny_workload_every_sample(mf):
     _compare(mf, wl.m1, wl.m2, wl.segments[0])
 
 
-@pytest.mark.parametrize("lg,p", [(10, 16), (12, 4), (14, 16), (17, 16), (18, 7)])
+@pytest.mark.parametrize("lg,p", [(10, 16), (12, 4), (14, 16), (17, 16), (18, 7), (21, 8)])
 def test_chisq_sizes(mf, lg, p):
-    """Every FFT split class and several p (including an odd p), heavy
-    templates whose band ends far below Nyquist."""
+    """Every FFT split class (2048-point rows at 2^21) and several p
+    (including an odd p), heavy templates whose band ends far below Nyquist."""
     wl = workloads.small(seed=100 + lg, N=1 << lg, fs=4096.0, n_templates=4, m_lo=1.2, m_hi=12.0)
     _compare(mf, wl.m1, wl.m2, wl.segments[0], p=p)
 
