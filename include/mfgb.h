@@ -338,14 +338,18 @@ int mf_launch_count(int64_t *n);
  * bytes and launch counts (host arrays of MF_N_STAGES), then clears them. */
 int mf_bank_profile(mf_bank bank, int on);
 
-/* mf_bank_debug_stall -- test hook for the bounded device-side waits of the
- * persistent scheduler (segments with N >= 2^13).  With unit >= 0, later
- * mf_filter_bank calls make the row-FFT tiles of that template wait for a
- * completion count that is never reached; after spin_limit back-off
- * iterations (each <= ~1 us; <= 0 restores the default of 4e6) the kernel sets
- * its abort flag and every block returns, so mf_bank_check then reports
- * MF_ETIMEOUT and the outputs of that call are invalid.  unit < 0 turns the
- * hook off.  Nothing faults: the GPU context stays usable. */
+/* mf_bank_debug_stall -- test hook for the bounded device-side waits.  With
+ * unit >= 0, later mf_filter_bank calls withhold something that template's
+ * waits depend on: under the persistent scheduler (N >= 2^13) its row-FFT
+ * tiles wait for a completion count that is never reached; in the per-batch
+ * rows kernels (N = 2^19 .. 2^22) the bulk copies of its rows are never
+ * issued, and in the tensor-core form (fft_mode != MF_FFT_FP32) its tiles'
+ * MMAs are never committed.  After spin_limit back-off iterations (each
+ * <= ~1 us; <= 0 restores the default of 4e6) the waiting threads give up,
+ * set the status, free what they hold (tensor memory) and return, so
+ * mf_bank_check then reports MF_ETIMEOUT and the outputs of that call are
+ * invalid.  unit < 0 turns the hook off.  Nothing faults: the GPU context
+ * stays usable. */
 int mf_bank_debug_stall(mf_bank bank, int64_t unit, int64_t spin_limit);
 int mf_bank_profile_read(mf_bank bank, double *ms, double *bytes, int64_t *launches);
 

@@ -769,7 +769,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             if (rows)
                 MF_CUDA(launch_pass2_rows(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                           std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, sm_count(),
-                                          b->params.fft_mode, st));
+                                          b->params.fft_mode, (int)b->stall_unit, st));
             else
                 MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                      std::max<int64_t>(trig_cap, 0), st));

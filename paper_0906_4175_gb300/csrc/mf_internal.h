@@ -142,7 +142,7 @@ int pass2_rows_partials(int log2N);
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,
-                              int fft_mode, cudaStream_t st);
+                              int fft_mode, int stall_unit, cudaStream_t st);
 cudaError_t launch_reduce_peaks(const SegDev &seg, const UnitInfo *units, int n_units, const float4 *partials,
                                 int nblk, int seg_idx, int n_seg, mf_peak *peaks, cudaStream_t st);
 cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,

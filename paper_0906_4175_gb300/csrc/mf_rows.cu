@@ -84,6 +84,7 @@ struct RowsParams {
     KeyLayout kl;
     int *status;
     long long spin_limit;
+    int stall_unit;             // test hook: rows of this unit never arrive (bounded-wait tests), -1 = none
 };
 
 // epilogue of one row: per-butterfly argmax (lowest j on ties), triggers
@@ -173,6 +174,12 @@ struct GroupRhoSink {
     }
 };
 
+// the test hook's unit: the FP32 rows kernel withholds its row copies, the
+// tensor-core kernel its MMA commits
+__device__ __forceinline__ bool row_withheld(const RowsParams &p, int64_t r) {
+    return p.unit0 + (int)(r >> p.log2N2) == p.stall_unit;
+}
+
 template <int L>
 __device__ __forceinline__ const float2 *row_src(const RowsParams &p, int64_t r) {
     const int64_t n2 = (int64_t)1 << p.log2N2;
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
     const int64_t total = (int64_t)p.n_units << p.log2N2;
     const int64_t step = (int64_t)gridDim.x * NG;
     int64_t r = (int64_t)blockIdx.x * NG + grp;
-    if (r < total && t == 0) {
+    if (r < total && t == 0 && !row_withheld(p, r)) {
         mbar_expect_tx(&bars[grp], L * sizeof(float2));
         bulk_row_copy(region, row_src<L>(p, r), L * sizeof(float2), &bars[grp]);
     }
@@ -244,7 +251,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
         GroupSync<G>::sync();
         // 3./4. the remaining stages, next-row copy, epilogue
         const int64_t rn = r + step;
-        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp], rn < total ? row_src<L>(p, rn) : nullptr);
+        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp],
+                               rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr);
         if constexpr (S::NST == 2) {
             stockham_stage<L, S::R1, 32, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
         } else {
@@ -422,8 +430,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_tc(RowsParams p) 
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         tile_sync(g);
-        // 3. one thread issues the tile's 12 MMAs
-        if (rl == 0 && t == 0) {
+        // 3. one thread issues the tile's 12 MMAs (the test hook withholds a unit's: its wait runs out)
+        if (rl == 0 && t == 0 && !row_withheld(p, r0)) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             constexpr uint32_t fmt = TCM == MF_FFT_TC_BF16 ? 1u : 0u;
             constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
@@ -530,7 +538,7 @@ int pass2_rows_partials(int log2N) {   // partials per unit: one per row and war
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,
-                              int fft_mode, cudaStream_t st) {
+                              int fft_mode, int stall_unit, cudaStream_t st) {
     if (!pass2_rows_applies(seg.log2N)) return cudaErrorInvalidValue;
     if (fft_mode != MF_FFT_FP32 && seg.log2N1 != 10) return cudaErrorInvalidValue;
     RowsParams p;
@@ -549,6 +557,7 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
     p.kl = kl;
     p.status = status;
     p.spin_limit = spin_limit;
+    p.stall_unit = stall_unit;
     const int64_t rows = (int64_t)n_units << seg.log2N2;
     if (seg.log2N1 == 10) {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps - 1) / kWarps);

@@ -363,6 +363,35 @@ def test_bounded_wait_timeout_reports_and_recovers(mf, monkeypatch):
     assert np.array_equal(ref.view(np.uint8), got.view(np.uint8))
 
 
+@pytest.mark.parametrize("lg,fft", [(20, "fp32"), (21, "fp32"), (20, "tc_fp16"), (19, "tc_bf16")])
+def test_rows_kernel_timeout_reports_and_recovers(mf, monkeypatch, lg, fft):
+    """The per-batch rows kernels (1024- and 2048-point rows, and the
+    tensor-core form) with one template's row copies or MMA commits withheld
+    (test hook): its waits run out, the call reports MF_ETIMEOUT, nothing
+    faults, tensor memory is released, and the next call is bit-identical to
+    one made before."""
+    import torch
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    fm = {"fp32": mf.MF_FFT_FP32, "tc_fp16": mf.MF_FFT_TC_FP16, "tc_bf16": mf.MF_FFT_TC_BF16}[fft]
+    wl = workloads.small(seed=40 + lg, N=1 << lg, fs=4096.0, n_templates=5, m_lo=1.2, m_hi=6.0)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2, fft_mode=fm)
+    a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)]
+    assert bank.check() == 0
+    bank.debug_stall(2, spin_limit=2000)
+    mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)
+    assert bank.check(allow_timeout=True) == mf._native.MF_ETIMEOUT
+    bank.debug_stall(-1)
+    b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)]
+    assert bank.check() == 0
+    n = int(a[2][0])
+    assert int(b[2][0]) == n
+    assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8))
+    assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
+
+
 def test_autotune_keeps_results(mf, tmp_path):
     """mf_autotune only changes the schedule: results stay bit-identical and
     the choice is written to the cache file."""
