@@ -46,6 +46,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// as mbar_try_wait, but the thread may sleep up to hint_ns before giving up
+// (fewer polling instructions while a long operation completes)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ void bulk_row_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(dst)),
@@ -459,7 +470,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_tc(RowsParams p) 
         bool mok = true;
         {
             long long it = 0;
-            while (!mbar_try_wait(&bars[kWarps + g], tparity)) {
+            while (!mbar_try_wait_sleep(&bars[kWarps + g], tparity, 1000u)) {
                 if (++it > p.spin_limit) { mok = false; break; }
             }
             mok = __all_sync(0xffffffffu, mok);
@@ -484,8 +495,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_tc(RowsParams p) 
                     : "r"(ta + 16 * c));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    v[8 * c + i] = make_float2(__uint_as_float(d[2 * i]) * unscale, __uint_as_float(d[2 * i + 1]) * unscale);
+                for (int i = 0; i < 8; ++i) {
+                    v[8 * c + i] = make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
+                    if constexpr (TCM == MF_FFT_TC_FP16) v[8 * c + i] = make_float2(v[8 * c + i].x * unscale, v[8 * c + i].y * unscale);
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
