@@ -233,7 +233,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
         // 1. the row has landed (bounded wait; every warp of the group waits on the same barrier)
         long long it = 0;
         bool ok = true;
-        while (!mbar_try_wait(&bars[grp], parity)) {
+        // 2048-point rows: the 16 KB copy is issued only in the last stage, so the
+        // wait may be long; the sleep hint keeps the waiting warps off the issue slots
+        while (!(G > 1 ? mbar_try_wait_sleep(&bars[grp], parity, 500u) : mbar_try_wait(&bars[grp], parity))) {
             if (++it > p.spin_limit) { ok = false; break; }
         }
         ok = __all_sync(0xffffffffu, ok);
