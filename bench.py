@@ -298,8 +298,8 @@ def run_uneven(args, mf, torch, dev):
     """4096 templates (m1, m2 in [1, 34], M <= 35, each cut at its own ISCO
     frequency) over 8 segments of 2^18, 2^18, 2^19, 2^19, 2^20, 2^20, 2^21,
     2^21 samples in one mf_filter_bank call: the per-segment persistent
-    launches as one CUDA graph, the per-batch launches, and per-template
-    launches."""
+    launches as one CUDA graph, the per-batch launches, per-template
+    launches, and the autotuner's choice."""
     import workloads
     wl = workloads.uneven(0)
     segs = [mf.Segment(mf.synth_segment(sp.normals(), sp.N, sp.fs, wl.f_low, sp.injections), sp.fs)
@@ -345,6 +345,18 @@ def run_uneven(args, mf, torch, dev):
             os.environ.pop(k, None)
             if v is not None:
                 os.environ[k] = v
+    # the autotuner's choice (scheduler, exchange budget, kernel forms of the two passes) on this call
+    if not args.no_autotune and not any(os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH")):
+        cache = os.path.join(tempfile.gettempdir(), "mfgb_autotune_uneven.json")
+        mf.autotune(bank, segs, wl.threshold, repeats=1, cache_path=cache)
+        with open(cache) as fh:
+            choice = json.loads(fh.readline())
+        call()
+        torch.cuda.synchronize()
+        g = _capture(torch, call)
+        ms = _timed_steps(torch, g.replay, args.steps, args.warmup, flush, stream)
+        assert bank.check() == 0
+        res["autotuned_graph"] = {"ms_per_call": ms, "n_trig": int(out[2].item()), "choice": choice}
     units = wl.n_templates * n_seg
     eq = wl.n_templates * sum(sp.N for sp in wl.segments) / float(1 << 20)
     best = min(res.values(), key=lambda r: r["ms_per_call"])["ms_per_call"]

@@ -246,8 +246,12 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
  * bank on these segments (the persistent scheduler with 55/60/65% of the SMs
  * starting on template generation + column FFTs, and per-batch launches with
  * 128 MiB..1 GiB of exchange in flight, i.e. 16..128 templates per batch at
- * N = 2^20 and proportionally more at shorter segments) and keeps the fastest
- * in the bank for later calls (the default is per-batch launches with 1 GiB).  It
+ * N = 2^20 and proportionally more at shorter segments, each with the kernel
+ * forms of the two passes: pass 1 persistent with the next tile's inputs
+ * staged by cp.async, or one CTA per column tile; pass 2 in warp-owned rows
+ * with bulk-copy prefetch, or one CTA per row tile) and keeps the fastest in
+ * the bank for later calls (the default is per-batch launches with 1 GiB, the
+ * staged pass 1 and the row pass 2 where they apply).  It
  * runs each candidate 1 + repeats times on cuda_stream and synchronises; it
  * allocates temporary outputs and may grow the bank's workspace.  threshold
  * should be the one the search will use (it sets the trigger traffic).  If

@@ -169,6 +169,9 @@ struct mf_bank_s {
     int sched = 1;
     int64_t tuned_exch = 0;
     double split = 0.60;
+    // kernel forms of the per-batch schedule: pass 1 persistent with staged
+    // inputs (0) or per tile (1); pass 2 in warp-owned rows (0) or per tile (1)
+    int p1_kind = 0, p2_kind = 0;
 };
 
 // Records an event before a launch when profiling; returns the record index or -1.
@@ -502,6 +505,7 @@ constexpr double kSplit = 0.60;
 static bool use_rows(const mf_bank_s *b, const mf_segment_s *g) {
     if (!pass2_rows_applies(g->log2N)) return false;
     if (b->params.fft_mode != MF_FFT_FP32) return true;   // the tensor-core stage lives in the rows kernel
+    if (b->p2_kind == 1) return false;
     const char *e = getenv("MFGB_P2ROWS");
     return !(e && strcmp(e, "0") == 0);
 }
@@ -752,7 +756,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             }
             pi = prof_begin(b, MF_STAGE_PASS1, by_band + by_anc + exch_bytes, st);
             MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors + aoff, w.anchors4 + aoff, w.exch,
-                                 b->params.phase_mode, b->d_tmpl, st));
+                                 b->params.phase_mode, b->d_tmpl, b->p1_kind == 0, st));
             prof_end(b, pi, st);
             if (overlap && u0 + batch < n_t) {
                 const int u1 = u0 + (int)batch;
@@ -860,7 +864,8 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
         }
         for (int l = 0; l <= p && e == cudaSuccess; ++l) {
             const UnitInfo *ul = units + (size_t)l * n;
-            e = launch_pass1(sd, ul, (int)u0, nb, lgD, man, anc, anc4, exch, b->params.phase_mode, b->d_tmpl, st);
+            e = launch_pass1(sd, ul, (int)u0, nb, lgD, man, anc, anc4, exch, b->params.phase_mode, b->d_tmpl,
+                             b->p1_kind == 0, st);
             if (e == cudaSuccess)
                 e = launch_chisq_pass2(sd, ul, (int)u0, nb, exch, chisq, l == p ? 2 : (l == 0 ? 0 : 1), p, st);
             launches += 2;
@@ -1020,13 +1025,25 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     if (!b || !segs || n_seg < 1) return set_err(MF_EINVAL, "need a bank and n_seg >= 1 segments");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (repeats < 1) repeats = 2;
-    struct Cand { int sched; int64_t exch; double split; };
+    struct Cand { int sched; int64_t exch; double split; int p1, p2; };
     std::vector<Cand> cands;
     if (b->params.fft_mode == MF_FFT_FP32)   // the tensor-core stage runs in the per-batch rows kernel only
-        for (double sp : {0.55, 0.60, 0.65}) cands.push_back({0, 0, sp});
+        for (double sp : {0.55, 0.60, 0.65}) cands.push_back({0, 0, sp, 0, 0});
     int64_t maxN = 0;
     for (int s = 0; s < n_seg; ++s) maxN = std::max(maxN, segs[s]->N);
-    for (int64_t mib : {128, 256, 512, 1024}) cands.push_back({1, mib << 20, 0.60});
+    // per-batch launches: exchange budget x the kernel forms of the two passes
+    // (the per-tile forms only where the other form would apply to some segment)
+    bool any_pf = false, any_rows = false;
+    for (int s = 0; s < n_seg; ++s) {
+        const int lgD = choose_log2D(b, segs[s]);
+        any_pf = any_pf || pass1_pf_applies(segs[s]->log2N, lgD, b->params.phase_mode);
+        any_rows = any_rows || (pass2_rows_applies(segs[s]->log2N) && b->params.fft_mode == MF_FFT_FP32);
+    }
+    for (int64_t mib : {128, 256, 512, 1024}) {
+        cands.push_back({1, mib << 20, 0.60, 0, 0});
+        if (any_pf) cands.push_back({1, mib << 20, 0.60, 1, 0});
+        if (any_rows) cands.push_back({1, mib << 20, 0.60, 0, 1});
+    }
     const int64_t cap = 1 << 16;
     mf_peak *pk = nullptr;
     mf_trigger *tr = nullptr;
@@ -1041,12 +1058,14 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     const int64_t saved_exch = b->tuned_exch;
     const double saved_split = b->split;
     float best_ms = 1e30f;
-    Cand best = {saved_sched, saved_exch, saved_split};
+    Cand best = {saved_sched, saved_exch, saved_split, b->p1_kind, b->p2_kind};
     int rc = MF_OK;
     for (const Cand &c : cands) {
         b->sched = c.sched;
         b->tuned_exch = c.exch;
         b->split = c.split;
+        b->p1_kind = c.p1;
+        b->p2_kind = c.p2;
         rc = mf_filter_bank(b, segs, n_seg, threshold, pk, tr, cap, nt, cuda_stream);   // warm-up, sizes workspace
         if (rc) break;
         cudaEventRecord(e0, st);
@@ -1066,15 +1085,20 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     b->sched = best.sched;
     b->tuned_exch = best.exch;
     b->split = best.split;
+    b->p1_kind = best.p1;
+    b->p2_kind = best.p2;
     if (rc) return rc;
     if (cache_path && cache_path[0]) {
         FILE *f = fopen(cache_path, "w");
         if (!f) return set_err(MF_EINVAL, "cannot write %s", cache_path);
         const int64_t ex = best.exch > 0 ? best.exch : kExchBudget;
         fprintf(f, "{\"N\": %lld, \"templates\": %lld, \"segments\": %d, \"scheduler\": \"%s\", "
-                   "\"exchange_mib\": %lld, \"batch_at_max_N\": %lld, \"split\": %.3f, \"ms_per_call\": %.4f}\n",
+                   "\"exchange_mib\": %lld, \"batch_at_max_N\": %lld, \"split\": %.3f, \"pass1\": \"%s\", "
+                   "\"pass2\": \"%s\", \"candidates\": %d, \"ms_per_call\": %.4f}\n",
                 (long long)maxN, (long long)b->n, n_seg, best.sched == 0 ? "persistent" : "batch",
-                (long long)(ex >> 20), (long long)choose_batch(maxN, b->n, ex), best.split, best_ms / repeats);
+                (long long)(ex >> 20), (long long)choose_batch(maxN, b->n, ex), best.split,
+                best.sched == 0 ? "fused" : (best.p1 == 0 ? "persistent-staged" : "per-tile"),
+                best.sched == 0 ? "fused" : (best.p2 == 0 ? "rows" : "per-tile"), (int)cands.size(), best_ms / repeats);
         fclose(f);
     }
     return MF_OK;

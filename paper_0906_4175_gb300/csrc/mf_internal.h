@@ -123,7 +123,7 @@ cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo
                            cudaStream_t st);
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                          int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
-                         int phase_mode, const double *tmpl, cudaStream_t st);
+                         int phase_mode, const double *tmpl, bool allow_pf, cudaStream_t st);
 cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units,
                          const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
                          mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
