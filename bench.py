@@ -880,7 +880,7 @@ def run_refine(args, mf, torch, dev):
     line = {"workload": "refine", "metric": "trigger objective+gradient evaluations/s (Adam ascent of rho^2)",
             "value": evals / (ms / 1e3), "unit": "evaluations/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": "f64 anchor phase + f32 Taylor, f32 sums", "ms_total": ms,
-            "gpu_launches": 2 * (steps + 1),
+            "gpu_launches": 3 * (steps + 1),
             "ascent": "CUDA graph of the whole ascent (refine launches, autograd backward, capturable Adam), "
                       "median of 5 replays",
             "ms_total_eager": ms_eager, "graph_vs_eager_max_rel_diff_rho2": agree,

@@ -306,7 +306,7 @@ int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const int32_t *r
  * memory while they refine: the call makes no cudaMalloc, cudaMallocAsync,
  * cudaFree or other allocating call.  The paper has no counterpart; it exists
  * for ascent loops that run while another component owns the device
- * allocator.  Its per-block partial sums live in one fixed 4 MiB array in
+ * allocator.  Its per-block partial sums and row records live in one fixed 4.5 MiB array in
  * device global memory that every device which loads the library holds until
  * the process exits; hence n <= 4096 rows per call (larger n returns
  * MF_EINVAL with a message).  The first call on a device looks up that

@@ -1191,9 +1191,9 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
     const SegDev sd = seg_dev(seg);
     const int bpr = refine_blocks_for(n, sm_count());
     double *partial = nullptr;
-    cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * 8 * bpr * n, st);
+    cudaError_t e = cudaMallocAsync(&partial, refine_scratch_bytes(n, bpr), st);
     if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, bpr, st);
-    if (e == cudaSuccess) count_launches(2);
+    if (e == cudaSuccess) count_launches(3)   /* row set-up, partial sums, totals */;
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers: %s",
@@ -1225,11 +1225,11 @@ extern "C" int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int bpr = refine_blocks_for(n, sm_count());
     double *partial = nullptr;
-    cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * 8 * bpr * n, st);
+    cudaError_t e = cudaMallocAsync(&partial, refine_scratch_bytes(n, bpr), st);
     if (e == cudaSuccess)
         e = launch_refine_multi(sd.data(), n_seg, row_seg, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial,
                                 bpr, st);
-    if (e == cudaSuccess) count_launches(2);
+    if (e == cudaSuccess) count_launches(3)   /* row set-up, partial sums, totals */;
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers_multi: %s",
@@ -1242,13 +1242,15 @@ extern "C" int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const
 // the point where they refine triggers: an ascent loop that runs while another
 // component owns the device allocator, or code that must never trigger an
 // allocator call inside its hot loop.  This variant keeps the per-block
-// partial sums in a fixed array in device global memory instead of the stream
-// allocation that mf_refine_triggers makes.
+// partial sums and row records in a fixed array in device global memory
+// instead of the stream allocation that mf_refine_triggers makes.
 // ---------------------------------------------------------------------------
 static constexpr int64_t kRefineStaticRows = 4096;   // at most this many theta rows per call
 static constexpr int kRefineStaticBpr = 16;           // blocks per row (== refine_blocks_per_row())
-// 4096 rows x 16 blocks x 8 partial sums x 8 bytes = 4 MiB on every device that loads the library
-static __device__ __align__(256) double g_refine_scratch[kRefineStaticRows * kRefineStaticBpr * 8];
+// 4096 rows x (16 blocks x 8 partial sums x 8 bytes + a 128-byte row record) = 4.5 MiB on every device
+// that loads the library
+static __device__ __align__(256) double
+    g_refine_scratch[kRefineStaticRows * (kRefineStaticBpr * 8 + kRefRowBytesMax / sizeof(double))];
 
 // Device address of g_refine_scratch per device ordinal.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up with
@@ -1291,6 +1293,6 @@ extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *p
     const SegDev sd = seg_dev(seg);
     MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, kRefineStaticBpr,
                           (cudaStream_t)cuda_stream));
-    count_launches(2);
+    count_launches(3)   /* row set-up, partial sums, totals */;
     return MF_OK;
 }

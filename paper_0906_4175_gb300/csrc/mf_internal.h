@@ -154,7 +154,10 @@ int sort_launches(int key_bits);   // kernels queued by launch_sort_triggers
 // tile status words the sort needs for cap records (one per 2048-key tile and digit)
 inline int64_t sort_tile_words(int64_t cap) { return ((cap + 2047) / 2048) * 256; }
 
-// refinement (mf_refine.cu)
+// refinement (mf_refine.cu).  partial: device scratch of refine_scratch_bytes(n, bpr)
+// bytes (8 partial sums per block, then one row record of at most kRefRowBytesMax bytes per row)
+constexpr size_t kRefRowBytesMax = 128;
+size_t refine_scratch_bytes(int64_t n, int bpr);
 cudaError_t launch_refine(const SegDev &seg, double f_low, int phase_mode, const double *theta, int64_t n,
                           const int64_t *band, double *obj, double *grad, double *partial, int bpr,
                           cudaStream_t st);

@@ -93,6 +93,17 @@ __device__ void refine_row_setup(const SegDev &seg, double f_low, int anchored, 
     }
 }
 
+static_assert(sizeof(RefRow) <= kRefRowBytesMax, "row record larger than the scratch layout allows");
+
+size_t refine_scratch_bytes(int64_t n, int bpr) {
+    return sizeof(double) * 8 * (size_t)bpr * (size_t)n + kRefRowBytesMax * (size_t)n;
+}
+
+// the row records follow the per-block partial sums in the scratch
+__device__ __host__ __forceinline__ RefRow *row_records(double *partial, int bpr, int64_t n) {
+    return reinterpret_cast<RefRow *>(partial + 8 * (size_t)bpr * (size_t)n);
+}
+
 struct RefAcc {
     float ar = 0.f, ai = 0.f, fr = 0.f, fi = 0.f, ar1 = 0.f, ai1 = 0.f, ar2 = 0.f, ai2 = 0.f;
     // one bin: phase (turns, reduced to [-1/2, 1/2]) and the FP32 factors
@@ -117,11 +128,23 @@ __device__ __forceinline__ int row_segment(const SegTable<NS> &tab, const int32_
     return (s >= 0 && s < tab.n) ? s : -1;
 }
 
+// One thread per row: template constants, mass derivatives, band, time split
+// and anchor spacing (FP64), once per row instead of once per block.
+template <int NS>
+__global__ void k_refine_setup(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg,
+                               double f_low, int anchored, const double *__restrict__ theta,
+                               const int64_t *__restrict__ band, int64_t n, RefRow *__restrict__ rows) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int si = row_segment(tab, row_seg, i);
+    if (si < 0) return;   // the other kernels check the segment index themselves
+    refine_row_setup(tab.s[si], f_low, anchored, theta, band, i, rows[i]);
+}
+
 template <int NS>
 __global__ void __launch_bounds__(kRefThreads)
-    k_refine_partial(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg, double f_low,
-                     int anchored, const double *__restrict__ theta, const int64_t *__restrict__ band,
-                     double *__restrict__ partial) {
+    k_refine_partial(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg,
+                     const RefRow *__restrict__ rows, double *__restrict__ partial) {
     __shared__ RefRow row;
     __shared__ double red[8][kRefThreads / 32];
     __shared__ float4 sanc[kRefAnchorsPerChunk];
@@ -133,7 +156,7 @@ __global__ void __launch_bounds__(kRefThreads)
         return;
     }
     const SegDev &seg = tab.s[si];
-    if (threadIdx.x == 0) refine_row_setup(seg, f_low, anchored, theta, band, i, row);
+    if (threadIdx.x == 0) row = rows[i];
     __syncthreads();
     const uint32_t nmask = (uint32_t)(seg.N - 1);
     RefAcc acc;
@@ -206,9 +229,8 @@ __global__ void __launch_bounds__(kRefThreads)
 
 template <int NS>
 __global__ void k_refine_final(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg,
-                               double f_low, const double *__restrict__ theta, const int64_t *__restrict__ band,
-                               const double *__restrict__ partial, int bpr, int64_t n, double *__restrict__ obj,
-                               double *__restrict__ grad) {
+                               const RefRow *__restrict__ rows, const double *__restrict__ partial, int bpr,
+                               int64_t n, double *__restrict__ obj, double *__restrict__ grad) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int si = row_segment(tab, row_seg, i);
@@ -218,14 +240,11 @@ __global__ void k_refine_final(const __grid_constant__ SegTable<NS> tab, const i
         grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = nan;
         return;
     }
-    const SegDev &seg = tab.s[si];
-    RefRow row;
-    refine_row_setup(seg, f_low, 0, theta, band, i, row);
     double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < bpr; ++b)
         for (int q = 0; q < 8; ++q) a[q] += partial[(i * bpr + b) * 8 + q];
     const double Rr = a[0], Ri = a[1];
-    const double pr = row.pratio;
+    const double pr = rows[i].pratio;
     obj[i] = (Rr * Rr + Ri * Ri) * pr;
     const double two_pi = 2.0 * kPiD;
     // 2 Re(conj(R) * (i X)) = 2 (Ri Xr - Rr Xi)
@@ -239,12 +258,15 @@ static cudaError_t launch_refine_table(const SegTable<NS> &tab, const int32_t *r
                                        int phase_mode, const double *theta, int64_t n, const int64_t *band,
                                        double *obj, double *grad, double *partial, int bpr, cudaStream_t st) {
     const int anchored = phase_mode == MF_PHASE_FP64 ? 0 : 1;
-    k_refine_partial<NS><<<dim3((unsigned)bpr, (unsigned)n), kRefThreads, 0, st>>>(tab, row_seg, f_low, anchored,
-                                                                                   theta, band, partial);
+    RefRow *rows = row_records(partial, bpr, n);
+    k_refine_setup<NS><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, row_seg, f_low, anchored, theta, band, n,
+                                                                     rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_refine_final<NS><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, row_seg, f_low, theta, band, partial, bpr,
-                                                                     n, obj, grad);
+    k_refine_partial<NS><<<dim3((unsigned)bpr, (unsigned)n), kRefThreads, 0, st>>>(tab, row_seg, rows, partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_refine_final<NS><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, row_seg, rows, partial, bpr, n, obj, grad);
     return cudaGetLastError();
 }
 
