@@ -104,9 +104,35 @@ __device__ __host__ __forceinline__ RefRow *row_records(double *partial, int bpr
     return reinterpret_cast<RefRow *>(partial + 8 * (size_t)bpr * (size_t)n);
 }
 
+// The mass-derivative weights g_m(k) = dpsi/dm(f_k) = sum_p d_p u^p at an
+// anchor centre k_a, with their first two k-derivatives (u = (k df)^(-1/3),
+// du/dk = -u/(3k), d2u/dk2 = 4u/(9k^2)): g(k_a + d) ~ g + g' d + g'' d^2 / 2
+// within the anchor's D <= 256 bins (relative error ~ (D/2k)^3 < 2e-6 at f_low).
+__device__ __forceinline__ void mass_weight_taylor(const float *dc, float u, float ik, float &g0, float &g1,
+                                                   float &g2) {
+    const float u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
+    const float g = dc[0] * u + dc[1] * u2 + dc[2] * u3 + dc[3] * u5;
+    const float gu = dc[0] + 2.f * dc[1] * u + 3.f * dc[2] * u2 + 5.f * dc[3] * u4;
+    const float guu = 2.f * dc[1] + 6.f * dc[2] * u + 20.f * dc[3] * u3;
+    const float du = -u * ik * (1.f / 3.f), d2u = u * ik * ik * (4.f / 9.f);
+    g0 = g;
+    g1 = gu * du;
+    g2 = 0.5f * (guu * du * du + gu * d2u);
+}
+
 struct RefAcc {
     float ar = 0.f, ai = 0.f, fr = 0.f, fi = 0.f, ar1 = 0.f, ai1 = 0.f, ar2 = 0.f, ai2 = 0.f;
-    // one bin: phase (turns, reduced to [-1/2, 1/2]) and the FP32 factors
+    // one bin: phase (turns, reduced to [-1/2, 1/2]), the frequency and the
+    // mass-derivative weights g1 = dpsi/dm1, g2 = dpsi/dm2 at the bin
+    __device__ __forceinline__ void add_w(const float2 w, float ph, float ff, float g1, float g2) {
+        float s, c;
+        __sincosf(6.283185307179586f * ph, &s, &c);
+        const float qr = w.x * c - w.y * s, qi = w.x * s + w.y * c;
+        ar += qr; ai += qi;
+        fr = fmaf(qr, ff, fr); fi = fmaf(qi, ff, fi);
+        ar1 = fmaf(qr, g1, ar1); ai1 = fmaf(qi, g1, ai1);
+        ar2 = fmaf(qr, g2, ar2); ai2 = fmaf(qi, g2, ai2);
+    }
     __device__ __forceinline__ void add(const RefRow &row, const float2 w, float ph, float ff, float uf) {
         float s, c;
         __sincosf(6.283185307179586f * ph, &s, &c);
@@ -149,6 +175,8 @@ __global__ void __launch_bounds__(kRefThreads)
     __shared__ double red[8][kRefThreads / 32];
     __shared__ float4 sanc[kRefAnchorsPerChunk];
     __shared__ float sanc4[kRefAnchorsPerChunk];
+    __shared__ float4 sg[kRefAnchorsPerChunk];    // g1 Taylor (3), g2 value
+    __shared__ float2 sg2[kRefAnchorsPerChunk];   // g2 first and second k-derivative terms
     const int64_t i = blockIdx.y;
     const int si = row_segment(tab, row_seg, i);
     if (si < 0) {   // invalid segment index: an empty sum (the final kernel reports NaN)
@@ -173,9 +201,18 @@ __global__ void __launch_bounds__(kRefThreads)
         const int half = (1 << lg) >> 1;
         for (int64_t gc = gb0; gc < gb1; gc += kRefAnchorsPerChunk) {
             const int64_t gce = (gc + kRefAnchorsPerChunk < gb1) ? gc + kRefAnchorsPerChunk : gb1;
-            if (gc + threadIdx.x < gce)
-                anchor_record(row.c[0], row.c[1], row.c[2], row.c[3], gc + threadIdx.x, lg, seg.df,
-                              sanc[threadIdx.x], sanc4[threadIdx.x]);
+            if (gc + threadIdx.x < gce) {
+                const int64_t g = gc + threadIdx.x;
+                anchor_record(row.c[0], row.c[1], row.c[2], row.c[3], g, lg, seg.df, sanc[threadIdx.x],
+                              sanc4[threadIdx.x]);
+                const float ka = (float)((g << lg) + half);
+                const float u = rcbrtf(ka * (float)seg.df), ik = 1.f / ka;
+                float a0, a1, a2, b0, b1, b2;
+                mass_weight_taylor(row.d1, u, ik, a0, a1, a2);
+                mass_weight_taylor(row.d2, u, ik, b0, b1, b2);
+                sg[threadIdx.x] = make_float4(a0, a1, a2, b0);
+                sg2[threadIdx.x] = make_float2(b1, b2);
+            }
             __syncthreads();
             int64_t kb0 = gc << lg, kb1 = gce << lg;
             if (kb0 < row.k_lo) kb0 = row.k_lo;
@@ -189,7 +226,11 @@ __global__ void __launch_bounds__(kRefThreads)
                 float ph = tt - psi;
                 ph -= rintf(ph);
                 const float ff = (float)k * dff;
-                acc.add(row, __ldg(&seg.W[k]), ph, ff, rcbrtf(ff));
+                const float4 ga = sg[a];
+                const float2 gb = sg2[a];
+                const float g1 = fmaf(fmaf(ga.z, d, ga.y), d, ga.x);
+                const float g2 = fmaf(fmaf(gb.y, d, gb.x), d, ga.w);
+                acc.add_w(__ldg(&seg.W[k]), ph, ff, g1, g2);
             }
             __syncthreads();
         }
