@@ -175,15 +175,17 @@ int mf_filter_bank(mf_bank bank, const mf_segment *segs, int n_seg, float thresh
                    mf_peak *peaks, mf_trigger *trig, int64_t trig_cap, int64_t *n_trig,
                    void *cuda_stream);
 
-/* mf_fft_c2c -- batched complex FP32 FFT with the library's own four-step
- * kernels (the batched transforms the paper timed in Figs. 1-2):
+/* mf_fft_c2c -- batched complex FP32 FFT with the library's own kernels (the
+ * batched transforms the paper timed in Figs. 1-2):
  *   y_b[k] = sum_n x_b[n] exp(sign 2 pi i n k / N),  b < batch, k < N,
  * unnormalised.  x, y: device complex64 (interleaved re, im float pairs,
  * 8-byte aligned), batch entries N apart; y may equal x (in place).
- * N a power of two in [2^10, 2^22]; sign = -1 (forward) or +1.  Allocates a
- * complex64 exchange of up to 1 GiB on cuda_stream (not capturable), queues
- * two kernels per 1 GiB of batch and returns without synchronising.
- * Errors: MF_EINVAL (NULL, size, sign, alignment, inside a capture),
+ * N a power of two in [2^10, 2^22]; sign = -1 (forward) or +1.  N = 2^10 and
+ * 2^11: one kernel holding whole sequences per CTA, no allocation (capturable).
+ * Larger N: the four-step passes through a complex64 exchange of up to 1 GiB
+ * allocated on cuda_stream (not capturable), two kernels per 1 GiB of batch.
+ * Returns without synchronising.
+ * Errors: MF_EINVAL (NULL, size, sign, alignment, N > 2^11 inside a capture),
  * MF_ENOMEM, MF_ECUDA. */
 int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int sign, void *cuda_stream);
 

@@ -18,6 +18,9 @@
 namespace mf {
 cudaError_t filter_kernel_attributes();
 cudaError_t prep_kernel_attributes();
+// batched FFT of whole sequences per CTA (mf_prep.cu), N = 1024 and 2048
+bool fft_c2c_single_pass(int64_t N);
+cudaError_t launch_fft_c2c_single(const float2 *x, float2 *y, int64_t N, int64_t batch, int sign, cudaStream_t st);
 cudaError_t synth_kernel_attributes();
 cudaError_t refine_kernel_attributes();
 cudaError_t chisq_kernel_attributes();
@@ -803,6 +806,11 @@ extern "C" int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int 
     int r0 = ensure_device_init();
     if (r0) return r0;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (fft_c2c_single_pass(N)) {   // whole sequences per CTA: no exchange
+        MF_CUDA(launch_fft_c2c_single((const float2 *)x, (float2 *)y, N, batch, sign, st));
+        count_launches(1);
+        return MF_OK;
+    }
     if (stream_capturing(st)) return set_err(MF_EINVAL, "mf_fft_c2c allocates its exchange and cannot be captured");
     const int64_t chunk = std::min<int64_t>({batch, std::max<int64_t>(1, kExchBudget / (8 * N)), 65535});
     float2 *exch = nullptr;

@@ -82,6 +82,73 @@ struct C2CAttrOp {
     }
 };
 
+// Single-pass batched FFT for N = L <= 2048: a CTA holds C = 8192/L whole
+// sequences (one or two warps each) in shared memory, so every point is read
+// and written once instead of twice through the four-step exchange.
+// Sequence s of the batch is x[s L .. s L + L); CTAs past the batch load zeros
+// and store nothing.
+template <int L, int C>
+struct SeqSrc {
+    static constexpr bool kHalfZero = false;
+    static constexpr size_t kScratchBytes = 0;
+    struct Params { const float2 *x; int64_t n_seq; };
+    const Params &p;
+    const int tile;
+    __device__ SeqSrc(const Params &pp, int tl, int, int, void *) : p(pp), tile(tl) {}
+    __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
+        constexpr int T = L / 32;
+        const int64_t s = (int64_t)tile * C + seq;
+        if (s >= p.n_seq) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = czero();
+            return;
+        }
+        const float2 *x = p.x + s * L;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = __ldcs(&x[t + r * T]);
+    }
+};
+template <int L, int C>
+struct SeqOut {
+    struct Params { float2 *y; int64_t n_seq; };
+    const Params &p;
+    const int tile;
+    __device__ SeqOut(const Params &pp, int tl, int, int) : p(pp), tile(tl) {}
+    template <int R>
+    __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
+        const int64_t s = (int64_t)tile * C + seq;
+        if (s >= p.n_seq) return;
+        float2 *y = p.y + s * L;
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcs(&y[b + r * stride], v[r]);
+    }
+    __device__ __forceinline__ void finish(float2 *) const {}
+};
+
+template <int L, int SIGN>
+static cudaError_t run_c2c_single(const float2 *x, float2 *y, int64_t batch, cudaStream_t st) {
+    constexpr int C = 8192 / L;
+    typename SeqSrc<L, C>::Params sp{x, batch};
+    typename SeqOut<L, C>::Params kp{y, batch};
+    return run_pass<L, C, false, SIGN, SeqSrc<L, C>, SeqOut<L, C>>(dim3((unsigned)((batch + C - 1) / C), 1), sp,
+                                                                   kp, st);
+}
+
+template <int SIGN>
+static cudaError_t c2c_single_attrs() {
+    cudaError_t e = set_pass_attrs<1024, 8, false, SIGN, SeqSrc<1024, 8>, SeqOut<1024, 8>>();
+    if (e != cudaSuccess) return e;
+    return set_pass_attrs<2048, 4, false, SIGN, SeqSrc<2048, 4>, SeqOut<2048, 4>>();
+}
+
+bool fft_c2c_single_pass(int64_t N) { return N == 1024 || N == 2048; }
+
+cudaError_t launch_fft_c2c_single(const float2 *x, float2 *y, int64_t N, int64_t batch, int sign, cudaStream_t st) {
+    if (N == 1024) return sign < 0 ? run_c2c_single<1024, -1>(x, y, batch, st) : run_c2c_single<1024, +1>(x, y, batch, st);
+    if (N == 2048) return sign < 0 ? run_c2c_single<2048, -1>(x, y, batch, st) : run_c2c_single<2048, +1>(x, y, batch, st);
+    return cudaErrorInvalidValue;
+}
+
 static int ilog2_i64(int64_t n) {
     int r = 0;
     while ((int64_t)1 << (r + 1) <= n) ++r;
@@ -121,7 +188,9 @@ cudaError_t prep_kernel_attributes() {
         cudaError_t e = dispatch_split(lg, op);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    cudaError_t e = c2c_single_attrs<-1>();
+    if (e == cudaSuccess) e = c2c_single_attrs<+1>();
+    return e;
 }
 
 // q_k = f^(-7/3)/S_k for 1 <= k < N/2, q_0 = 0.  Eq. (2) is evaluated as

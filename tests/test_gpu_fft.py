@@ -45,16 +45,20 @@ def test_fft_matches_numpy(mf, lg, batch, sign):
     _check(y, x.astype(np.complex128), sign)
 
 
-def test_fft_in_place_and_large_batch(mf):
-    """In place, and a batch larger than one exchange chunk (1 GiB / 8 N)."""
+@pytest.mark.parametrize("lg,batch", [(10, 131073), (12, 32769)])
+def test_fft_in_place_and_large_batch(mf, lg, batch):
+    """In place with a ragged batch: N = 2^10 through the single-pass kernel
+    (8 sequences per CTA, 131073 of them), N = 2^12 through the four-step
+    passes with a batch one larger than an exchange chunk (1 GiB / 8 N)."""
     import torch
-    N, batch = 1 << 10, 131073
-    rng = np.random.default_rng(5)
-    x = (rng.standard_normal((batch, N)) + 1j * rng.standard_normal((batch, N))).astype(np.complex64)
+    N = 1 << lg
+    rng = np.random.default_rng(5 + lg)
+    x = (rng.standard_normal((batch, N), dtype=np.float32)
+         + 1j * rng.standard_normal((batch, N), dtype=np.float32)).astype(np.complex64)
     t = torch.from_numpy(x).cuda()
     mf.fft(t, sign=-1, out=t)
     y = t.cpu().numpy()
-    for b in (0, 1, 65534, 65535, 131071, 131072):
+    for b in sorted({0, 1, batch // 2 - 1, batch // 2, batch - 2, batch - 1}):
         _check(y[b:b + 1], x[b:b + 1].astype(np.complex128), -1)
 
 
