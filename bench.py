@@ -1047,6 +1047,34 @@ def main():
     path = {"model_bytes_per_template": b_total / (wl.n_templates * args.steps),
             "achieved_gbs": b_total / (tot_ms / 1e3) / 1e9, "frac": b_total / (tot_ms / 1e3) / 1e9 / peak}
 
+    # segment conditioning timed on its own, and the filter without it (the
+    # step above includes mf_segment_refresh, so `value` is the inclusive rate)
+    conditioning = None
+    if graph is not None and rank == 0:
+        g_ref = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_ref):
+            seg.refresh(s_dev)
+        g_fil = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_fil):
+            mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
+        ms_ref = _timed_steps(torch, g_ref.replay, args.steps, args.warmup, flush, stream)
+        ms_fil = _timed_steps(torch, g_fil.replay, args.steps, args.warmup, flush, stream)
+        ups = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s_new = mf.Segment(s_dev, spec.fs)   # mf_segment_upload: allocation + conditioning
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ups.append(e0.elapsed_time(e1))
+            del s_new
+        assert bank.check() == 0
+        conditioning = {"segment_upload_ms": statistics.median(ups), "segment_refresh_ms": ms_ref,
+                        "filter_only_ms": ms_fil, "filter_only_templates_per_s": wl.n_templates / (ms_fil / 1e3),
+                        "note": "value includes mf_segment_refresh in every step; filter_only excludes it "
+                                "(each timed on its own CUDA graph, L2 flushed per step)"}
+
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     s_host = torch.empty(spec.N, dtype=torch.float32, pin_memory=True)
     s_host.copy_(s_dev.cpu())
@@ -1119,6 +1147,7 @@ def main():
                        "step": "mf_segment_refresh (device s) + mf_filter_bank, one CUDA-graph replay"
                                if graph is not None else "mf_segment_refresh (device s) + mf_filter_bank",
                        "launch": launch_mode,
+                       "conditioning": conditioning,
                        "schedule": schedule,
                        "phase": "FP64 anchors + FP32 Taylor; FFT " + {
                            "fp32": "FP32", "tc_fp16": "FP32 but pass 2's first radix-32 stage on the tensor cores "
