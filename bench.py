@@ -635,12 +635,12 @@ def run_chisq(args, mf, torch, dev):
     steps = max(3, args.steps // 10)
     ms = _timed_steps(torch, call, steps, args.warmup, flush, torch.cuda.current_stream())
     # algorithmic bytes per template (model): the W band once; anchors and the
-    # exchange write + read for each sub-band and the full band; the
-    # accumulator's first store, later read-modify-writes and the final
-    # read + write of chi^2
+    # exchange write + read for each sub-band and the full band; one write of
+    # chi^2 (at N = 2^20 the rows kernel sums every sub-band of a row in
+    # registers: no accumulator in memory)
     K = _band_bins(wl.m1[sel], wl.m2[sel], N, spec.fs, wl.f_low).astype(np.float64)
     n_anc = K / 128.0
-    per_t = 8.0 * K + (p + 1) * (20.0 * n_anc + 16.0 * N) + 4.0 * N + (p - 1) * 8.0 * N + 8.0 * N
+    per_t = 8.0 * K + (p + 1) * (20.0 * n_anc + 16.0 * N) + 4.0 * N
     achieved = float(per_t.sum()) / (ms / 1e3) / 1e9
     peak, peak_kind = _hbm_peak()
     cpu = None

@@ -200,9 +200,12 @@ int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int sign, void 
  * chisq: device FP32 [n][N] (row i for template tmpl[i]); edges: NULL or
  * device int64 [n][p+1] receiving b_0..b_p.  A template index outside the
  * bank gives an empty band (a zero row).  1 <= p <= 64, 1 <= n <= 2^24.
- * Cost: p + 1 inverse FFTs of length N per template.  Allocates scratch on
- * cuda_stream (so it cannot be captured in a graph) and returns without
- * synchronising.
+ * Cost: p + 1 inverse FFTs of length N per template (at N = 2^19, 2^20 their
+ * second passes run as one kernel that sums the sub-bands in registers).
+ * Allocates scratch on cuda_stream (so it cannot be captured in a graph) and
+ * returns without synchronising.  A bounded device wait that runs out (row
+ * copies of the N = 2^19, 2^20 kernel) makes the next mf_bank_check on this
+ * bank return MF_ETIMEOUT.
  * Errors: MF_EINVAL (NULL, sizes, devices, f_low >= f_cut, inside a capture),
  * MF_ENOMEM, MF_ECUDA. */
 int mf_chisq_series(mf_bank bank, mf_segment seg, const int32_t *tmpl, int64_t n, int p,

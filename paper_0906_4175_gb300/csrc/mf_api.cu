@@ -18,6 +18,10 @@
 namespace mf {
 cudaError_t filter_kernel_attributes();
 cudaError_t prep_kernel_attributes();
+// chi^2 of 1024-point rows over all sub-bands in one pass (mf_chisq.cu)
+bool chisq_rows_applies(int log2N);
+cudaError_t launch_chisq_rows(const SegDev &seg, const float2 *exch, const UnitInfo *full, int unit0, int nb, int p,
+                              float *chisq, int *status, long long spin_limit, int n_sm, cudaStream_t st);
 // batched FFT of whole sequences per CTA (mf_prep.cu), N = 1024 and 2048
 bool fft_c2c_single_pass(int64_t N);
 cudaError_t launch_fft_c2c_single(const float2 *x, float2 *y, int64_t N, int64_t batch, int sign, cudaStream_t st);
@@ -175,6 +179,7 @@ struct mf_bank_s {
     // kernel forms of the per-batch schedule: pass 1 persistent with staged
     // inputs (0) or per tile (1); pass 2 in warp-owned rows (0) or per tile (1)
     int p1_kind = 0, p2_kind = 0;
+    int *chi_status = nullptr;        // status of the last mf_chisq_series (bit 2: a bounded wait ran out)
 };
 
 // Records an event before a launch when profiling; returns the record index or -1.
@@ -291,6 +296,7 @@ extern "C" int mf_bank_destroy(mf_bank b) {
     for (auto &r : b->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     b->ws.release();
     cudaFree(b->d_tmpl);
+    cudaFree(b->chi_status);
     if (b->ev_p1) cudaEventDestroy(b->ev_p1);
     if (b->ev_anc) cudaEventDestroy(b->ev_anc);
     if (b->side) cudaStreamDestroy(b->side);
@@ -848,8 +854,15 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     const int lgD = choose_log2D(b, seg);
     const int man = (int)(((seg->N / 2) >> lgD) + 2);
     const int n_t = (int)b->n;
-    const int64_t batch = std::min<int64_t>(n, choose_batch(seg->N, n, b->tuned_exch));
+    // 1024-point rows: every sub-band's exchange of a batch first, then one
+    // rows kernel over all of them (p + 1 exchanges per template in flight)
+    const bool rows = chisq_rows_applies(seg->log2N);
+    const int64_t budget = b->tuned_exch > 0 ? b->tuned_exch : kExchBudget;
+    const int64_t batch = rows ? std::max<int64_t>(1, std::min<int64_t>(n, budget / (8 * seg->N * (p + 1))))
+                               : std::min<int64_t>(n, choose_batch(seg->N, n, b->tuned_exch));
     const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
+    if (rows && !b->chi_status) MF_CUDA(cudaMalloc(&b->chi_status, sizeof(int)));
+    if (b->chi_status) MF_CUDA(cudaMemsetAsync(b->chi_status, 0, sizeof(int), st));
     UnitInfo *all = nullptr, *units = nullptr;
     float4 *anc = nullptr;
     float *anc4 = nullptr;
@@ -858,7 +871,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     if (e == cudaSuccess) e = cudaMallocAsync(&units, sizeof(UnitInfo) * (size_t)(p + 1) * n, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&anc, sizeof(float4) * man * batch, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&anc4, sizeof(float) * man * batch, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * seg->N * batch, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * seg->N * batch * (rows ? p + 1 : 1), st);
     int launches = 0;
     if (e == cudaSuccess) e = launch_units(sd, b->d_tmpl, n_t, b->params.f_low, 0.f, lgD, all, st);
     if (e == cudaSuccess) e = launch_chisq_units(sd, all, n_t, tmpl, (int)n, p, units, edges, st);
@@ -869,6 +882,19 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
         if (anchors) {
             e = launch_anchors(sd, b->d_tmpl, full, (int)u0, nb, lgD, man, anc, anc4, st);
             ++launches;
+        }
+        if (rows) {
+            for (int l = 0; l <= p && e == cudaSuccess; ++l) {
+                e = launch_pass1(sd, units + (size_t)l * n, (int)u0, nb, lgD, man, anc, anc4,
+                                 exch + (size_t)l * nb * seg->N, b->params.phase_mode, b->d_tmpl, b->p1_kind == 0,
+                                 st);
+                ++launches;
+            }
+            if (e == cudaSuccess)
+                e = launch_chisq_rows(sd, exch, full, (int)u0, nb, p, chisq, b->chi_status, b->spin_limit, sm_count(),
+                                      st);
+            ++launches;
+            continue;
         }
         for (int l = 0; l <= p && e == cudaSuccess; ++l) {
             const UnitInfo *ul = units + (size_t)l * n;
@@ -1016,6 +1042,11 @@ extern "C" int mf_bank_profile_read(mf_bank b, double *ms, double *bytes, int64_
 extern "C" int mf_bank_check(mf_bank b, void *cuda_stream) {
     if (!b) return set_err(MF_EINVAL, "NULL bank");
     MF_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    if (b->chi_status) {
+        int cs = 0;
+        MF_CUDA(cudaMemcpy(&cs, b->chi_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (cs & 2) return set_err(MF_ETIMEOUT, "a bounded device wait expired in the last mf_chisq_series");
+    }
     if (!b->ws.status) return MF_OK;
     int st = 0;
     MF_CUDA(cudaMemcpy(&st, b->ws.status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -12,6 +12,8 @@
 // the sub-band only, column IFFTs) and a pass 2 whose sink accumulates
 // |raw_l|^2 into the caller's output row; the last, full-band pass 2 turns
 // the sum into chi^2.  Neither z_l nor z is stored.
+#include <algorithm>
+
 #include "mf_filter.cuh"
 
 namespace mf {
@@ -150,7 +152,176 @@ struct ChiSink {
     }
 };
 
+// ---------------------------------------------------------------------------
+// chi^2 rows kernel (N1 = 1024, N = 2^19 and 2^20).  Pass 1 has written the
+// exchange of every sub-band l = 0..p of a batch of nb templates, sub-band l
+// of entry b at exch + (l nb + b) N.  Each warp owns one row j2 of one entry
+// and transforms it for l = 0..p in turn: the row arrives by a bulk copy
+// (cp.async.bulk, mbarrier, bounded wait), stage 0 runs from the staged row,
+// and once the last stage has read the warp's region the copy of the same row
+// of sub-band l + 1 is issued, so it lands under the arithmetic.  |raw_l|^2 is
+// summed in registers over l < p and |raw|^2 (l = p) kept, so
+//   chi^2 = rho_scale^2 (p sum_l |raw_l|^2 - |raw|^2)
+// is formed without any accumulator in memory.  The CTA's 8 warps own 8
+// consecutive rows; they park their 1024 values each in their regions and
+// write the 8 x 1024 tile with 8 consecutive samples per 32-byte sector.  The
+// sums run in the same order and with the same butterflies as the per-tile
+// path, so the results are the same bit for bit.
+// ---------------------------------------------------------------------------
 namespace {
+
+__device__ __forceinline__ uint32_t cs_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cs_mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cs_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool cs_mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(cs_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// generic-proxy accesses of this thread before the async-proxy refill of its region
+__device__ __forceinline__ void cs_fence_proxy() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void cs_row_copy(float2 *dst, const float2 *src, uint64_t *bar) {
+    constexpr uint32_t bytes = 1024 * sizeof(float2);
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     cs_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     cs_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(cs_addr(bar))
+                 : "memory");
+}
+
+struct ChiWarpSync {
+    static __device__ __forceinline__ void sync() { __syncwarp(); }
+};
+
+constexpr int kChiWarps = 8;
+
+struct ChiRowsParams {
+    const float2 *exch;
+    const UnitInfo *full;   // full-band units of the call's template list
+    float *chisq;           // [n][N]
+    int unit0, nb, p;
+    int log2N, log2N2;
+    int *status;            // bit 2: a wait ran out
+    long long spin_limit;
+};
+
+// last-stage sink: |raw_l|^2 of the thread's 32 outputs (t + 32 q) summed over
+// l < p; at l = p (the full band) the sum becomes chi^2 in place; refills the
+// region with the next sub-band's row
+struct ChiRowAcc {
+    float acc[32];
+    int l = 0, p = 0;
+    float pf = 0.f, rs2 = 0.f;
+    float2 *region = nullptr;
+    uint64_t *bar = nullptr;
+    const float2 *next_src = nullptr;
+    __device__ __forceinline__ void after_loads() {
+        __syncwarp();
+        cs_fence_proxy();
+        if (next_src != nullptr && (threadIdx.x & 31) == 0) cs_row_copy(region, next_src, bar);
+    }
+    template <int R>
+    __device__ __forceinline__ void store(int, int, int, const float2 *v) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float pw = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+            if (l < p) acc[r] = l == 0 ? pw : acc[r] + pw;
+            else acc[r] = rs2 * fmaf(pf, acc[r], -pw);
+        }
+    }
+};
+
+__device__ __forceinline__ const float2 *chi_row_src(const ChiRowsParams &p, int64_t r, int l) {
+    const int64_t b = r >> p.log2N2, j2 = r & (((int64_t)1 << p.log2N2) - 1);
+    return p.exch + (((int64_t)l * p.nb + b) << p.log2N) + (j2 << 10);
+}
+
+__global__ void __launch_bounds__(kChiWarps * 32, 2) k_chisq_rows(ChiRowsParams p) {
+    constexpr int L = 1024;
+    using S = FftShape<L>;
+    extern __shared__ __align__(16) float2 chi_rows_smem[];
+    float2 *tw = chi_rows_smem + kChiWarps * S::STRIDE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tw + TwTable<L>::SIZE);
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+    float2 *region = chi_rows_smem + w * S::STRIDE;
+    fill_twiddles<L>(tw);
+    if (t == 0) cs_mbar_init(&bars[w]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    // rows of the batch: nb N2, a multiple of 8 (N2 >= 512), so every warp has a row in every round
+    const int64_t total = (int64_t)p.nb << p.log2N2;
+    const int64_t step = (int64_t)gridDim.x * kChiWarps;
+    const float pf = (float)p.p;
+    int64_t r0 = (int64_t)blockIdx.x * kChiWarps;
+    if (r0 < total && t == 0) cs_row_copy(region, chi_row_src(p, r0 + w, 0), &bars[w]);
+    uint32_t parity = 0;
+    bool ok = true;
+    for (; r0 < total; r0 += step) {
+        const int64_t r = r0 + w;
+        ChiRowAcc snk;
+        snk.p = p.p;
+        snk.pf = pf;
+        {
+            const float rs = p.full[p.unit0 + (int)(r >> p.log2N2)].rho_scale;
+            snk.rs2 = rs * rs;
+        }
+        snk.region = region;
+        snk.bar = &bars[w];
+        for (int l = 0; l <= p.p; ++l) {
+            // the row of sub-band l has landed (bounded; on expiry the status
+            // bit is set and the loop runs on, so no barrier waits for it)
+            long long it = 0;
+            while (!cs_mbar_try_wait(&bars[w], parity)) {
+                if (++it > p.spin_limit) { ok = false; break; }
+            }
+            parity ^= 1u;
+            float2 v[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = region[t + 32 * q];
+            Dft<32, +1>::run(v);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
+            __syncwarp();
+            snk.l = l;
+            snk.next_src = l < p.p ? chi_row_src(p, r, l + 1) : nullptr;   // the next row waits for the flush
+            stockham_stage<L, S::R1, 32, +1, true, ChiRowAcc, ChiWarpSync>(region, tw, 0, t, snk);
+        }
+        // chi^2 of the row's 1024 samples j2 + N2 (t + 32 q), parked in the warp's region
+        float *rowf = reinterpret_cast<float *>(region);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) rowf[t + 32 * q] = snk.acc[q];
+        __syncthreads();
+        // the CTA's 8 rows j2 .. j2 + 7 of entry b: 8 consecutive samples per j1
+        const int64_t jb = r0 & (((int64_t)1 << p.log2N2) - 1);
+        float *out = p.chisq + ((int64_t)(p.unit0 + (r0 >> p.log2N2)) << p.log2N) + jb;
+        for (int idx = threadIdx.x; idx < kChiWarps * L; idx += kChiWarps * 32) {
+            const int s = idx & (kChiWarps - 1), j1 = idx >> 3;
+            __stcs(&out[s + ((int64_t)j1 << p.log2N2)],
+                   reinterpret_cast<const float *>(chi_rows_smem + s * S::STRIDE)[j1]);
+        }
+        cs_fence_proxy();
+        __syncthreads();   // the tile is read: the regions may be refilled
+        const int64_t rn = r + step;
+        if (rn < total && t == 0) cs_row_copy(region, chi_row_src(p, rn, 0), &bars[w]);
+    }
+    if (!ok && t == 0 && p.status != nullptr) atomicOr(p.status, 2);
+}
+
+static size_t chi_rows_smem_bytes() {
+    return (size_t)kChiWarps * FftShape<1024>::STRIDE * sizeof(float2) + (size_t)TwTable<1024>::SIZE * sizeof(float2) +
+           kChiWarps * sizeof(uint64_t);
+}
+
 struct ChiPass2Op {
     const SegDev &seg;
     const UnitInfo *units;
@@ -192,10 +363,27 @@ cudaError_t launch_chisq_pass2(const SegDev &seg, const UnitInfo *units, int uni
     return dispatch_split(seg.log2N, op);
 }
 
+bool chisq_rows_applies(int log2N) { return log2N - log2_n2(log2N) == 10; }
+
+cudaError_t launch_chisq_rows(const SegDev &seg, const float2 *exch, const UnitInfo *full, int unit0, int nb, int p,
+                              float *chisq, int *status, long long spin_limit, int n_sm, cudaStream_t st) {
+    if (!chisq_rows_applies(seg.log2N) || nb < 1) return cudaErrorInvalidValue;
+    ChiRowsParams q{exch, full, chisq, unit0, nb, p, seg.log2N, seg.log2N2, status, spin_limit};
+    const int64_t rounds = ((int64_t)nb << seg.log2N2) / kChiWarps;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)n_sm, rounds));
+    k_chisq_rows<<<grid, kChiWarps * 32, chi_rows_smem_bytes(), st>>>(q);
+    return cudaGetLastError();
+}
+
 cudaError_t chisq_kernel_attributes() {
     {
         cudaError_t e0 = init_twiddle_tables();
         if (e0 != cudaSuccess) return e0;
+    }
+    {
+        cudaError_t e1 = cudaFuncSetAttribute(k_chisq_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)chi_rows_smem_bytes());
+        if (e1 != cudaSuccess) return e1;
     }
     for (int lg = 10; lg <= 22; ++lg) {
         ChiAttrOp op;

@@ -95,10 +95,11 @@ def test_chisq_tiny_workload_every_sample(mf):
     _compare(mf, wl.m1, wl.m2, wl.segments[0])
 
 
-@pytest.mark.parametrize("lg,p", [(10, 16), (12, 4), (14, 16), (17, 16), (18, 7), (21, 8)])
+@pytest.mark.parametrize("lg,p", [(10, 16), (12, 4), (14, 16), (17, 16), (18, 7), (19, 5), (21, 8)])
 def test_chisq_sizes(mf, lg, p):
-    """Every FFT split class (2048-point rows at 2^21) and several p
-    (including an odd p), heavy templates whose band ends far below Nyquist."""
+    """Every FFT split class (2048-point rows at 2^21; at 2^19 and 2^20 the
+    rows kernel over all sub-bands) and several p (including an odd p), heavy
+    templates whose band ends far below Nyquist."""
     wl = workloads.small(seed=100 + lg, N=1 << lg, fs=4096.0, n_templates=4, m_lo=1.2, m_hi=12.0)
     _compare(mf, wl.m1, wl.m2, wl.segments[0], p=p)
 
@@ -117,6 +118,13 @@ def test_chisq_bench_segment_sampled(mf):
     chi, refs, _ = _compare(mf, wl.m1[sel], wl.m2[sel], spec)
     loud = [i for i, t in enumerate(sel) if t in set(int(x) for x in np.argsort(-pk["rho"])[:4])]
     assert all(float(np.max(refs[i]["rho"])) > 7.0 for i in loud)
+
+
+def test_chisq_two_batches_at_2p20(mf):
+    """N = 2^20, p = 16: 9 templates make two batches of the rows kernel (7
+    templates' 17 exchanges fill the 1 GiB budget), every sample checked."""
+    wl = workloads.small(seed=2020, N=1 << 20, fs=4096.0, n_templates=9, m_lo=1.2, m_hi=6.0)
+    _compare(mf, wl.m1, wl.m2, wl.segments[0], p=16)
 
 
 def test_chisq_noise_mean_and_invalid_index(mf):
