@@ -353,7 +353,8 @@ int mf_bank_profile(mf_bank bank, int on);
  * tiles wait for a completion count that is never reached; in the per-batch
  * rows kernels (N = 2^19 .. 2^22) the bulk copies of its rows are never
  * issued, and in the tensor-core form (fft_mode != MF_FFT_FP32) its tiles'
- * MMAs are never committed.  After spin_limit back-off iterations (each
+ * MMAs are never committed; in mf_chisq_series at N = 2^19, 2^20 the row
+ * copies of the template list's entry `unit` are never issued.  After spin_limit back-off iterations (each
  * <= ~1 us; <= 0 restores the default of 4e6) the waiting threads give up,
  * set the status, free what they hold (tensor memory) and return, so
  * mf_bank_check then reports MF_ETIMEOUT and the outputs of that call are

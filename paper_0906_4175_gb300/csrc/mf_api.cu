@@ -21,7 +21,7 @@ cudaError_t prep_kernel_attributes();
 // chi^2 of 1024-point rows over all sub-bands in one pass (mf_chisq.cu)
 bool chisq_rows_applies(int log2N);
 cudaError_t launch_chisq_rows(const SegDev &seg, const float2 *exch, const UnitInfo *full, int unit0, int nb, int p,
-                              float *chisq, int *status, long long spin_limit, int n_sm, cudaStream_t st);
+                              float *chisq, int *status, long long spin_limit, int stall, int n_sm, cudaStream_t st);
 // batched FFT of whole sequences per CTA (mf_prep.cu), N = 1024 and 2048
 bool fft_c2c_single_pass(int64_t N);
 cudaError_t launch_fft_c2c_single(const float2 *x, float2 *y, int64_t N, int64_t batch, int sign, cudaStream_t st);
@@ -891,8 +891,8 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
                 ++launches;
             }
             if (e == cudaSuccess)
-                e = launch_chisq_rows(sd, exch, full, (int)u0, nb, p, chisq, b->chi_status, b->spin_limit, sm_count(),
-                                      st);
+                e = launch_chisq_rows(sd, exch, full, (int)u0, nb, p, chisq, b->chi_status, b->spin_limit,
+                                      (int)b->stall_unit, sm_count(), st);
             ++launches;
             continue;
         }

@@ -211,6 +211,7 @@ struct ChiRowsParams {
     int log2N, log2N2;
     int *status;            // bit 2: a wait ran out
     long long spin_limit;
+    int stall;              // test hook: the row copies of list entry `stall` are never issued (-1: none)
 };
 
 // last-stage sink: |raw_l|^2 of the thread's 32 outputs (t + 32 q) summed over
@@ -239,6 +240,10 @@ struct ChiRowAcc {
     }
 };
 
+__device__ __forceinline__ bool chi_withheld(const ChiRowsParams &p, int64_t r) {
+    return p.unit0 + (int)(r >> p.log2N2) == p.stall;
+}
+
 __device__ __forceinline__ const float2 *chi_row_src(const ChiRowsParams &p, int64_t r, int l) {
     const int64_t b = r >> p.log2N2, j2 = r & (((int64_t)1 << p.log2N2) - 1);
     return p.exch + (((int64_t)l * p.nb + b) << p.log2N) + (j2 << 10);
@@ -261,9 +266,11 @@ __global__ void __launch_bounds__(kChiWarps * 32, 2) k_chisq_rows(ChiRowsParams 
     const int64_t step = (int64_t)gridDim.x * kChiWarps;
     const float pf = (float)p.p;
     int64_t r0 = (int64_t)blockIdx.x * kChiWarps;
-    if (r0 < total && t == 0) cs_row_copy(region, chi_row_src(p, r0 + w, 0), &bars[w]);
+    if (r0 < total && t == 0 && !chi_withheld(p, r0 + w)) cs_row_copy(region, chi_row_src(p, r0 + w, 0), &bars[w]);
     uint32_t parity = 0;
-    bool ok = true;
+    // a warp whose wait ran out stops waiting and issues no further copies
+    // (none of its copies is then in flight), but keeps to the CTA barriers
+    bool dead = false;
     for (; r0 < total; r0 += step) {
         const int64_t r = r0 + w;
         ChiRowAcc snk;
@@ -276,13 +283,17 @@ __global__ void __launch_bounds__(kChiWarps * 32, 2) k_chisq_rows(ChiRowsParams 
         snk.region = region;
         snk.bar = &bars[w];
         for (int l = 0; l <= p.p; ++l) {
-            // the row of sub-band l has landed (bounded; on expiry the status
-            // bit is set and the loop runs on, so no barrier waits for it)
-            long long it = 0;
-            while (!cs_mbar_try_wait(&bars[w], parity)) {
-                if (++it > p.spin_limit) { ok = false; break; }
+            // the row of sub-band l has landed (bounded; on expiry the warp is
+            // marked dead and the status bit set at the end)
+            if (!dead) {
+                long long it = 0;
+                bool got = true;
+                while (!cs_mbar_try_wait(&bars[w], parity)) {
+                    if (++it > p.spin_limit) { got = false; break; }
+                }
+                dead = !__all_sync(0xffffffffu, got);
+                parity ^= 1u;
             }
-            parity ^= 1u;
             float2 v[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) v[q] = region[t + 32 * q];
@@ -292,7 +303,8 @@ __global__ void __launch_bounds__(kChiWarps * 32, 2) k_chisq_rows(ChiRowsParams 
             for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
             __syncwarp();
             snk.l = l;
-            snk.next_src = l < p.p ? chi_row_src(p, r, l + 1) : nullptr;   // the next row waits for the flush
+            // the next row's first copy waits for the flush
+            snk.next_src = (l < p.p && !dead && !chi_withheld(p, r)) ? chi_row_src(p, r, l + 1) : nullptr;
             stockham_stage<L, S::R1, 32, +1, true, ChiRowAcc, ChiWarpSync>(region, tw, 0, t, snk);
         }
         // chi^2 of the row's 1024 samples j2 + N2 (t + 32 q), parked in the warp's region
@@ -312,9 +324,9 @@ __global__ void __launch_bounds__(kChiWarps * 32, 2) k_chisq_rows(ChiRowsParams 
         cs_fence_proxy();
         __syncthreads();   // the tile is read: the regions may be refilled
         const int64_t rn = r + step;
-        if (rn < total && t == 0) cs_row_copy(region, chi_row_src(p, rn, 0), &bars[w]);
+        if (rn < total && t == 0 && !dead && !chi_withheld(p, rn)) cs_row_copy(region, chi_row_src(p, rn, 0), &bars[w]);
     }
-    if (!ok && t == 0 && p.status != nullptr) atomicOr(p.status, 2);
+    if (dead && t == 0 && p.status != nullptr) atomicOr(p.status, 2);
 }
 
 static size_t chi_rows_smem_bytes() {
@@ -366,9 +378,9 @@ cudaError_t launch_chisq_pass2(const SegDev &seg, const UnitInfo *units, int uni
 bool chisq_rows_applies(int log2N) { return log2N - log2_n2(log2N) == 10; }
 
 cudaError_t launch_chisq_rows(const SegDev &seg, const float2 *exch, const UnitInfo *full, int unit0, int nb, int p,
-                              float *chisq, int *status, long long spin_limit, int n_sm, cudaStream_t st) {
+                              float *chisq, int *status, long long spin_limit, int stall, int n_sm, cudaStream_t st) {
     if (!chisq_rows_applies(seg.log2N) || nb < 1) return cudaErrorInvalidValue;
-    ChiRowsParams q{exch, full, chisq, unit0, nb, p, seg.log2N, seg.log2N2, status, spin_limit};
+    ChiRowsParams q{exch, full, chisq, unit0, nb, p, seg.log2N, seg.log2N2, status, spin_limit, stall};
     const int64_t rounds = ((int64_t)nb << seg.log2N2) / kChiWarps;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)n_sm, rounds));
     k_chisq_rows<<<grid, kChiWarps * 32, chi_rows_smem_bytes(), st>>>(q);

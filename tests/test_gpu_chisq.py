@@ -127,6 +127,27 @@ def test_chisq_two_batches_at_2p20(mf):
     _compare(mf, wl.m1, wl.m2, wl.segments[0], p=16)
 
 
+def test_chisq_rows_timeout_reports_and_recovers(mf):
+    """N = 2^19 rows kernel with one list entry's row copies withheld (test
+    hook): its waits run out, mf_bank_check reports MF_ETIMEOUT, nothing
+    faults, and the next call equals one made before."""
+    import torch
+    wl = workloads.small(seed=1919, N=1 << 19, fs=4096.0, n_templates=3, m_lo=1.2, m_hi=6.0)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    bank = mf.Bank(wl.m1, wl.m2)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    a = mf.chisq_series(bank, seg, [0, 1, 2], p=8)[0].cpu().numpy()
+    assert bank.check() == 0
+    bank.debug_stall(1, spin_limit=2000)
+    mf.chisq_series(bank, seg, [0, 1, 2], p=8)
+    assert bank.check(allow_timeout=True) == mf._native.MF_ETIMEOUT
+    bank.debug_stall(-1)
+    b = mf.chisq_series(bank, seg, [0, 1, 2], p=8)[0].cpu().numpy()
+    assert bank.check() == 0
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
 def test_chisq_noise_mean_and_invalid_index(mf):
     """Pure noise: the mean of chi^2 over all samples of 8 templates is near
     2p - 2; a template index outside the bank gives a zero row."""
