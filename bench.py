@@ -316,9 +316,12 @@ def run_uneven(args, mf, torch, dev):
         mf.filter_bank(bank, segs, wl.threshold, trig_cap=cap, out=out)
 
     res = {}
+    # units run widest band first by default; the *_bank_order runs keep bank order for comparison
     for name, env in (("persistent_graph", {"MFGB_SCHED": "persistent"}), ("batch_graph", {"MFGB_SCHED": "batch"}),
+                      ("persistent_graph_bank_order", {"MFGB_SCHED": "persistent", "MFGB_UNIT_ORDER": "bank"}),
+                      ("batch_graph_bank_order", {"MFGB_SCHED": "batch", "MFGB_UNIT_ORDER": "bank"}),
                       ("per_template_eager", {"MFGB_SCHED": "batch", "MFGB_BATCH": "1"})):
-        old = {k: os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH")}
+        old = {k: os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH", "MFGB_UNIT_ORDER")}
         for k in old:
             os.environ.pop(k, None)
         os.environ.update(env)
@@ -346,7 +349,7 @@ def run_uneven(args, mf, torch, dev):
             if v is not None:
                 os.environ[k] = v
     # the autotuner's choice (scheduler, exchange budget, kernel forms of the two passes) on this call
-    if not args.no_autotune and not any(os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH")):
+    if not args.no_autotune and not any(os.environ.get(k) for k in ("MFGB_SCHED", "MFGB_BATCH", "MFGB_UNIT_ORDER")):
         cache = os.path.join(tempfile.gettempdir(), "mfgb_autotune_uneven.json")
         mf.autotune(bank, segs, wl.threshold, repeats=1, cache_path=cache)
         with open(cache) as fh:
@@ -366,7 +369,8 @@ def run_uneven(args, mf, torch, dev):
             "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 2 injections per segment)",
             "config": {"workload": "4096 templates m1,m2 in [1,34] Msun with M <= 35, 8 segments "
                                    "N = 2^18,2^18,2^19,2^19,2^20,2^20,2^21,2^21 at 4096 Hz, thr 6",
-                       "l2": "flushed before every timed step (256 MiB write)"},
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "unit_order": "descending band width (f_isco) per segment; *_bank_order: bank order"},
             "equivalent_2p20_templates_per_s": eq / (best / 1e3), "schedules": res}
     print(json.dumps(line))
     return 0

@@ -160,7 +160,10 @@ int mf_segment_info(mf_segment seg, int64_t *N, double *fs);
  * sample with rho_j > threshold to trig (device array of trig_cap records),
  * sorted by (tmpl, seg, j).  *n_trig (device int64) receives the true count,
  * also when it exceeds trig_cap.  Neither h~(f) nor z(t) is stored.
- * segs: host array of n_seg >= 1 handles.  The call queues work on
+ * segs: host array of n_seg >= 1 handles.  Within a segment the templates
+ * are processed widest band first (descending f_isco, ties in bank order:
+ * the costliest units start first); outputs are in bank order all the same.
+ * The call queues work on
  * cuda_stream and returns; mf_bank_check() reports overflow and device-side
  * timeouts of the last call on this bank.
  * The first call for a given (segment length, bank size, trig_cap) allocates

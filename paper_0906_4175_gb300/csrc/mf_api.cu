@@ -160,6 +160,11 @@ struct mf_bank_s {
     mf_bank_params params{};
     double *d_tmpl = nullptr;
     std::vector<double> fisco;   // host copy of f_isco per template (profiling byte counts)
+    // unit order of every segment: descending cost.  A template's band runs
+    // from f_low to min(f_isco, fs/2), so descending f_isco (ties in bank
+    // order) puts the widest bands first for every segment.  pos is the inverse.
+    std::vector<int> order, pos;
+    int *d_order = nullptr;
     double B1 = 0.0, B5 = 0.0, fisco_min = 0.0;
     int device = 0;
     Workspace ws;
@@ -278,11 +283,21 @@ extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, con
     b->fisco_min = fmin;
     b->fisco.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) b->fisco[(size_t)i] = rec[(size_t)i * kTmplStride + TF_FISCO];
+    b->order.resize((size_t)n);
+    b->pos.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) b->order[(size_t)i] = (int)i;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int x, int y) { return b->fisco[(size_t)x] > b->fisco[(size_t)y]; });
+    for (int64_t i = 0; i < n; ++i) b->pos[(size_t)b->order[(size_t)i]] = (int)i;
     cudaGetDevice(&b->device);
     cudaError_t e = cudaMalloc(&b->d_tmpl, sizeof(double) * rec.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tmpl, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(b->d_tmpl);
+        cudaFree(b->d_order);
         delete b;
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "bank upload: %s",
                        cudaGetErrorString(e));
@@ -296,6 +311,7 @@ extern "C" int mf_bank_destroy(mf_bank b) {
     for (auto &r : b->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     b->ws.release();
     cudaFree(b->d_tmpl);
+    cudaFree(b->d_order);
     cudaFree(b->chi_status);
     if (b->ev_p1) cudaEventDestroy(b->ev_p1);
     if (b->ev_anc) cudaEventDestroy(b->ev_anc);
@@ -637,6 +653,12 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     MF_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st));
     MF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
     const int n_t = (int)b->n;
+    // descending-cost unit order (MFGB_UNIT_ORDER=bank keeps bank order); the
+    // stall hook names a template, the kernels see its unit position
+    const char *uo = getenv("MFGB_UNIT_ORDER");
+    const int *unit_order = (uo && !strcmp(uo, "bank")) ? nullptr : b->d_order;
+    const int stall_pos =
+        b->stall_unit < 0 ? -1 : (unit_order ? b->pos[(size_t)b->stall_unit] : (int)b->stall_unit);
     for (int s = 0; s < n_seg; ++s) {
         const SegDev sd = seg_dev(segs[s]);
         const int lgD = choose_log2D(b, segs[s]);
@@ -659,7 +681,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             }
         }
         int pi = prof_begin(b, MF_STAGE_SETUP, 48.0 * n_t, st);
-        MF_CUDA(launch_units(sd, b->d_tmpl, n_t, b->params.f_low, threshold, lgD, w.units, st));
+        MF_CUDA(launch_units(sd, b->d_tmpl, n_t, b->params.f_low, threshold, lgD, unit_order, w.units, st));
         prof_end(b, pi, st);
         count_launches(1);
         PersistParams P;
@@ -703,7 +725,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             P.kl = kl;
             P.peaks = peaks;
             P.spin_limit = b->spin_limit;
-            P.stall_unit = (int)b->stall_unit;
+            P.stall_unit = stall_pos;
             P.stats = nullptr;
             const bool want_stats = getenv("MFGB_SCHED_STATS") != nullptr && !capturing;
             if (want_stats) {
@@ -752,7 +774,11 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             const int64_t aoff = overlap ? (bi & 1) * slot_elems : 0;
             double by_band = 0.0, by_anc = 0.0;
             if (b->prof_on)
-                for (int t = u0; t < u0 + nb; ++t) { by_band += band_bytes[(size_t)t]; by_anc += anc_bytes[(size_t)t]; }
+                for (int u = u0; u < u0 + nb; ++u) {
+                    const size_t t = unit_order ? (size_t)b->order[(size_t)u] : (size_t)u;
+                    by_band += band_bytes[t];
+                    by_anc += anc_bytes[t];
+                }
             const double exch_bytes = 8.0 * (double)sd.N * nb;
             if (anchors && (!overlap || bi == 0)) {
                 pi = prof_begin(b, MF_STAGE_ANCHORS, by_anc, st);
@@ -782,7 +808,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             if (rows)
                 MF_CUDA(launch_pass2_rows(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                           std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, sm_count(),
-                                          b->params.fft_mode, (int)b->stall_unit, st));
+                                          b->params.fft_mode, stall_pos, st));
             else
                 MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                      std::max<int64_t>(trig_cap, 0), st));
@@ -873,7 +899,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     if (e == cudaSuccess) e = cudaMallocAsync(&anc4, sizeof(float) * man * batch, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * seg->N * batch * (rows ? p + 1 : 1), st);
     int launches = 0;
-    if (e == cudaSuccess) e = launch_units(sd, b->d_tmpl, n_t, b->params.f_low, 0.f, lgD, all, st);
+    if (e == cudaSuccess) e = launch_units(sd, b->d_tmpl, n_t, b->params.f_low, 0.f, lgD, nullptr, all, st);
     if (e == cudaSuccess) e = launch_chisq_units(sd, all, n_t, tmpl, (int)n, p, units, edges, st);
     launches += 2;
     const UnitInfo *full = units + (size_t)p * n;

@@ -20,10 +20,12 @@ namespace mf {
 // ---------------------------------------------------------------------------
 // per-unit set-up
 // ---------------------------------------------------------------------------
+// Unit i of a segment is template order[i] (bank order when order is NULL).
 __global__ void k_units(SegDev seg, const double *__restrict__ tmpl, int n_t, double f_low, float thr,
-                        int log2D, UnitInfo *__restrict__ units) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_t) return;
+                        int log2D, const int *__restrict__ order, UnitInfo *__restrict__ units) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_t) return;
+    const int t = order ? order[i] : i;
     const double *T = tmpl + (int64_t)t * kTmplStride;
     const double N = (double)seg.N, fs = seg.fs;
     const double fisco = T[TF_FISCO];
@@ -45,7 +47,7 @@ __global__ void k_units(SegDev seg, const double *__restrict__ tmpl, int n_t, do
     u.thr2 = (float)(th * th);
     u.z_scale = (float)(4.0 * seg.df * T[TF_AMP] / seg.consts->alpha);
     u.tmpl = t;
-    units[t] = u;
+    units[i] = u;
 }
 
 __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const UnitInfo *__restrict__ units,
@@ -70,8 +72,8 @@ __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const Uni
 // launches
 // ---------------------------------------------------------------------------
 cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double f_low, float thr, int log2D,
-                         UnitInfo *units, cudaStream_t st) {
-    k_units<<<(n_t + 255) / 256, 256, 0, st>>>(seg, tmpl, n_t, f_low, thr, log2D, units);
+                         const int *order, UnitInfo *units, cudaStream_t st) {
+    k_units<<<(n_t + 255) / 256, 256, 0, st>>>(seg, tmpl, n_t, f_low, thr, log2D, order, units);
     return cudaGetLastError();
 }
 

@@ -116,8 +116,9 @@ cudaError_t launch_inverse_real_fft(const float2 *Y, int64_t N, double scale, fl
                                     cudaStream_t st);
 
 // filter (mf_filter.cu)
+// units[i] <- template order[i] (order NULL: template i)
 cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double f_low, float thr,
-                         int log2D, UnitInfo *units, cudaStream_t st);
+                         int log2D, const int *order, UnitInfo *units, cudaStream_t st);
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0,
                            int n_units, int log2D, int max_anc, float4 *anchors, float *anchors4,
                            cudaStream_t st);

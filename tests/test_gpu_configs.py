@@ -163,6 +163,22 @@ def test_uneven_bank_pass1_kernels_agree(mf, uneven_data, monkeypatch):
     assert np.array_equal(tr_a.view(np.uint8), tr_b.view(np.uint8))
 
 
+@pytest.mark.parametrize("sched", ["batch", "persistent"])
+def test_uneven_bank_unit_order_agrees(mf, uneven_data, monkeypatch, sched):
+    """Units run in descending band width (widest first); bank order gives
+    bit-identical peaks and triggers under both schedulers, and the outputs
+    stay in bank order (template t's peak in row t, whatever its position)."""
+    wl, _, segs = uneven_data
+    monkeypatch.setenv("MFGB_SCHED", sched)
+    monkeypatch.setenv("MFGB_UNIT_ORDER", "bank")
+    _, pk_a, tr_a, n_a = _uneven_call(mf, wl, segs)
+    monkeypatch.delenv("MFGB_UNIT_ORDER")
+    _, pk_b, tr_b, n_b = _uneven_call(mf, wl, segs)
+    assert n_a == n_b
+    assert np.array_equal(pk_a.view(np.uint8), pk_b.view(np.uint8))
+    assert np.array_equal(tr_a.view(np.uint8), tr_b.view(np.uint8))
+
+
 def _mode_errors(mf, wl, sample, s32, ref, phase_mode):
     """Full rho series of the sampled templates in one phase mode, compared
     with the oracle: (max err, median err, peak indices agree, trigger sets
