@@ -252,6 +252,38 @@ def test_z_equals_time_domain_correlation(oracle_lib):
     assert np.max(np.abs(out["rho"] - np.abs(out["z"]) / out["sigma"])) < 1e-13 * np.max(out["rho"])
 
 
+def test_quadrature_templates_orthogonal(oracle_lib):
+    """h~_c = -i h~_s (Sec. 1.1): filtering the data r_c whose spectrum is
+    the template itself gives z_0 = sigma^2 (Eq. 4), real and positive; the
+    quadrature data r_s (spectrum i h~_c, orthogonal to r_c under the
+    S_n-weighted inner product) gives z = -i z_c at every lag, so x and y swap
+    roles and rho is the same series.  A conjugate on the wrong factor gives
+    +i z_c; a filter that kept only x = Re z loses half of rho."""
+    N, fs, f_low = 1 << 13, 2048.0, 40.0
+    df = fs / N
+    m1, m2 = 1.6, 2.3
+    S = oracle_lib.psd_bins(N, fs)
+    h, (lo, hi) = oracle_lib.htilde(m1, m2, N, fs, f_low)
+    r_c = np.fft.irfft(h, n=N) * N * df
+    r_s = np.fft.irfft(1j * h, n=N) * N * df
+    # the two real signals are orthogonal in the whitened inner product
+    # 4 Re sum a~ conj(b~)/S df, computed from their own DFTs
+    a = np.fft.rfft(r_c) / fs
+    b = np.fft.rfft(r_s) / fs
+    ip = lambda u, v: 4 * df * np.real(np.sum(u[lo:hi] * np.conj(v[lo:hi]) / S[lo:hi]))
+    assert abs(ip(a, b)) < 1e-12 * ip(a, a)
+    assert abs(ip(b, b) / ip(a, a) - 1) < 1e-12
+    zc = oracle_lib.filter_template(m1, m2, oracle_lib.data_spectrum(r_c, fs), S, N, fs, f_low)
+    zs = oracle_lib.filter_template(m1, m2, oracle_lib.data_spectrum(r_s, fs), S, N, fs, f_low)
+    sig2 = zc["sigma"] ** 2
+    assert abs(zc["z"][0].real / sig2 - 1) < 1e-12
+    assert abs(zc["z"][0].imag) < 1e-12 * sig2
+    assert int(np.argmax(zc["rho"])) == 0 and abs(zc["rho"][0] - zc["sigma"]) < 1e-12 * zc["sigma"]
+    scale = np.max(np.abs(zc["z"]))
+    assert np.max(np.abs(zs["z"] + 1j * zc["z"])) < 1e-12 * scale
+    assert np.max(np.abs(zs["rho"] - zc["rho"])) < 1e-12 * zc["sigma"]
+
+
 def test_data_spectrum_is_scaled_dft(oracle_lib):
     N, fs = 512, 512.0
     s = np.random.default_rng(5).standard_normal(N)
