@@ -269,6 +269,24 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
 int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold, int repeats,
                 const char *cache_path, void *cuda_stream);
 
+/* Schedule overrides, read from the environment at every mf_filter_bank call
+ * (for comparisons and tests; none changes a result, every combination is
+ * bit-identical):
+ *   MFGB_SCHED=batch|persistent  per-batch launches or the persistent
+ *                                scheduler, over the bank's (autotuned) choice
+ *   MFGB_BATCH=n                 templates per batch of the per-batch launches
+ *   MFGB_SPLIT=x                 fraction of the SMs the persistent scheduler
+ *                                starts on queue 1 (anchors + pass 1)
+ *   MFGB_P1PF=0                  pass 1 one CTA per column tile instead of the
+ *                                persistent kernel with staged inputs
+ *   MFGB_P2ROWS=0                pass 2 one CTA per row tile instead of
+ *                                warp-owned rows (FP32 FFT form only)
+ *   MFGB_UNIT_ORDER=bank         templates in bank order instead of widest
+ *                                band first
+ *   MFGB_SCHED_STATS=1           the persistent scheduler prints its queue
+ *                                wait counts to stderr (synchronises; not
+ *                                inside a stream capture) */
+
 /* mf_synth_segment -- seeded synthetic data: stationary Gaussian noise
  * coloured by S_n (Eq. 2, or psd) plus frequency-domain injections, the
  * stand-in for the paper's coloured-noise test data (Sec. 3).
