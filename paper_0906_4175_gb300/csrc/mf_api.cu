@@ -1258,7 +1258,7 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
     double *partial = nullptr;
     cudaError_t e = cudaMallocAsync(&partial, refine_scratch_bytes(n, bpr), st);
     if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, bpr, st);
-    if (e == cudaSuccess) count_launches(3)   /* row set-up, partial sums, totals */;
+    if (e == cudaSuccess) count_launches(3);   // row set-up, partial sums, totals
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers: %s",
@@ -1294,7 +1294,7 @@ extern "C" int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const
     if (e == cudaSuccess)
         e = launch_refine_multi(sd.data(), n_seg, row_seg, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial,
                                 bpr, st);
-    if (e == cudaSuccess) count_launches(3)   /* row set-up, partial sums, totals */;
+    if (e == cudaSuccess) count_launches(3);   // row set-up, partial sums, totals
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers_multi: %s",
@@ -1358,6 +1358,6 @@ extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *p
     const SegDev sd = seg_dev(seg);
     MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, kRefineStaticBpr,
                           (cudaStream_t)cuda_stream));
-    count_launches(3)   /* row set-up, partial sums, totals */;
+    count_launches(3);   // row set-up, partial sums, totals
     return MF_OK;
 }
