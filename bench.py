@@ -1085,29 +1085,59 @@ def main():
     peaks_h = torch.empty((wl.n_templates, 4), dtype=torch.float32, pin_memory=True)
     ntr_h = torch.empty(1, dtype=torch.int64, pin_memory=True)
     trig_h = torch.empty((cap, 6), dtype=torch.float32, pin_memory=True)
-    d2h = []
-    e2e_ms = []
-    for k in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        seg.refresh(s_host.numpy())     # H2D of the step's samples (pinned) + conditioning
-        mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
-        peaks_h.copy_(outb[0], non_blocking=True)
-        ntr_h.copy_(outb[2], non_blocking=True)
-        torch.cuda.synchronize()
-        n = min(int(ntr_h.item()), cap)
-        trig_h[:n].copy_(outb[1][:n], non_blocking=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if k >= 2:
-            e2e_ms.append(dt * 1e3)
-            d2h.append(peaks_h.numel() * 4 + 8 + n * 24)
-    e2e_tot = sum(e2e_ms) if e2e_ms else float("nan")
-    if dist:
-        e2e_tot = max_over_ranks(e2e_tot, dist, dev)
-    e2e = {"value": whole_job_rate(world, wl.n_templates * len(e2e_ms), e2e_tot) if e2e_ms else None, "unit": UNIT,
-           "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)) if d2h else 0,
-           "includes": "pinned host s -> mf_segment_refresh (H2D inside), mf_filter_bank, D2H peaks + n_trig + triggers"}
+    # Two forms of the same user loop.  eager: mf_segment_refresh from the
+    # pinned host samples (its H2D copy inside) and an eager mf_filter_bank.
+    # graph: the H2D copy of the samples into a device staging buffer, then one
+    # CUDA-graph replay of mf_segment_refresh (device samples) + mf_filter_bank,
+    # the pattern the boundary documents for a fixed-shape search.  Both read
+    # back peaks, n_trig and the triggers every step.
+    s_stage = torch.empty(spec.N, dtype=torch.float32, device=dev)
+    g_e2e = None
+    if graph is not None:
+        s_stage.copy_(s_dev)
+        g_e2e = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_e2e):
+            seg.refresh(s_stage)
+            mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
+
+    def e2e_run(form):
+        d2h, ms = [], []
+        for k in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if form == "graph":
+                s_stage.copy_(s_host, non_blocking=True)   # H2D of the step's samples (pinned)
+                g_e2e.replay()
+            else:
+                seg.refresh(s_host.numpy())     # H2D of the step's samples (pinned) + conditioning
+                mf.filter_bank(bank, [seg], wl.threshold, trig_cap=cap, out=outb)
+            peaks_h.copy_(outb[0], non_blocking=True)
+            ntr_h.copy_(outb[2], non_blocking=True)
+            torch.cuda.synchronize()
+            n = min(int(ntr_h.item()), cap)
+            trig_h[:n].copy_(outb[1][:n], non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if k >= 2:
+                ms.append(dt * 1e3)
+                d2h.append(peaks_h.numel() * 4 + 8 + n * 24)
+        tot = sum(ms) if ms else float("nan")
+        if dist:
+            tot = max_over_ranks(tot, dist, dev)
+        rate = whole_job_rate(world, wl.n_templates * len(ms), tot) if ms else None
+        return rate, (int(statistics.mean(d2h)) if d2h else 0)
+
+    e2e_eager, d2h_bytes = e2e_run("eager")
+    e2e_graph = None
+    if g_e2e is not None:
+        e2e_graph, d2h_bytes = e2e_run("graph")
+        assert bank.check() == 0
+    e2e = {"value": e2e_graph if e2e_graph is not None else e2e_eager, "unit": UNIT,
+           "h2d_bytes_per_step": spec.N * 4, "d2h_bytes_per_step": d2h_bytes,
+           "form": "graph" if e2e_graph is not None else "eager",
+           "includes": ("H2D of the pinned host samples, mf_segment_refresh + mf_filter_bank (one CUDA-graph replay "
+                        "in the graph form, eager calls in the eager form), D2H of peaks + n_trig + triggers"),
+           "eager_value": e2e_eager}
 
     cpu = None
     acc = None
