@@ -217,6 +217,45 @@ def test_multi_segment_call_equals_separate_calls(mf):
         assert np.array_equal(sub[["tmpl", "j", "rho", "z_re", "z_im"]], t1[["tmpl", "j", "rho", "z_re", "z_im"]])
 
 
+@pytest.mark.parametrize("f_low", [30.0, 60.0])
+def test_mixed_rates_and_f_low_one_call(mf, f_low):
+    """Segments of three sample rates (1024, 2048, 4096 Hz) and lengths in ONE
+    call, with a lower cut-off other than 40 Hz (the band rule of Sec. 1.1:
+    k_lo = ceil(f_low N / fs), f_cut = min(f_isco, fs/2), so the heavier
+    templates end below Nyquist at 4096 Hz and the lighter ones are cut at
+    Nyquist at 1024 Hz): every rho_j and z_j of every (template, segment)
+    against the oracle run at that f_low.  (Below about 28 Hz the Eq. 2 noise
+    between f_low and the seismic wall dominates the FP32 samples, and the
+    FP32 transforms' round-off, relative to that amplitude, reaches the 1e-4
+    bound: 1.2e-4 was seen at f_low = 25 Hz, fs = 1024 Hz.)"""
+    import torch
+    m1 = np.array([1.25, 1.6, 2.9, 4.8, 9.0, 1.4])
+    m2 = np.array([1.2, 1.45, 2.1, 3.5, 7.5, 1.4])
+    specs = [workloads.small(seed=40 + i, N=N, fs=fs, n_templates=1, m_lo=1.2, m_hi=3.0).segments[0]
+             for i, (N, fs) in enumerate(((1 << 13, 1024.0), (1 << 15, 2048.0), (1 << 17, 4096.0)))]
+    data = [oracle_segment(sp, f_low) for sp in specs]
+    segs = [mf.Segment(torch.from_numpy(s32).cuda(), sp.fs) for (s32, _), sp in zip(data, specs)]
+    bank = mf.Bank(m1, m2, f_low=f_low)
+    n_t, n_seg = len(m1), len(segs)
+    total = n_t * sum(sp.N for sp in specs)
+    p, t, n = mf.filter_bank(bank, segs, 0.0, trig_cap=total)
+    assert bank.check() == 0
+    tr = mf.triggers_to_numpy(t, n)
+    assert tr.size == total
+    pk = mf.peaks_to_numpy(p).reshape(n_t, n_seg)
+    for si, (sp, (_, s64)) in enumerate(zip(specs, data)):
+        ref = oracle_rho_series(m1, m2, s64, sp.fs, f_low)
+        for ti, r in enumerate(ref):
+            sel = tr[(tr["tmpl"] == ti) & (tr["seg"] == si)]
+            assert sel.size == sp.N and np.array_equal(sel["j"], np.arange(sp.N))
+            e = rho_err(sel["rho"].astype(np.float64), r["rho"])
+            assert e.max() <= RHO_TOL, (si, ti, float(e.max()))
+            ez = np.abs(sel["z_re"] + 1j * sel["z_im"] - r["z"]) / r["sigma"]
+            assert ez.max() <= RHO_TOL, (si, ti, float(ez.max()))
+            jr = int(np.argmax(r["rho"]))
+            assert peak_index_agrees(r["rho"], int(pk[ti, si]["j"]), jr), (si, ti)
+
+
 def test_ragged_batches(mf, monkeypatch):
     """A bank size that is not a multiple of the templates in flight."""
     import torch
