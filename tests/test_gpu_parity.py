@@ -256,6 +256,31 @@ def test_mixed_rates_and_f_low_one_call(mf, f_low):
             assert peak_index_agrees(r["rho"], int(pk[ti, si]["j"]), jr), (si, ti)
 
 
+@pytest.mark.parametrize("lg", [12, 20])
+def test_degenerate_bands(mf, lg):
+    """Templates whose ISCO cut leaves 1, 2 and 3 bins above f_low (mid-bin
+    f_isco, so the integer band is not a rounding decision), beside an
+    ordinary one: the full rho and z series against the oracle (a 1-bin band
+    gives a rho series that is flat up to rounding, so the peak index is a
+    tie).  At 2^20 the staged pass 1 and the rows kernel run them.  A
+    template cut below f_low is refused."""
+    import torch
+    N, fs = 1 << lg, 4096.0
+    c = oracle.f_isco(1.0, 1.0) * 2.0           # f_isco(m, m) = c / (2 m)
+    ms = [c / (2.0 * (40.0 + (nb - 0.5) * fs / N)) for nb in (1, 2, 3)]
+    for nb, m in zip((1, 2, 3), ms):
+        lo, hi = oracle.band(N, fs, 40.0, min(oracle.f_isco(m, m), fs / 2))
+        assert hi - lo == nb
+    m1 = np.array(ms + [1.4])
+    spec = workloads.small(seed=70 + lg, N=N, fs=fs).segments[0]
+    _full_compare(mf, m1, m1.copy(), spec)
+    bank = mf.Bank([c / (2.0 * 39.0)], [c / (2.0 * 39.0)])
+    seg = mf.Segment(torch.zeros(N, device="cuda"), fs)
+    with pytest.raises(mf.MFError) as ei:
+        mf.filter_bank(bank, [seg], 6.0)
+    assert "MF_EINVAL" in str(ei.value)
+
+
 def test_ragged_batches(mf, monkeypatch):
     """A bank size that is not a multiple of the templates in flight."""
     import torch
