@@ -281,6 +281,30 @@ def test_degenerate_bands(mf, lg):
     assert "MF_EINVAL" in str(ei.value)
 
 
+@pytest.mark.parametrize("snr", [200.0, 2000.0])
+def test_loud_injection_envelope(mf, snr):
+    """FP32 round-off in the transforms scales with the loudest signal of the
+    segment, so the error at noise-level samples grows linearly with the
+    injection's SNR: within RHO_TOL up to SNR ~ 1000 (the paper's workloads
+    use SNR 8-20), RHO_TOL * SNR / 1000 beyond.  One 1.4+1.4 injection, N = 2^16,
+    the full series of the matched and a mismatched template."""
+    import torch
+    N, fs = 1 << 16, 4096.0
+    inj = np.zeros(1, dtype=oracle.INJ_DTYPE)
+    inj[0] = (1.4, 1.4, snr, 12345, 0.7)
+    spec = workloads.SegmentSpec(N, fs, 91, inj)
+    s32, s64 = oracle_segment(spec)
+    m1, m2 = np.array([1.4, 1.6]), np.array([1.4, 1.3])
+    bank = mf.Bank(m1, m2)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), fs)
+    rho_g, _, pk = gpu_rho_series(mf, bank, seg, 2, N)
+    ref = oracle_rho_series(m1, m2, s64, fs)
+    bound = RHO_TOL * max(1.0, snr / 1000.0)
+    for t in range(2):
+        assert rho_err(rho_g[t], ref[t]["rho"]).max() <= bound, t
+    assert abs(ref[0]["rho"].max() / snr - 1) < 0.05 and int(pk["j"][0]) == (N - 12345) % N
+
+
 def test_ragged_batches(mf, monkeypatch):
     """A bank size that is not a multiple of the templates in flight."""
     import torch
