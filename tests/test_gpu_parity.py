@@ -340,33 +340,34 @@ def test_psd_table_and_scale(mf):
     assert np.max(np.abs(ph["rho"] - base["rho"]) / base["rho"]) < 1e-4
 
 
-def test_refine_matches_oracle(mf):
+@pytest.mark.parametrize("lg,fs,f_low", [(16, 4096.0, 40.0), (15, 2048.0, 30.0)])
+def test_refine_matches_oracle(mf, lg, fs, f_low):
     """mf_refine_triggers: rho^2 and its gradient against the oracle's direct
-    sum and analytic gradient."""
+    sum and analytic gradient (two sample rates and lower cut-offs)."""
     import torch
-    N, fs = 1 << 16, 4096.0
+    N = 1 << lg
     spec = workloads.SegmentSpec(N, fs, 123)
     inj = np.zeros(1, dtype=oracle.INJ_DTYPE)
     inj[0] = (1.7, 1.3, 12.0, 5000, 0.4)
     spec.injections = inj
-    s32, s64 = oracle_segment(spec)
+    s32, s64 = oracle_segment(spec, f_low)
     seg = mf.Segment(torch.from_numpy(s32).cuda(), fs)
     t0 = ((N - 5000) % N) / fs
     theta = np.array([[1.7, 1.3, t0], [1.72, 1.31, t0 + 0.3 / fs], [1.65, 1.36, t0 - 1.7 / fs],
                       [2.5, 1.2, 1.0]])
-    lo_hi = [oracle.band(N, fs, 40.0, oracle.f_isco(a, b)) for a, b, _ in theta]
-    ref_obj, ref_grad = oracle.refine(theta, s64, fs, 40.0, bands=np.array(lo_hi))
+    lo_hi = [oracle.band(N, fs, f_low, min(oracle.f_isco(a, b), fs / 2)) for a, b, _ in theta]
+    ref_obj, ref_grad = oracle.refine(theta, s64, fs, f_low, bands=np.array(lo_hi))
     th = torch.tensor(theta, dtype=torch.float64, device="cuda")
     scale = np.abs(ref_grad).max(axis=0)
     for mode in (mf.MF_PHASE_FP64, mf.MF_PHASE_ANCHOR):     # per-bin FP64 phase, then the default anchors
-        obj, grad = mf.refine(seg, th, phase_mode=mode)
+        obj, grad = mf.refine(seg, th, f_low=f_low, phase_mode=mode)
         obj = obj.cpu().numpy()
         grad = grad.cpu().numpy()
         assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < 2e-4), (mode, obj, ref_obj)
         assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * scale), (mode, grad, ref_grad)
     # explicit band gives the same as the default band at the same masses
     band = torch.tensor(np.array(lo_hi), dtype=torch.int64, device="cuda")
-    obj2, grad2 = mf.refine(seg, th, band=band)
+    obj2, grad2 = mf.refine(seg, th, band=band, f_low=f_low)
     assert np.array_equal(obj2.cpu().numpy(), obj)
 
 
