@@ -305,6 +305,41 @@ def test_loud_injection_envelope(mf, snr):
     assert abs(ref[0]["rho"].max() / snr - 1) < 0.05 and int(pk["j"][0]) == (N - 12345) % N
 
 
+def test_stage_profile_counts(mf, monkeypatch):
+    """mf_bank_profile: per-stage launches match the batches (two of 24 and
+    one of 16 templates), the algorithmic bytes are exact (pass 2 reads
+    8 N per template; pass 1 writes 8 N and reads the 8 K_t-byte W band,
+    K_t from the oracle's band rule, plus the anchor records the anchor stage
+    reports), a read clears the counters, and results with profiling on
+    equal those without."""
+    import torch
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    monkeypatch.setenv("MFGB_BATCH", "24")
+    wl = workloads.small(seed=9, N=1 << 17, fs=4096.0, n_templates=64)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    ref = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 16)[0])
+    bank.profile(True)
+    got = mf.peaks_to_numpy(mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 16)[0])
+    pr = bank.profile_read()
+    bank.profile(False)
+    assert bank.check() == 0
+    assert np.array_equal(ref.view(np.uint8), got.view(np.uint8))
+    N, n_t, n_b = spec.N, 64, 3
+    assert pr["setup"][2] == 1 and pr["anchors"][2] == n_b and pr["pass1"][2] == n_b and pr["pass2"][2] == n_b
+    assert all(pr[k][0] > 0 for k in ("setup", "anchors", "pass1", "pass2", "final"))
+    assert pr["fused"][2] == 0
+    assert pr["pass2"][1] == 8.0 * N * n_t
+    band = sum(8.0 * (hi - lo) for lo, hi in (oracle.band(N, spec.fs, 40.0, min(oracle.f_isco(a, b), spec.fs / 2))
+                                               for a, b in zip(wl.m1, wl.m2)))
+    assert pr["pass1"][1] - pr["anchors"][1] == band + 8.0 * N * n_t
+    assert pr["anchors"][1] > 0
+    again = bank.profile_read()
+    assert all(v == (0.0, 0.0, 0) for v in again.values())
+
+
 def test_ragged_batches(mf, monkeypatch):
     """A bank size that is not a multiple of the templates in flight."""
     import torch
