@@ -1252,13 +1252,16 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
     if (rc) return rc;
     int r0 = ensure_device_init();
     if (r0) return r0;
+    int cur = 0;
+    MF_CUDA(cudaGetDevice(&cur));
+    if (seg->device != cur) return set_err(MF_EINVAL, "segment lives on device %d, current device is %d", seg->device, cur);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const SegDev sd = seg_dev(seg);
     const int bpr = refine_blocks_for(n, sm_count());
     double *partial = nullptr;
     cudaError_t e = cudaMallocAsync(&partial, refine_scratch_bytes(n, bpr), st);
     if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, bpr, st);
-    if (e == cudaSuccess) count_launches(3);   // row set-up, partial sums, totals
+    if (e == cudaSuccess) count_launches(refine_launches(n));
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers: %s",
@@ -1294,7 +1297,7 @@ extern "C" int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const
     if (e == cudaSuccess)
         e = launch_refine_multi(sd.data(), n_seg, row_seg, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial,
                                 bpr, st);
-    if (e == cudaSuccess) count_launches(3);   // row set-up, partial sums, totals
+    if (e == cudaSuccess) count_launches(refine_launches(n));
     if (partial) cudaFreeAsync(partial, st);
     if (e != cudaSuccess)
         return set_err(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "refine_triggers_multi: %s",
@@ -1350,6 +1353,9 @@ extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *p
     if (rc) return rc;
     rc = ensure_device_init();
     if (rc) return rc;
+    int cur = 0;
+    MF_CUDA(cudaGetDevice(&cur));
+    if (seg->device != cur) return set_err(MF_EINVAL, "segment lives on device %d, current device is %d", seg->device, cur);
     double *scratch = nullptr;
     rc = refine_scratch_ptr(&scratch);
     if (rc) return rc;
@@ -1358,6 +1364,6 @@ extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *p
     const SegDev sd = seg_dev(seg);
     MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, kRefineStaticBpr,
                           (cudaStream_t)cuda_stream));
-    count_launches(3);   // row set-up, partial sums, totals
+    count_launches(refine_launches(n));
     return MF_OK;
 }

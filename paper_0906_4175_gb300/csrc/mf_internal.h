@@ -196,6 +196,9 @@ cudaError_t launch_refine_multi(const SegDev *segs, int n_seg, const int32_t *ro
                                 double *grad, double *partial, int bpr, cudaStream_t st);
 int refine_blocks_per_row();
 int refine_blocks_for(int64_t n, int n_sm);   // blocks per row that fill the GPU
+// kernels queued by one refinement call of n rows: the row set-up, the
+// partial sums in chunks of at most 65535 rows (grid y limit), the totals
+inline int refine_launches(int64_t n) { return 2 + (int)((n + 65534) / 65535); }
 
 // persistent scheduler (mf_persist.cu): segments with N >= 2^13
 cudaError_t launch_persistent(const PersistParams &P, int grid, cudaStream_t st);

@@ -25,6 +25,7 @@ constexpr int kRefBlocksPerRow = 16;          // the allocation-free entry point
 constexpr int kRefMinBlocksPerRow = 2;
 constexpr int kRefMaxBlocksPerRow = 256;
 constexpr int kRefAnchorsPerChunk = kRefThreads;
+constexpr int64_t kRefMaxGridRows = 65535;    // rows per launch of the partial-sum kernel (grid y)
 int refine_blocks_per_row() { return kRefBlocksPerRow; }
 
 // The segments of one call, passed by value as a kernel parameter: row i
@@ -76,8 +77,12 @@ __device__ void refine_row_setup(const SegDev &seg, double f_low, int anchored, 
         lo = (int64_t)ceil(f_low * N / fs);
         hi = (int64_t)floor(fc * N / fs) + 1;
     }
+    // clamp into [1, N/2]: P has N/2 + 1 entries, so both edges stay readable
+    // whatever band the caller passes (an edge beyond N/2 gives an empty band)
+    const int64_t kmax = seg.N / 2;
     if (lo < 1) lo = 1;
-    if (hi > seg.N / 2) hi = seg.N / 2;
+    if (lo > kmax) lo = kmax;
+    if (hi > kmax) hi = kmax;
     if (hi < lo) hi = lo;
     r.k_lo = lo;
     r.k_hi = hi;
@@ -174,14 +179,14 @@ __global__ void k_refine_setup(const __grid_constant__ SegTable<NS> tab, const i
 template <int NS>
 __global__ void __launch_bounds__(kRefThreads)
     k_refine_partial(const __grid_constant__ SegTable<NS> tab, const int32_t *__restrict__ row_seg,
-                     const RefRow *__restrict__ rows, double *__restrict__ partial) {
+                     const RefRow *__restrict__ rows, double *__restrict__ partial, int64_t i0) {
     __shared__ RefRow row;
     __shared__ double red[8][kRefThreads / 32];
     __shared__ float4 sanc[kRefAnchorsPerChunk];
     __shared__ float sanc4[kRefAnchorsPerChunk];
     __shared__ float4 sg[kRefAnchorsPerChunk];    // g1 Taylor (3), g2 value
     __shared__ float2 sg2[kRefAnchorsPerChunk];   // g2 first and second k-derivative terms
-    const int64_t i = blockIdx.y;
+    const int64_t i = i0 + blockIdx.y;   // rows go in chunks of at most 65535 (grid y limit)
     const int si = row_segment(tab, row_seg, i);
     if (si < 0) {   // invalid segment index: an empty sum (the final kernel reports NaN)
         if (threadIdx.x < 8) partial[(i * gridDim.x + blockIdx.x) * 8 + threadIdx.x] = 0.0;
@@ -308,9 +313,13 @@ static cudaError_t launch_refine_table(const SegTable<NS> &tab, const int32_t *r
                                                                      rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_refine_partial<NS><<<dim3((unsigned)bpr, (unsigned)n), kRefThreads, 0, st>>>(tab, row_seg, rows, partial);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    for (int64_t i0 = 0; i0 < n; i0 += kRefMaxGridRows) {
+        const int64_t rows_here = n - i0 < kRefMaxGridRows ? n - i0 : kRefMaxGridRows;
+        k_refine_partial<NS><<<dim3((unsigned)bpr, (unsigned)rows_here), kRefThreads, 0, st>>>(tab, row_seg, rows,
+                                                                                              partial, i0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_refine_final<NS><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, row_seg, rows, partial, bpr, n, obj, grad);
     return cudaGetLastError();
 }

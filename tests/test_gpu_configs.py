@@ -345,3 +345,37 @@ def test_refine_multi_segment_rows(mf):
     ob, gb = mf.refine(segs, theta, row_seg=bad)
     assert torch.isnan(ob[0]) and torch.all(torch.isnan(gb[0]))
     assert torch.equal(ob[1:], obj[1:])
+
+
+def test_refine_band_edges_outside_the_spectrum(mf):
+    """A caller band whose edges lie beyond N/2 (or below 1) is clamped into
+    [1, N/2] before the FP64 prefix P is read: a band starting beyond N/2 is
+    empty (rho^2 = 0, zero gradient), one ending beyond N/2 equals the band
+    ending at N/2, in every refinement entry point."""
+    import ctypes
+    import torch
+    N, fs = 1 << 13, 4096.0
+    s32, _ = oracle_segment(workloads.SegmentSpec(N, fs, 17))
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), fs)
+    theta = torch.tensor([[1.5, 1.4, 0.3]] * 4, dtype=torch.float64, device="cuda")
+    band = torch.tensor([[N // 2 + 5, N // 2 + 9], [N, 2 * N], [400, N // 2 + 100], [-50, 3000]],
+                        dtype=torch.int64, device="cuda")
+    clamped = torch.tensor([[N // 2, N // 2], [N // 2, N // 2], [400, N // 2], [1, 3000]],
+                           dtype=torch.int64, device="cuda")
+    obj, grad = mf.refine(seg, theta, band=band)
+    ref, rgrad = mf.refine(seg, theta, band=clamped)
+    assert torch.equal(obj, ref) and torch.equal(grad, rgrad)
+    assert float(obj[0]) == 0.0 and float(obj[1]) == 0.0 and torch.all(grad[:2] == 0)
+    assert float(obj[2]) > 0.0 and float(obj[3]) > 0.0
+    row_seg = torch.zeros(4, dtype=torch.int32, device="cuda")
+    om, gm = mf.refine([seg], theta, band=band, row_seg=row_seg)
+    assert torch.equal(om[:2], obj[:2]) and torch.allclose(om, obj, rtol=2e-5, atol=1e-6)
+    L = mf._native.lib()
+    os_ = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    gs = torch.full((4, 3), float("nan"), dtype=torch.float64, device="cuda")
+    rc = L.mf_refine_triggers_static(seg.handle, None, ctypes.c_void_p(theta.data_ptr()), 4,
+                                     ctypes.c_void_p(band.data_ptr()), ctypes.c_void_p(os_.data_ptr()),
+                                     ctypes.c_void_p(gs.data_ptr()), None)
+    assert rc == 0, L.mf_last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(os_[:2], obj[:2]) and torch.allclose(os_, obj, rtol=2e-5, atol=1e-6)

@@ -201,6 +201,62 @@ def test_htilde_amplitude_and_phase(oracle_lib):
     assert abs(amp[0] - Mc ** (5.0 / 6.0)) < 1e-12
 
 
+def _quadrupole_chirp_spectrum(m1, m2, fs, Nfft, f_start, f_rise, f_fall, f_end):
+    """Numerical Fourier transform of a Newtonian (quadrupole) inspiral in the
+    time domain, built from the Peters-Mathews relations and not from any
+    frequency-domain template formula: with tau = t_c - t and M_c in seconds,
+      f(tau)   = (1/pi) (5 / (256 tau))^(3/8) M_c^(-5/8),
+      Phi(tau) = -2 (tau / (5 M_c))^(5/8),
+      h(t)     = M_c^(5/3) (pi f)^(2/3) cos Phi,
+    the quadrupole amplitude up to a distance factor.  Cosine tapers in time
+    switch the signal on between f_start and f_rise and off between f_fall and
+    f_end.  Returns dt * rfft(h) on k = 0..Nfft/2."""
+    M = m1 + m2
+    mc = (m1 * m2 / M ** 2) ** 0.6 * M * _msun_s()
+
+    def tau_of(f):
+        return (5.0 / 256.0) * mc ** (-5.0 / 3.0) * (np.pi * f) ** (-8.0 / 3.0)
+
+    dt = 1.0 / fs
+    t0, t1, t2, t3 = tau_of(f_start), tau_of(f_rise), tau_of(f_fall), tau_of(f_end)
+    assert t0 - t3 < Nfft * dt, "the chirp must fit the transform length"
+    tau = t0 - np.arange(int((t0 - t3) / dt)) * dt
+    f = (5.0 / (256.0 * tau)) ** 0.375 * mc ** (-0.625) / np.pi
+    phi = -2.0 * (tau / (5.0 * mc)) ** 0.625
+    h = mc ** (5.0 / 3.0) * (np.pi * f) ** (2.0 / 3.0) * np.cos(phi)
+    w = np.ones_like(tau)
+    on = tau > t1
+    w[on] = 0.5 * (1.0 - np.cos(np.pi * (t0 - tau[on]) / (t0 - t1)))
+    off = tau < t2
+    w[off] = 0.5 * (1.0 + np.cos(np.pi * (t2 - tau[off]) / (t2 - t3)))
+    return np.fft.rfft(h * w, Nfft) * dt
+
+
+def _msun_s():
+    return 4.925490947e-6   # G Msun / c^3 in seconds (IAU nominal)
+
+
+def test_htilde_amplitude_is_stationary_phase_of_quadrupole_chirp(oracle_lib):
+    """The Newtonian amplitude of the Sec. 1.1 templates, pinned without the
+    oracle's formula: the FFT of a time-domain quadrupole chirp (amplitude
+    M_c^(5/3) f^(2/3), Newtonian frequency sweep) divided by |h~| of the
+    oracle must be one and the same constant at every in-band frequency and
+    for every mass pair.  Stationary phase gives |h~(f)| = (A/2) fdot^(-1/2)
+    with fdot = (96/5) pi^(8/3) M_c^(5/3) f^(11/3), so the constant is
+    sqrt(5/384) pi^(-2/3) (G Msun/c^3)^(5/6) for the oracle's A = M_c^(5/6)
+    in solar masses.  A wrong power of f or of M_c in h~ changes the ratio
+    with frequency or between the two binaries (by 47 % for M_c^(5/3))."""
+    fs, Nfft = 2048.0, 1 << 18
+    f = np.arange(Nfft // 2 + 1) * fs / Nfft
+    mid = (f >= 50.0) & (f <= 200.0)   # well inside the tapers; SPA corrections < 0.1 % here
+    const = math.sqrt(5.0 / 384.0) * math.pi ** (-2.0 / 3.0) * _msun_s() ** (5.0 / 6.0)
+    for m1, m2 in [(1.4, 1.4), (2.5, 2.0), (3.0, 1.2)]:
+        H = _quadrupole_chirp_spectrum(m1, m2, fs, Nfft, 25.0, 35.0, 300.0, 400.0)
+        h, _ = oracle_lib.htilde(m1, m2, Nfft, fs, 20.0)
+        ratio = np.abs(H[mid]) / np.abs(h[mid])
+        assert np.max(np.abs(ratio / const - 1.0)) < 3e-3, (m1, m2, ratio.min() / const, ratio.max() / const)
+
+
 def test_mirror_symmetry(oracle_lib):
     """(m1, m2) and (m2, m1) are the same binary: identical template."""
     h1, b1 = oracle_lib.htilde(1.3, 2.7, 4096, 4096.0, 40.0)
@@ -595,3 +651,44 @@ def test_cluster_empty_and_single(oracle_lib):
     one = np.array([(3, 1, 77, 0, 6.2, 0.5, -0.5)], dtype=oracle_lib.TRIG_DTYPE)
     ev = oracle_lib.cluster(one, 10)
     assert ev.size == 1 and ev[0]["j"] == 77 and ev[0]["n_trig"] == 1 and ev[0]["n_tmpl"] == 1
+
+
+# A trigger set worked by hand (window W = 10 samples).  Rows: (template,
+# segment, j, rho).  Stage 1, per (template, segment), chains with gaps <= W:
+#   t0 s0: {100, 105, 112} -> 105 (8.0, 3 triggers), {200} -> 200 (6.5)
+#   t1 s0: {108} (9.0), {300} (6.1);  t2 s0: {118} (7.2), {129} (6.3), {210} (7.9)
+#   t3 s0: {311} (6.0);  t0 s1: {100} (6.6)
+#   s2: t0 {55}, t1 {55}, t3 {60}, all rho 7.0
+# Stage 2, per segment in (j, template) order, chains with gaps <= W:
+#   s0: 105 -3- 108 -10- 118 | 11 | 129 | 71 | 200 -10- 210 | 90 | 300 | 11 | 311
+#   s2: 55 (t0) -0- 55 (t1) -5- 60: a three-way tie, kept by the lowest j, then template
+HAND_TRIGGERS = [
+    (0, 0, 100, 7.0), (0, 0, 105, 8.0), (0, 0, 112, 7.5), (0, 0, 200, 6.5),
+    (1, 0, 108, 9.0), (1, 0, 300, 6.1),
+    (2, 0, 118, 7.2), (2, 0, 129, 6.3), (2, 0, 210, 7.9),
+    (3, 0, 311, 6.0),
+    (0, 1, 100, 6.6),
+    (3, 2, 60, 7.0), (1, 2, 55, 7.0), (0, 2, 55, 7.0),
+]
+# (template, segment, j, rho, n_trig, n_tmpl) of every event, in (segment, j) order
+HAND_EVENTS = [
+    (1, 0, 108, 9.0, 5, 3),
+    (2, 0, 129, 6.3, 1, 1),
+    (2, 0, 210, 7.9, 2, 2),
+    (1, 0, 300, 6.1, 1, 1),
+    (3, 0, 311, 6.0, 1, 1),
+    (0, 1, 100, 6.6, 1, 1),
+    (0, 2, 55, 7.0, 3, 3),
+]
+
+
+def test_cluster_hand_worked_set(oracle_lib):
+    rows = [(t, s, j, 0, rho, 0.1 * j, -0.1 * t) for t, s, j, rho in HAND_TRIGGERS]
+    tr = np.array(rows, dtype=oracle_lib.TRIG_DTYPE)
+    tr = tr[np.lexsort((tr["j"], tr["seg"], tr["tmpl"]))]
+    ev = oracle_lib.cluster(tr, 10)
+    got = [(int(e["tmpl"]), int(e["seg"]), int(e["j"]), float(e["rho"]), int(e["n_trig"]), int(e["n_tmpl"]))
+           for e in ev]
+    assert got == HAND_EVENTS
+    for e in ev:   # z travels with the loudest member
+        assert e["z_re"] == 0.1 * e["j"] and e["z_im"] == -0.1 * e["tmpl"]
