@@ -218,6 +218,8 @@ struct mf_segment_s {
     float *fac = nullptr;          // a_k = alpha f^(-7/6) dt / S_k: W_k = a_k conj(X_k) for new samples
     float2 *r_exch = nullptr, *r_X = nullptr;
     float *r_s = nullptr;
+    alignas(64) unsigned char w_tmap[128];   // CUtensorMap over W for pass 1 (valid when has_tmap)
+    bool has_tmap = false;
     void release() {
         cudaFree(W); cudaFree(P); cudaFree(consts); cudaFree(psd); cudaFree(fac);
         cudaFree(r_exch); cudaFree(r_X); cudaFree(r_s);
@@ -355,6 +357,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     double *q = nullptr, *btmp = nullptr, *psd_dev = nullptr;
     const int64_t nbt = prefix_block_tmp_count(half);
     cudaError_t e = cudaMalloc(&g->W, sizeof(float2) * half);
+    if (e == cudaSuccess) g->has_tmap = make_w_tensor_map(g->W, g->log2N, g->w_tmap);   // pass 1's TMA view of W
     if (e == cudaSuccess) e = cudaMalloc(&g->fac, sizeof(float) * half);
     if (e == cudaSuccess) e = cudaMalloc(&g->P, sizeof(double) * (half + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->consts, sizeof(SegConsts));
@@ -454,6 +457,7 @@ static SegDev seg_dev(const mf_segment_s *g) {
     d.log2N = g->log2N;
     d.log2N2 = g->log2N / 2;
     d.log2N1 = g->log2N - d.log2N2;
+    d.w_tmap = g->has_tmap ? (const void *)g->w_tmap : nullptr;
     return d;
 }
 
@@ -662,7 +666,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     for (int s = 0; s < n_seg; ++s) {
         const SegDev sd = seg_dev(segs[s]);
         const int lgD = choose_log2D(b, segs[s]);
-        const int man = (int)(((segs[s]->N / 2) >> lgD) + 2);
+        const int man = (int)anchor_slot_records(segs[s]->log2N, lgD);   // records per anchor slot
         const bool rows = !use_persistent(b, segs[s]) && use_rows(b, segs[s]);
         const int nbk = rows ? pass2_rows_partials(sd.log2N) : pass2_blocks(sd.log2N);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
@@ -791,7 +795,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             }
             pi = prof_begin(b, MF_STAGE_PASS1, by_band + by_anc + exch_bytes, st);
             MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors + aoff, w.anchors4 + aoff, w.exch,
-                                 b->params.phase_mode, b->d_tmpl, b->p1_kind == 0, st));
+                                 b->params.phase_mode, b->d_tmpl, b->p1_kind == 0, w.status, b->spin_limit, st));
             prof_end(b, pi, st);
             if (overlap && u0 + batch < n_t) {
                 const int u1 = u0 + (int)batch;
@@ -878,7 +882,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     if (stream_capturing(st)) return set_err(MF_EINVAL, "mf_chisq_series allocates scratch and cannot be captured");
     const SegDev sd = seg_dev(seg);
     const int lgD = choose_log2D(b, seg);
-    const int man = (int)(((seg->N / 2) >> lgD) + 2);
+    const int man = (int)anchor_slot_records(seg->log2N, lgD);   // records per anchor slot
     const int n_t = (int)b->n;
     // 1024-point rows: every sub-band's exchange of a batch first, then one
     // rows kernel over all of them (p + 1 exchanges per template in flight)
@@ -913,7 +917,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
             for (int l = 0; l <= p && e == cudaSuccess; ++l) {
                 e = launch_pass1(sd, units + (size_t)l * n, (int)u0, nb, lgD, man, anc, anc4,
                                  exch + (size_t)l * nb * seg->N, b->params.phase_mode, b->d_tmpl, b->p1_kind == 0,
-                                 st);
+                                 b->chi_status, b->spin_limit, st);
                 ++launches;
             }
             if (e == cudaSuccess)
@@ -925,7 +929,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
         for (int l = 0; l <= p && e == cudaSuccess; ++l) {
             const UnitInfo *ul = units + (size_t)l * n;
             e = launch_pass1(sd, ul, (int)u0, nb, lgD, man, anc, anc4, exch, b->params.phase_mode, b->d_tmpl,
-                             b->p1_kind == 0, st);
+                             b->p1_kind == 0, b->chi_status, b->spin_limit, st);
             if (e == cudaSuccess)
                 e = launch_chisq_pass2(sd, ul, (int)u0, nb, exch, chisq, l == p ? 2 : (l == 0 ? 0 : 1), p, st);
             launches += 2;

@@ -62,9 +62,11 @@ __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const Uni
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < u.n_anc; i += gridDim.x * blockDim.x) {
         float4 r;
         float r4;
-        anchor_record(c1, c2, c3, c5, (int64_t)u.g_lo + i, log2D, seg.df, r, r4);
-        out[i] = r;
-        out4[i] = r4;
+        const int64_t g = (int64_t)u.g_lo + i;
+        anchor_record(c1, c2, c3, c5, g, log2D, seg.df, r, r4);
+        const int64_t a = anchor_slot_index(g, seg.log2N, seg.log2N1, log2D);
+        out[a] = r;
+        out4[a] = r4;
     }
 }
 
@@ -158,9 +160,10 @@ struct AttrOp {
 
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D, int max_anc,
                          const float4 *anchors, const float *anchors4, float2 *exch, int phase_mode,
-                         const double *tmpl, bool allow_pf, cudaStream_t st) {
+                         const double *tmpl, bool allow_pf, int *status, long long spin_limit, cudaStream_t st) {
     if (allow_pf && pass1_pf_applies(seg.log2N, log2D, phase_mode))
-        return launch_pass1_pf(seg, units, unit0, n_units, log2D, max_anc, anchors, anchors4, exch, st);
+        return launch_pass1_pf(seg, units, unit0, n_units, log2D, max_anc, anchors, anchors4, exch, status,
+                               spin_limit, st);
     Pass1Op op{seg, units, unit0, n_units, log2D, max_anc, phase_mode, anchors, anchors4, exch, tmpl, st};
     return dispatch_split(seg.log2N, op);
 }

@@ -68,8 +68,9 @@ struct TemplateSrc {
     __device__ __forceinline__ void load(int seq, int t, float2 *v) const {
         constexpr int T = L / 32;
         const UnitInfo u = p.units[unit];
-        const float4 *anc0 = p.anchors + (int64_t)slot * p.anc_stride;   // index: anchor - g_lo
+        const float4 *anc0 = p.anchors + (int64_t)slot * p.anc_stride;   // index: anchor_slot_index(g)
         const float *anc40 = p.anchors4 + (int64_t)slot * p.anc_stride;
+        constexpr int LGL = cx_ilog2(L);
         const int k1 = tile * C + seq;
         const int D = 1 << p.log2D;
         float2 w[16];
@@ -84,14 +85,18 @@ struct TemplateSrc {
         if (D >= C && p.log2D <= LG1) {
             // Every column of this tile falls in the same anchor group on a
             // given row n, so the tile needs one anchor per row:
-            // g(n) = (tile C >> log2D) + n (N1 >> log2D), staged once in shared memory.
+            // g(n) = (tile C >> log2D) + n (N1 >> log2D), record (tile C >> log2D) R + n,
+            // staged once in shared memory.
             const int gstep = 1 << (LG1 - p.log2D);
-            const int gbase = ((tile * C) >> p.log2D) - u.g_lo;
+            const int gcol = (tile * C) >> p.log2D;
+            const int gbase = gcol - u.g_lo;
+            const float4 *acol = anc0 + ((int64_t)gcol << (LGL - 1));
+            const float *acol4 = anc40 + ((int64_t)gcol << (LGL - 1));
             for (int n = threadIdx.x; n < L / 2; n += blockDim.x) {
                 const int a = gbase + n * gstep;
                 if (a >= 0 && a < u.n_anc) {
-                    sa[n] = __ldcg(&anc0[a]);   // anchors may be rewritten in the same launch (ring)
-                    sa4[n] = __ldcg(&anc40[a]);
+                    sa[n] = __ldcg(&acol[n]);   // anchors may be rewritten in the same launch (ring)
+                    sa4[n] = __ldcg(&acol4[n]);
                 }
             }
             release_hook(rel);
@@ -115,16 +120,15 @@ struct TemplateSrc {
             }
         } else {
             release_hook(rel);
-            const float4 *anc = anc0 - u.g_lo;
-            const float *anc4 = anc40 - u.g_lo;
             const int half = D >> 1;
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
                 const int k = k0 + ((r * T) << LG1);
                 const int kk = in[r] ? k : u.k_lo;
                 const int g = kk >> p.log2D;
-                const float4 a = __ldcg(&anc[g]);
-                const float a4 = __ldcg(&anc4[g]);
+                const int64_t ai = anchor_slot_index(g, LGL + LG1, LG1, p.log2D);
+                const float4 a = __ldcg(&anc0[ai]);
+                const float a4 = __ldcg(&anc40[ai]);
                 const float d = (float)(kk - ((g << p.log2D) + half));
                 float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
                 ph -= rintf(ph);

@@ -31,6 +31,7 @@ struct SegDev {
     double fs, df;
     int64_t N;
     int log2N, log2N1, log2N2;   // N = N1 * N2, N2 = column (pass-1) length
+    const void *w_tmap = nullptr;   // host copy of a CUtensorMap over W for pass 1 (NULL: none)
 };
 
 // Per (template, segment) unit, computed on the device for each filter call.
@@ -43,6 +44,27 @@ struct UnitInfo {
     int32_t tmpl;         // template index
 };
 static_assert(sizeof(UnitInfo) == 32, "the persistent pass 1 reads the band fields as one int4");
+
+// Anchor slot layout.  A template's G = (N/2)/D anchor groups g (bins
+// [g D, g D + D)) are stored column-major over gs = max(1, N1/D) anchor
+// columns: g -> (g mod gs) R + g / gs with R = G / gs (= N2/2 when D <= N1).
+// A pass-1 column tile (C <= D consecutive columns k1 sharing k1 / D, one
+// anchor group per column row n) then reads anchor column k1 / D, rows
+// n = 0..N2/2-1, as one contiguous run: record (kc / D) R + n.  With D > N1
+// (short segments) gs = 1 and the layout is linear.  A slot holds G records.
+__host__ __device__ __forceinline__ int anchor_log2gs(int log2N1, int log2D) {
+    return log2N1 > log2D ? log2N1 - log2D : 0;
+}
+__host__ __device__ __forceinline__ int anchor_log2R(int log2N, int log2N1, int log2D) {
+    return log2N - 1 - log2D - anchor_log2gs(log2N1, log2D);
+}
+__host__ __device__ __forceinline__ int64_t anchor_slot_index(int64_t g, int log2N, int log2N1, int log2D) {
+    const int lgs = anchor_log2gs(log2N1, log2D);
+    return ((g & ((1 << lgs) - 1)) << anchor_log2R(log2N, log2N1, log2D)) + (g >> lgs);
+}
+__host__ __device__ __forceinline__ int64_t anchor_slot_records(int log2N, int log2D) {
+    return (int64_t)1 << (log2N - 1 - log2D);
+}
 
 // Stable trigger keys: (tmpl, seg, j) packed into 64 bits.
 struct KeyLayout {
@@ -122,9 +144,11 @@ cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double 
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0,
                            int n_units, int log2D, int max_anc, float4 *anchors, float *anchors4,
                            cudaStream_t st);
+// status / spin_limit: the persistent form's bounded wait on its W copies (bit 1 of *status on expiry)
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                          int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
-                         int phase_mode, const double *tmpl, bool allow_pf, cudaStream_t st);
+                         int phase_mode, const double *tmpl, bool allow_pf, int *status, long long spin_limit,
+                         cudaStream_t st);
 cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units,
                          const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
                          mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
@@ -134,8 +158,11 @@ int pass2_blocks(int log2N);
 // launch_pass1 takes it where it applies
 bool pass1_pf_applies(int log2N, int log2D, int phase_mode);
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
-                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
-                            cudaStream_t st);
+                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, int *status,
+                            long long spin_limit, cudaStream_t st);
+// tensor map over W (128 bytes at map_out) for the persistent pass 1; false if
+// it does not apply (N outside 2^16..2^21) or cannot be made
+bool make_w_tensor_map(const float2 *W, int log2N, void *map_out);
 cudaError_t pass1_pf_kernel_attributes();
 // pass 2 with whole rows per warp and bulk-copy prefetch (row length 1024 only)
 bool pass2_rows_applies(int log2N);

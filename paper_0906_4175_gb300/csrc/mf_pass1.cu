@@ -9,9 +9,18 @@
 // CTA wait on them at once, and with two CTAs per SM (128 registers, 86 KB of
 // shared memory each) the other CTA rarely covers the wait.  Here each CTA
 // loops over tiles (item = blockIdx.x + i * gridDim.x, template-major) and
-// issues cp.async copies of item i + 1's W rows and anchors into a staging
-// area right after the column data of item i is in shared memory, so the
-// copies run under item i's second Stockham stage and exchange stores.
+// starts the copies of item i + 1's W rows and anchors into a staging area
+// right after the column data of item i is in shared memory, so the copies
+// run under item i's second Stockham stage and exchange stores:
+//   W rows      2-D TMA loads (cp.async.bulk.tensor) of the segment's W viewed
+//               as [N2/2 rows][N1 columns], boxes of C columns x 64 rows, only
+//               the boxes that meet the template's band;
+//   anchors     one record per column row: the tile's rows of one anchor
+//               column, contiguous in the column-major anchor slot, as two
+//               bulk copies (cp.async.bulk) of the rows in the band.
+// One thread issues them, completion on an mbarrier (bounded wait).  Without a
+// tensor map (segments prepared outside mf_segment_upload), every thread
+// copies 16-byte chunks with cp.async instead.
 //
 // Shared memory (L <= 1024, two CTAs per SM):
 //   column data   C x STRIDE complex64           (as in the per-tile kernel)
@@ -21,27 +30,36 @@
 //   twiddles     the second stage's table w[r * 32 + k] = exp(2 pi i r k / L)
 //                 for L <= 512; for L = 1024 (no room for all 32 rows) rows
 //                 r <= 16 only, and w[r] = w[r - 16] w[16] for r > 16
+//   mbarrier      8 bytes
+//
+// Template generation skips, warp by warp, groups of four column rows that lie
+// outside the band of every lane (the rows of a column are 32 N1 bins apart,
+// so a template's band covers a contiguous range of them); the arithmetic of
+// every in-band bin is that of the per-tile kernel, so results are bit-identical.
 //
 // Applies to the FP64-anchor phase when the anchor spacing D is at least the
 // tile width C and at most N1, for N = 2^16 .. 2^21 (L = 256 .. 1024); every
 // other case launches the per-tile kernel.
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
+#include "mf_async.cuh"
 #include "mf_filter.cuh"
 
 namespace mf {
 namespace {
 
-__device__ __forceinline__ unsigned sh_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sh_addr(dst)), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sh_addr(dst)), "l"(src) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int kBoxRows = 64;   // rows of one W box (C x 64 complex64 = 4 KB at C = 8)
 
 struct Pass1PfParams {
     const float2 *W;
@@ -51,6 +69,8 @@ struct Pass1PfParams {
     float2 *E;
     int anc_stride, log2D, log2N;
     int unit0, n_items;
+    int *status;                // bit 1: a bounded wait expired
+    long long spin_limit;
 };
 
 template <int L, int C>
@@ -63,112 +83,170 @@ __host__ __device__ constexpr int pf_tw_elems() { return L == 1024 ? 17 * 32 : T
 template <int L, int C>
 __host__ __device__ constexpr size_t pf_smem_bytes() {
     return pass_data_bytes<L, C>() + pf_wbuf_elems<L, C>() * sizeof(float2) +
-           (size_t)(L / 2) * (sizeof(float4) + sizeof(float)) + (size_t)pf_tw_elems<L>() * sizeof(float2);
+           (size_t)(L / 2) * (sizeof(float4) + sizeof(float)) + (size_t)pf_tw_elems<L>() * sizeof(float2) +
+           sizeof(uint64_t);
 }
 
-// Issue the copies of one item's inputs: W rows n < L/2 (C consecutive
-// columns each, 16-byte chunks, skipped when both columns of a chunk are
-// outside the template's band) and the anchor record of every row that has an
-// anchor.  Every thread commits one group.
 // The band fields of a unit (k_lo, k_hi, g_lo, n_anc: the first 16 bytes of
 // its 32-byte-aligned UnitInfo), loaded a full item ahead of their use.
 __device__ __forceinline__ int4 pf_band(const Pass1PfParams &p, int slot) {
     return __ldg(reinterpret_cast<const int4 *>(p.units + p.unit0 + slot));
 }
 
-template <int L, int C, int LG1>
-__device__ __forceinline__ void pf_issue(const Pass1PfParams &p, int item, int4 band, float2 *wbuf, float4 *abuf,
-                                         float *abuf4) {
+// Start the copies of one item's inputs: the W rows n < L/2 of the tile's C
+// columns and the anchor record of each row (anchor column kc / D, rows n,
+// contiguous in the slot).  With a tensor map, thread 0 issues the TMA boxes
+// of W that meet the band and bulk copies of the anchor rows in the band, all
+// counted on bar (one phase per item); otherwise every thread copies 16-byte
+// W chunks (skipped when both columns of a chunk are outside the band) and
+// the anchor records of its rows with cp.async and commits one group.
+// Called by all threads after a barrier that ends every read of the staging
+// area.
+template <int L, int C, int LG1, bool TMA>
+__device__ __forceinline__ void pf_issue(const Pass1PfParams &p, const CUtensorMap *wmap, int item, int4 band,
+                                         float2 *wbuf, float4 *abuf, float *abuf4, uint64_t *bar) {
     constexpr int NT = C * (L / 32);
     constexpr int TILES = (1 << LG1) / C;
-    constexpr int CH = C / 2;   // 16-byte chunks per row
     const int slot = item / TILES, tile = item - slot * TILES;
     const int k_lo = band.x, k_hi = band.y, g_lo = band.z, n_anc = band.w;
     const int kc = tile * C;
-#pragma unroll
-    for (int i = 0; i < (L / 2) * CH / NT; ++i) {
-        const int c = threadIdx.x + i * NT;
-        const int n = c / CH, j = c - n * CH;
-        const int k = kc + 2 * j + (n << LG1);
-        if (k + 1 >= k_lo && k < k_hi) cp_async16(wbuf + n * C + 2 * j, p.W + k);
-    }
-    const float4 *anc0 = p.anchors + (int64_t)slot * p.anc_stride;
-    const float *anc40 = p.anchors4 + (int64_t)slot * p.anc_stride;
-    const int gstep = 1 << (LG1 - p.log2D);
-    const int gbase = (kc >> p.log2D) - g_lo;
-    for (int n = threadIdx.x; n < L / 2; n += NT) {
-        const int a = gbase + n * gstep;
-        if (a >= 0 && a < n_anc) {
-            cp_async16(abuf + n, anc0 + a);
-            cp_async4(abuf4 + n, anc40 + a);
+    const int gcol = kc >> p.log2D;
+    const float4 *acol = p.anchors + (int64_t)slot * p.anc_stride + ((int64_t)gcol << (cx_ilog2(L) - 1));
+    const float *acol4 = p.anchors4 + (int64_t)slot * p.anc_stride + ((int64_t)gcol << (cx_ilog2(L) - 1));
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            // rows holding a bin of the band: kc + C - 1 + n N1 >= k_lo and kc + n N1 < k_hi
+            const int lo_num = k_lo - kc - (C - 1), hi_num = k_hi - kc;
+            const int n_lo = lo_num <= 0 ? 0 : (lo_num + (1 << LG1) - 1) >> LG1;
+            const int n_hi = hi_num <= 0 ? 0 : min(L / 2, (hi_num + (1 << LG1) - 1) >> LG1);
+            fence_proxy_async();
+            if (n_hi > n_lo) {
+                const int b0 = n_lo / kBoxRows, b1 = (n_hi + kBoxRows - 1) / kBoxRows;
+                const int a0 = n_lo & ~3, a1 = (n_hi + 3) & ~3;   // 16-byte runs of the FP32 q4 terms
+                mbar_expect_tx(bar, (uint32_t)((b1 - b0) * kBoxRows * C * sizeof(float2) +
+                                               (n_hi - n_lo) * sizeof(float4) + (a1 - a0) * sizeof(float)));
+                for (int b = b0; b < b1; ++b) tma_load_2d(wbuf + b * kBoxRows * C, wmap, kc, b * kBoxRows, bar);
+                bulk_copy_g2s(abuf + n_lo, acol + n_lo, (uint32_t)((n_hi - n_lo) * sizeof(float4)), bar);
+                bulk_copy_g2s(abuf4 + a0, acol4 + a0, (uint32_t)((a1 - a0) * sizeof(float)), bar);
+            } else {
+                mbar_arrive(bar);
+            }
         }
+    } else {
+        constexpr int CH = C / 2;   // 16-byte chunks per row
+#pragma unroll
+        for (int i = 0; i < (L / 2) * CH / NT; ++i) {
+            const int c = threadIdx.x + i * NT;
+            const int n = c / CH, j = c - n * CH;
+            const int k = kc + 2 * j + (n << LG1);
+            if (k + 1 >= k_lo && k < k_hi) cp_async16(wbuf + n * C + 2 * j, p.W + k);
+        }
+        const int gstep = 1 << (LG1 - p.log2D);
+        const int gbase = gcol - g_lo;
+        for (int n = threadIdx.x; n < L / 2; n += NT) {
+            const int a = gbase + n * gstep;
+            if (a >= 0 && a < n_anc) {
+                cp_async16(abuf + n, acol + n);
+                cp_async4(abuf4 + n, acol4 + n);
+            }
+        }
+        cp_async_commit();
     }
-    cp_async_commit();
 }
 
-template <int L, int C, int LG1>
-__global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams p) {
+template <int L, int C, int LG1, bool TMA>
+__global__ void __launch_bounds__(C *(L / 32), 2)
+    k_pass1_pf(const Pass1PfParams p, const __grid_constant__ CUtensorMap wmap) {
     using S = FftShape<L>;
     static_assert(S::NST == 2, "two-stage column lengths only");
+    static_assert(pass_data_bytes<L, C>() % 128 == 0, "TMA destinations must be 128-byte aligned");
     constexpr int T = S::T;
     constexpr int NT = C * T;
     constexpr int TILES = (1 << LG1) / C;
-    extern __shared__ float2 smem[];
-    float2 *wbuf = smem + pass_data_bytes<L, C>() / sizeof(float2);
+    extern __shared__ __align__(128) float2 pf_smem[];
+    float2 *wbuf = pf_smem + pass_data_bytes<L, C>() / sizeof(float2);
     float4 *abuf = (float4 *)(wbuf + pf_wbuf_elems<L, C>());
     float *abuf4 = (float *)(abuf + L / 2);
     float2 *tw = (float2 *)(abuf4 + L / 2);
+    uint64_t *bar = (uint64_t *)(tw + pf_tw_elems<L>());
     const int seq = threadIdx.x % C, t = threadIdx.x / C;
-    float2 *sq = smem + seq * SeqStride<L, C>::value;
-    {   // published by the first item's barrier
+    float2 *sq = pf_smem + seq * SeqStride<L, C>::value;
+    {
         const float2 *src = g_tw_tables + tw_offset<L>();
         for (int m = threadIdx.x; m < pf_tw_elems<L>(); m += NT) tw[m] = __ldg(&src[m]);
     }
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_fence_init();
+        }
+    }
+    __syncthreads();   // twiddles and the mbarrier initialised
     const int D = 1 << p.log2D;
     const typename ExchSink<L, C, +1, LG1>::Params kp{p.E, LG1, p.log2N};
 
     int item = blockIdx.x;
+    uint32_t parity = 0;
     int4 band = make_int4(0, 0, 0, 0);
     if (item < p.n_items) {
         band = pf_band(p, item / TILES);
-        pf_issue<L, C, LG1>(p, item, band, wbuf, abuf, abuf4);
+        pf_issue<L, C, LG1, TMA>(p, &wmap, item, band, wbuf, abuf, abuf4, bar);
     }
     for (; item < p.n_items; item += gridDim.x) {
         const int slot = item / TILES, tile = item - slot * TILES;
         const int next = item + (int)gridDim.x;
         const int4 nband = next < p.n_items ? pf_band(p, next / TILES) : make_int4(0, 0, 0, 0);
         const int k_lo = band.x, k_hi = band.y;
-        cp_async_wait_all();
-        __syncthreads();   // staged inputs visible; the previous item's last stage has read the column data
+        bool ok = true;
+        if constexpr (TMA) {
+            ok = mbar_wait_bounded(bar, parity, p.spin_limit);
+            parity ^= 1u;
+        }
+        if constexpr (!TMA) cp_async_wait_all();
+        // staged inputs visible; the previous item's last stage has read the column data
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(p.status, 2);
+            return;   // the W copy of this item never completed; no other copy is in flight
+        }
         float2 v[32];
+        const int k1 = tile * C + seq;
         {
-            const int k1 = tile * C + seq;
             const int k0 = k1 + (t << LG1);
             // offset from the anchor centre, the same on every row (D divides N1)
             const float d = (float)((k1 & (D - 1)) - (D >> 1));
+            // rows r of this thread in the band: [rlo, rhi) (k grows with r)
+            constexpr int LGS = cx_ilog2(T) + LG1;   // log2 of the row step T N1 in bins
+            const int rlo = k_lo <= k0 ? 0 : min(16, (k_lo - k0 + (1 << LGS) - 1) >> LGS);
+            const int rhi = k_hi <= k0 ? 0 : min(16, (k_hi - k0 + (1 << LGS) - 1) >> LGS);
+            const int wlo = (int)__reduce_min_sync(0xffffffffu, (unsigned)rlo);
+            const int whi = (int)__reduce_max_sync(0xffffffffu, (unsigned)rhi);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                const int n = t + r * T;
-                const int k = k0 + ((r * T) << LG1);
-                float2 x = czero();
-                if (k >= k_lo && k < k_hi) {
-                    const float2 w = wbuf[n * C + seq];
-                    const float4 a = abuf[n];
-                    const float a4 = abuf4[n];
-                    float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
-                    ph -= rintf(ph);
-                    float sn, cs;
-                    __sincosf(6.283185307179586f * ph, &sn, &cs);
-                    x = make_float2(fmaf(w.x, cs, w.y * sn), fmaf(w.y, cs, -w.x * sn));   // W e^{-i 2 pi ph}
+            for (int g = 0; g < 4; ++g) {
+                if (4 * g + 4 > wlo && 4 * g < whi) {   // some lane of the warp has a bin of rows 4g..4g+3
+#pragma unroll
+                    for (int r = 4 * g; r < 4 * g + 4; ++r) {
+                        const int n = t + r * T;
+                        const float2 w = wbuf[n * C + seq];
+                        const float4 a = abuf[n];
+                        const float a4 = abuf4[n];
+                        float ph = fmaf(fmaf(fmaf(fmaf(a4, d, a.w), d, a.z), d, a.y), d, a.x);
+                        ph -= rintf(ph);
+                        float sn, cs;
+                        __sincosf(6.283185307179586f * ph, &sn, &cs);
+                        const float2 x = make_float2(fmaf(w.x, cs, w.y * sn), fmaf(w.y, cs, -w.x * sn));  // W e^{-i 2 pi ph}
+                        v[r] = (r >= rlo && r < rhi) ? x : czero();   // staging outside the band is stale
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 4 * g; r < 4 * g + 4; ++r) v[r] = czero();
                 }
-                v[r] = x;
             }
         }
         dft32_halfzero<+1>(v);
 #pragma unroll
         for (int r = 0; r < 32; ++r) sq[spad(32 * t + r)] = v[r];
         __syncthreads();   // column data complete; every thread has consumed the staged inputs
-        if (next < p.n_items) pf_issue<L, C, LG1>(p, next, nband, wbuf, abuf, abuf4);
+        if (next < p.n_items) pf_issue<L, C, LG1, TMA>(p, &wmap, next, nband, wbuf, abuf, abuf4, bar);
         ExchSink<L, C, +1, LG1> snk(kp, tile, p.unit0 + slot, slot);
         if constexpr (L == 1024) last_stage_1024_split<+1>(sq, tw, seq, t, snk);
         else stockham_stage<L, S::R1, 32, +1, true>(sq, tw, seq, t, snk);
@@ -178,12 +256,14 @@ __global__ void __launch_bounds__(C *(L / 32), 2) k_pass1_pf(const Pass1PfParams
 
 int g_pf_blocks_per_sm[3] = {0, 0, 0};   // L = 256, 512, 1024
 int g_pf_sms = 0;
+int g_pf_tma = 1;
 
 template <int L>
 constexpr int pf_index() { return L == 256 ? 0 : (L == 512 ? 1 : 2); }
 
 struct PfOp {
     const Pass1PfParams *p;
+    const CUtensorMap *wmap;   // NULL: cp.async staging of W
     int n_units;
     cudaStream_t st;
     bool attrs = false;
@@ -192,28 +272,61 @@ struct PfOp {
         if constexpr (N2 >= 256 && N2 <= 1024) {
             constexpr int C = seqs_per_cta<N2>(N1);
             constexpr int LG1 = cx_ilog2(N1);
-            auto kern = k_pass1_pf<N2, C, LG1>;
+            constexpr int SM = (int)pf_smem_bytes<N2, C>();
             if (attrs) {
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)pf_smem_bytes<N2, C>());
+                cudaError_t e = cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, false>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SM);
                 if (e != cudaSuccess) return e;
-                int nb = 0;
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C * (N2 / 32), pf_smem_bytes<N2, C>());
+                int nb = 0, nb2 = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pass1_pf<N2, C, LG1, false>, C * (N2 / 32), SM);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_pass1_pf<N2, C, LG1, true>, C * (N2 / 32),
+                                                                      SM);
                 if (e != cudaSuccess) return e;
-                g_pf_blocks_per_sm[pf_index<N2>()] = nb;
+                g_pf_blocks_per_sm[pf_index<N2>()] = std::min(nb, nb2);
                 return cudaSuccess;
             }
             Pass1PfParams q = *p;
             q.n_items = n_units * (N1 / C);
             const int per_sm = g_pf_blocks_per_sm[pf_index<N2>()];
             const int grid = (int)std::min<int64_t>(q.n_items, (int64_t)per_sm * g_pf_sms);
-            kern<<<grid, C * (N2 / 32), pf_smem_bytes<N2, C>(), st>>>(q);
+            if (wmap != nullptr && g_pf_tma) {
+                k_pass1_pf<N2, C, LG1, true><<<grid, C * (N2 / 32), SM, st>>>(q, *wmap);
+            } else {
+                CUtensorMap none;
+                memset(&none, 0, sizeof(none));
+                k_pass1_pf<N2, C, LG1, false><<<grid, C * (N2 / 32), SM, st>>>(q, none);
+            }
             return cudaGetLastError();
         } else {
             return cudaErrorNotSupported;
         }
     }
 };
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against
+// the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    }
+    return fn;
+}
 
 }  // namespace
 
@@ -229,12 +342,29 @@ bool pass1_pf_applies(int log2N, int log2D, int phase_mode) {
     return g_pf_blocks_per_sm[idx] >= 1;
 }
 
+bool make_w_tensor_map(const float2 *W, int log2N, void *map_out) {
+    if (log2N < 16 || log2N > 21 || W == nullptr || ((uintptr_t)W & 15u) != 0) return false;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const int log2N2 = log2_n2(log2N), log2N1 = log2N - log2N2;
+    const int C = (8192 >> log2N2) < (1 << log2N1) ? (8192 >> log2N2) : (1 << log2N1);   // seqs_per_cta
+    // W[k], k < N/2, as rows n (k = k1 + n N1) of N1 complex64 (8-byte elements)
+    const cuuint64_t dims[2] = {(cuuint64_t)1 << log2N1, (cuuint64_t)1 << (log2N2 - 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)sizeof(float2) << log2N1};
+    const cuuint32_t box[2] = {(cuuint32_t)C, (cuuint32_t)kBoxRows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap *m = (CUtensorMap *)map_out;
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
-                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
-                            cudaStream_t st) {
+                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, int *status,
+                            long long spin_limit, cudaStream_t st) {
     if (n_units <= 0) return cudaSuccess;
-    Pass1PfParams p{seg.W, units, anchors, anchors4, exch, max_anc, log2D, seg.log2N, unit0, 0};
-    PfOp op{&p, n_units, st};
+    Pass1PfParams p{seg.W, units, anchors, anchors4, exch, max_anc, log2D, seg.log2N, unit0, 0, status, spin_limit};
+    PfOp op{&p, (const CUtensorMap *)seg.w_tmap, n_units, st};
     return dispatch_split(seg.log2N, op);
 }
 
@@ -245,9 +375,13 @@ cudaError_t pass1_pf_kernel_attributes() {
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_pf_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    {
+        const char *v = std::getenv("MFGB_P1TMA");   // "0": cp.async staging of W (comparisons)
+        g_pf_tma = (v && v[0] == '0') ? 0 : 1;
+    }
     for (int lg = 16; lg <= 21; ++lg) {
         Pass1PfParams p{};
-        PfOp op{&p, 0, nullptr, true};
+        PfOp op{&p, nullptr, 0, nullptr, true};
         if ((e = dispatch_split(lg, op)) != cudaSuccess) return e;
     }
     return cudaSuccess;

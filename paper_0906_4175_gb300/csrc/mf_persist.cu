@@ -107,9 +107,11 @@ __device__ __noinline__ void persist_anchors(const PersistParams &P, int u, int 
     for (int i = lo + (int)threadIdx.x; i < hi; i += 256) {
         float4 r;
         float r4;
-        anchor_record(c1, c2, c3, c5, (int64_t)ui.g_lo + i, P.log2D, P.seg.df, r, r4);
-        out[i] = r;
-        out4[i] = r4;
+        const int64_t g = (int64_t)ui.g_lo + i;
+        anchor_record(c1, c2, c3, c5, g, P.log2D, P.seg.df, r, r4);
+        const int64_t a = anchor_slot_index(g, P.seg.log2N, P.seg.log2N1, P.log2D);
+        out[a] = r;
+        out4[a] = r4;
     }
 }
 

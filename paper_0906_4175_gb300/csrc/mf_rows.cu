@@ -20,52 +20,12 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "mf_async.cuh"
 #include "mf_filter.cuh"
 
 namespace mf {
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// as mbar_try_wait, but the thread may sleep up to hint_ns before giving up
-// (fewer polling instructions while a long operation completes)
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_row_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-// orders this thread's earlier generic-proxy shared-memory accesses before
-// later async-proxy ones (the bulk copy refilling the region)
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 constexpr int kWarps = 8;                     // warps per CTA
 
@@ -119,7 +79,7 @@ struct GroupRhoSink {
         fence_proxy_async();
         if (next_src != nullptr && (threadIdx.x & (32 * G - 1)) == 0) {
             mbar_expect_tx(bar, L * sizeof(float2));
-            bulk_row_copy(region, next_src, L * sizeof(float2), bar);
+            bulk_copy_g2s(region, next_src, L * sizeof(float2), bar);
         }
     }
     template <int R>
@@ -226,7 +186,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
     int64_t r = (int64_t)blockIdx.x * NG + grp;
     if (r < total && t == 0 && !row_withheld(p, r)) {
         mbar_expect_tx(&bars[grp], L * sizeof(float2));
-        bulk_row_copy(region, row_src<L>(p, r), L * sizeof(float2), &bars[grp]);
+        bulk_copy_g2s(region, row_src<L>(p, r), L * sizeof(float2), &bars[grp]);
     }
     uint32_t parity = 0;
     for (; r < total; r += step) {
@@ -385,7 +345,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_tc(RowsParams p) 
     int64_t r0 = (int64_t)blockIdx.x * kWarps + 4 * g;   // the tile's first row; rows r0 .. r0 + 3 go together
     if (r0 + rl < total && t == 0) {
         mbar_expect_tx(&bars[w], L * sizeof(float2));
-        bulk_row_copy(region, row_src<L>(p, r0 + rl), L * sizeof(float2), &bars[w]);
+        bulk_copy_g2s(region, row_src<L>(p, r0 + rl), L * sizeof(float2), &bars[w]);
     }
     uint32_t parity = 0, tparity = 0;
     for (; r0 < total; r0 += step) {
