@@ -120,6 +120,31 @@ int mf_bank_destroy(mf_bank bank);
 /* Number of templates (host out). */
 int mf_bank_size(mf_bank bank, int64_t *n);
 
+/* Template sharding: templates are independent (Sec. 2, data parallelism
+ * over templates and segments), so a bank can be split by template range
+ * across processes or devices, each filtering the same segments.
+ *
+ * mf_bank_partition -- contiguous ranges of near-equal modelled cost:
+ * starts[0] = 0 < starts[1] < ... < starts[parts] = n (host int64 array of
+ * parts + 1 entries, written), part r being templates [starts[r],
+ * starts[r+1]).  The cost of a template is the sum over the n_seg segments
+ * (seg_N[s] samples at seg_fs[s] Hz, host arrays) of 16 N + 8 K, the bytes
+ * its filter moves (the complex64 exchange written and read, its band of K
+ * weighted-data bins, Sec. 1.1 band rule with params->f_low).  Host only, no
+ * device work.  Errors: MF_EINVAL (NULL, n <= 0, parts outside [1, n], a bad
+ * mass or segment).
+ *
+ * mf_bank_create_shard -- mf_bank_create for templates [first, first + count)
+ * of the n masses m1, m2.  The anchor spacing of the phase evaluation is fixed
+ * by all n templates, so the shard filters its templates bit-identically to
+ * the bank of all n.  The shard numbers its templates 0 .. count-1 (peaks,
+ * triggers): template i of the shard is template first + i of the list.
+ * Errors: as mf_bank_create, and MF_EINVAL when the range is not inside [0, n). */
+int mf_bank_partition(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                      const int64_t *seg_N, const double *seg_fs, int n_seg, int parts, int64_t *starts);
+int mf_bank_create_shard(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                         int64_t first, int64_t count, mf_bank *out);
+
 /* mf_segment_upload -- data conditioning for Eq. (1), once per segment.
  * s: N float32 samples of s(t) at rate fs (device if s_on_device, else host).
  * N: power of two, 2^10 <= N <= 2^22.  fs > 0.
@@ -256,7 +281,8 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
  * 128 MiB..1 GiB of exchange in flight, i.e. 16..128 templates per batch at
  * N = 2^20 and proportionally more at shorter segments, each with the kernel
  * forms of the two passes: pass 1 persistent with the next tile's inputs
- * staged by cp.async, or one CTA per column tile; pass 2 in warp-owned rows
+ * staged by TMA and bulk copies, in tiles of C = 8192/N2 columns or of C/2
+ * (the CTA tile), or one CTA per column tile; pass 2 in warp-owned rows
  * with bulk-copy prefetch, or one CTA per row tile) and keeps the fastest in
  * the bank for later calls (the default is per-batch launches with 1 GiB, the
  * staged pass 1 and the row pass 2 where they apply).  It
@@ -279,6 +305,10 @@ int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold
  *                                starts on queue 1 (anchors + pass 1)
  *   MFGB_P1PF=0                  pass 1 one CTA per column tile instead of the
  *                                persistent kernel with staged inputs
+ *   MFGB_P1TILE=half             the persistent pass 1 with tiles of half the
+ *                                columns (three CTAs per SM)
+ *   MFGB_P1TMA=0                 the persistent pass 1 stages W with per-thread
+ *                                cp.async instead of TMA
  *   MFGB_P2ROWS=0                pass 2 one CTA per row tile instead of
  *                                warp-owned rows (FP32 FFT form only)
  *   MFGB_UNIT_ORDER=bank         templates in bank order instead of widest

@@ -47,9 +47,14 @@ def params(f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR, pn_order: int
 
 
 class Bank:
-    """mf_bank_create: template constants for masses m1, m2 (solar masses)."""
+    """mf_bank_create: template constants for masses m1, m2 (solar masses).
 
-    def __init__(self, m1, m2, f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR, fft_mode: int = MF_FFT_FP32):
+    With ``first``/``count`` the bank holds templates [first, first + count) of
+    the mass list (mf_bank_create_shard: a shard of a bank split by template
+    range, numbered 0 .. count-1, filtered as the whole list's bank would)."""
+
+    def __init__(self, m1, m2, f_low: float = 40.0, phase_mode: int = MF_PHASE_ANCHOR, fft_mode: int = MF_FFT_FP32,
+                 first: int = 0, count: int = None):
         m1 = np.ascontiguousarray(m1, dtype=np.float64)
         m2 = np.ascontiguousarray(m2, dtype=np.float64)
         if m1.shape != m2.shape or m1.ndim != 1:
@@ -57,11 +62,18 @@ class Bank:
         self.params = params(f_low, phase_mode, fft_mode=fft_mode)
         h = ctypes.c_void_p()
         L = _native.lib()
-        check(L.mf_bank_create(m1.ctypes.data, m2.ctypes.data, m1.size, ctypes.byref(self.params),
-                               ctypes.byref(h)))
+        if count is None and first == 0:
+            check(L.mf_bank_create(m1.ctypes.data, m2.ctypes.data, m1.size, ctypes.byref(self.params),
+                                   ctypes.byref(h)))
+            count = m1.size
+        else:
+            count = m1.size - first if count is None else count
+            check(L.mf_bank_create_shard(m1.ctypes.data, m2.ctypes.data, m1.size, ctypes.byref(self.params),
+                                         int(first), int(count), ctypes.byref(h)))
         self._h = h
-        self.n = int(m1.size)
-        self.m1, self.m2 = m1, m2
+        self.n = int(count)
+        self.first = int(first)
+        self.m1, self.m2 = m1[first:first + count], m2[first:first + count]
 
     @property
     def handle(self):

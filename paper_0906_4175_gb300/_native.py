@@ -33,6 +33,8 @@ SIGNATURES = {
     "mf_bank_create": (_I, [_P, _P, _I64, _P, _P]),
     "mf_bank_destroy": (_I, [_P]),
     "mf_bank_size": (_I, [_P, _P]),
+    "mf_bank_partition": (_I, [_P, _P, _I64, _P, _P, _P, _I, _I, _P]),
+    "mf_bank_create_shard": (_I, [_P, _P, _I64, _P, _I64, _I64, _P]),
     "mf_segment_upload": (_I, [_P, _I64, _D, _P, _D, _D, _I, _P, _P]),
     "mf_segment_destroy": (_I, [_P]),
     "mf_segment_refresh": (_I, [_P, _P, _I, _P]),

@@ -182,7 +182,8 @@ struct mf_bank_s {
     int64_t tuned_exch = 0;
     double split = 0.60;
     // kernel forms of the per-batch schedule: pass 1 persistent with staged
-    // inputs (0) or per tile (1); pass 2 in warp-owned rows (0) or per tile (1)
+    // inputs (0), per tile (1), or persistent with tiles of half the width (2);
+    // pass 2 in warp-owned rows (0) or per tile (1)
     int p1_kind = 0, p2_kind = 0;
     int *chi_status = nullptr;        // status of the last mf_chisq_series (bit 2: a bounded wait ran out)
 };
@@ -218,7 +219,7 @@ struct mf_segment_s {
     float *fac = nullptr;          // a_k = alpha f^(-7/6) dt / S_k: W_k = a_k conj(X_k) for new samples
     float2 *r_exch = nullptr, *r_X = nullptr;
     float *r_s = nullptr;
-    alignas(64) unsigned char w_tmap[128];   // CUtensorMap over W for pass 1 (valid when has_tmap)
+    alignas(64) unsigned char w_tmap[256];   // two CUtensorMaps over W for pass 1 (valid when has_tmap)
     bool has_tmap = false;
     void release() {
         cudaFree(W); cudaFree(P); cudaFree(consts); cudaFree(psd); cudaFree(fac);
@@ -254,28 +255,38 @@ static int check_params(const mf_bank_params &p) {
     return MF_OK;
 }
 
-extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
-                              mf_bank *out) {
+// A bank of templates [first, first + count) of the mass list m1, m2 (n
+// entries).  The phase-derivative bounds that fix the anchor spacing are taken
+// over all n templates, so every shard of a list uses the spacing the whole
+// list would and filters its templates exactly as the whole bank does.
+static int bank_create_range(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                             int64_t first, int64_t count, mf_bank *out) {
     if (!out) return set_err(MF_EINVAL, "out is NULL");
     *out = nullptr;
     if (!m1 || !m2 || n <= 0) return set_err(MF_EINVAL, "need n > 0 masses");
-    if (n > (int64_t)1 << 24) return set_err(MF_EINVAL, "at most 2^24 templates per bank");
+    if (first < 0 || count <= 0 || first > n - count)
+        return set_err(MF_EINVAL, "templates [%lld, %lld) outside the %lld masses", (long long)first,
+                       (long long)(first + count), (long long)n);
+    if (count > (int64_t)1 << 24) return set_err(MF_EINVAL, "at most 2^24 templates per bank");
     mf_bank_params p = params ? *params : default_params();
     int rc = check_params(p);
     if (rc) return rc;
     int r0 = ensure_device_init();
     if (r0) return r0;
-    std::vector<double> rec((size_t)n * kTmplStride);
+    std::vector<double> rec((size_t)count * kTmplStride);
     double B1 = 0.0, B5 = 0.0, fmin = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         if (!(m1[i] > 0.0) || !(m2[i] > 0.0) || !isfinite(m1[i]) || !isfinite(m2[i]))
             return set_err(MF_EINVAL, "template %lld: masses must be finite and > 0", (long long)i);
-        double *r = &rec[(size_t)i * kTmplStride];
+        double tmp[kTmplStride];
+        const bool mine = i >= first && i < first + count;
+        double *r = mine ? &rec[(size_t)(i - first) * kTmplStride] : tmp;
         template_constants(m1[i], m2[i], r);
         B1 = std::max(B1, psi_deriv_bound(r, p.f_low, 1));
         B5 = std::max(B5, psi_deriv_bound(r, p.f_low, 5));
-        fmin = std::min(fmin, r[TF_FISCO]);
+        if (mine) fmin = std::min(fmin, r[TF_FISCO]);
     }
+    n = count;
     mf_bank b = new (std::nothrow) mf_bank_s();
     if (!b) return set_err(MF_ENOMEM, "host allocation");
     b->n = n;
@@ -305,6 +316,59 @@ extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, con
                        cudaGetErrorString(e));
     }
     *out = b;
+    return MF_OK;
+}
+
+extern "C" int mf_bank_create(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                              mf_bank *out) {
+    return bank_create_range(m1, m2, n, params, 0, n, out);
+}
+
+extern "C" int mf_bank_create_shard(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                                    int64_t first, int64_t count, mf_bank *out) {
+    return bank_create_range(m1, m2, n, params, first, count, out);
+}
+
+// Contiguous template ranges of near-equal modelled cost: per template
+// sum over segments of 16 N (the exchange written and read) + 8 K (its band
+// of W), with K from the Sec. 1.1 band rule.
+extern "C" int mf_bank_partition(const double *m1, const double *m2, int64_t n, const mf_bank_params *params,
+                                 const int64_t *seg_N, const double *seg_fs, int n_seg, int parts,
+                                 int64_t *starts) {
+    if (!m1 || !m2 || !seg_N || !seg_fs || !starts) return set_err(MF_EINVAL, "NULL argument");
+    if (n <= 0 || n_seg < 1 || parts < 1) return set_err(MF_EINVAL, "need n > 0, n_seg >= 1, parts >= 1");
+    if (parts > n) return set_err(MF_EINVAL, "%d parts for %lld templates", parts, (long long)n);
+    mf_bank_params p = params ? *params : default_params();
+    int rc = check_params(p);
+    if (rc) return rc;
+    for (int s = 0; s < n_seg; ++s)
+        if (seg_N[s] < 2 || !(seg_fs[s] > 0.0)) return set_err(MF_EINVAL, "segment %d: bad N or fs", s);
+    std::vector<double> prefix((size_t)n + 1, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(m1[i] > 0.0) || !(m2[i] > 0.0) || !isfinite(m1[i]) || !isfinite(m2[i]))
+            return set_err(MF_EINVAL, "template %lld: masses must be finite and > 0", (long long)i);
+        double r[kTmplStride];
+        template_constants(m1[i], m2[i], r);
+        double c = 0.0;
+        for (int s = 0; s < n_seg; ++s) {
+            const double N = (double)seg_N[s], fs = seg_fs[s];
+            const double fc = std::min(r[TF_FISCO], 0.5 * fs);
+            const int64_t lo = std::max((int64_t)1, (int64_t)ceil(p.f_low * N / fs));
+            const int64_t hi = std::min((int64_t)floor(fc * N / fs) + 1, seg_N[s] / 2);
+            c += 16.0 * N + 8.0 * (double)std::max<int64_t>(0, hi - lo);
+        }
+        prefix[(size_t)i + 1] = prefix[(size_t)i] + c;
+    }
+    const double total = prefix[(size_t)n];
+    starts[0] = 0;
+    for (int r = 1; r < parts; ++r) {
+        const double target = total * (double)r / (double)parts;
+        int64_t i = std::lower_bound(prefix.begin(), prefix.end(), target) - prefix.begin();
+        if (i > 0 && target - prefix[(size_t)i - 1] < prefix[(size_t)i] - target) --i;   // nearer boundary
+        const int64_t lo = starts[r - 1] + 1, hi = n - (parts - r);   // every part non-empty
+        starts[r] = std::min(std::max(i, lo), hi);
+    }
+    starts[parts] = n;
     return MF_OK;
 }
 
@@ -357,7 +421,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     double *q = nullptr, *btmp = nullptr, *psd_dev = nullptr;
     const int64_t nbt = prefix_block_tmp_count(half);
     cudaError_t e = cudaMalloc(&g->W, sizeof(float2) * half);
-    if (e == cudaSuccess) g->has_tmap = make_w_tensor_map(g->W, g->log2N, g->w_tmap);   // pass 1's TMA view of W
+    if (e == cudaSuccess) g->has_tmap = make_w_tensor_maps(g->W, g->log2N, g->w_tmap);   // pass 1's TMA view of W
     if (e == cudaSuccess) e = cudaMalloc(&g->fac, sizeof(float) * half);
     if (e == cudaSuccess) e = cudaMalloc(&g->P, sizeof(double) * (half + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->consts, sizeof(SegConsts));
@@ -529,6 +593,14 @@ static int ensure_workspace(mf_bank_s *b, int64_t exch_elems, int64_t cap, int64
 // on queue 1 (anchors + pass 1, about 60% of the work), the rest on queue 2.
 constexpr int kLA = 4, kS = 8, kSA = kLA + 4;
 constexpr double kSplit = 0.60;
+
+// Pass-1 form of a call: the bank's (autotuned) form unless MFGB_P1TILE=half
+// asks for the half-width tiles of the persistent form.
+static int p1_form(const mf_bank_s *b) {
+    const char *e = getenv("MFGB_P1TILE");
+    if (e && strcmp(e, "half") == 0) return 2;
+    return b->p1_kind;
+}
 
 // Pass 2 as whole rows per warp (row length 1024) unless MFGB_P2ROWS=0.
 static bool use_rows(const mf_bank_s *b, const mf_segment_s *g) {
@@ -795,7 +867,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             }
             pi = prof_begin(b, MF_STAGE_PASS1, by_band + by_anc + exch_bytes, st);
             MF_CUDA(launch_pass1(sd, w.units, u0, nb, lgD, man, w.anchors + aoff, w.anchors4 + aoff, w.exch,
-                                 b->params.phase_mode, b->d_tmpl, b->p1_kind == 0, w.status, b->spin_limit, st));
+                                 b->params.phase_mode, b->d_tmpl, p1_form(b), w.status, b->spin_limit, st));
             prof_end(b, pi, st);
             if (overlap && u0 + batch < n_t) {
                 const int u1 = u0 + (int)batch;
@@ -916,7 +988,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
         if (rows) {
             for (int l = 0; l <= p && e == cudaSuccess; ++l) {
                 e = launch_pass1(sd, units + (size_t)l * n, (int)u0, nb, lgD, man, anc, anc4,
-                                 exch + (size_t)l * nb * seg->N, b->params.phase_mode, b->d_tmpl, b->p1_kind == 0,
+                                 exch + (size_t)l * nb * seg->N, b->params.phase_mode, b->d_tmpl, p1_form(b),
                                  b->chi_status, b->spin_limit, st);
                 ++launches;
             }
@@ -929,7 +1001,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
         for (int l = 0; l <= p && e == cudaSuccess; ++l) {
             const UnitInfo *ul = units + (size_t)l * n;
             e = launch_pass1(sd, ul, (int)u0, nb, lgD, man, anc, anc4, exch, b->params.phase_mode, b->d_tmpl,
-                             b->p1_kind == 0, b->chi_status, b->spin_limit, st);
+                             p1_form(b), b->chi_status, b->spin_limit, st);
             if (e == cudaSuccess)
                 e = launch_chisq_pass2(sd, ul, (int)u0, nb, exch, chisq, l == p ? 2 : (l == 0 ? 0 : 1), p, st);
             launches += 2;
@@ -1111,6 +1183,7 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     for (int64_t mib : {128, 256, 512, 1024}) {
         cands.push_back({1, mib << 20, 0.60, 0, 0});
         if (any_pf) cands.push_back({1, mib << 20, 0.60, 1, 0});
+        if (any_pf) cands.push_back({1, mib << 20, 0.60, 2, 0});
         if (any_rows) cands.push_back({1, mib << 20, 0.60, 0, 1});
     }
     const int64_t cap = 1 << 16;
@@ -1166,7 +1239,9 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
                    "\"pass2\": \"%s\", \"candidates\": %d, \"ms_per_call\": %.4f}\n",
                 (long long)maxN, (long long)b->n, n_seg, best.sched == 0 ? "persistent" : "batch",
                 (long long)(ex >> 20), (long long)choose_batch(maxN, b->n, ex), best.split,
-                best.sched == 0 ? "fused" : (best.p1 == 0 ? "persistent-staged" : "per-tile"),
+                best.sched == 0 ? "fused"
+                                : (best.p1 == 0 ? "persistent-staged" : (best.p1 == 2 ? "persistent-staged-half-tile"
+                                                                                        : "per-tile")),
                 best.sched == 0 ? "fused" : (best.p2 == 0 ? "rows" : "per-tile"), (int)cands.size(), best_ms / repeats);
         fclose(f);
     }

@@ -31,7 +31,8 @@ struct SegDev {
     double fs, df;
     int64_t N;
     int log2N, log2N1, log2N2;   // N = N1 * N2, N2 = column (pass-1) length
-    const void *w_tmap = nullptr;   // host copy of a CUtensorMap over W for pass 1 (NULL: none)
+    const void *w_tmap = nullptr;   // host copies of two CUtensorMaps over W for pass 1, boxes of C and C/2
+                                    // columns (NULL: none)
 };
 
 // Per (template, segment) unit, computed on the device for each filter call.
@@ -144,10 +145,14 @@ cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double 
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0,
                            int n_units, int log2D, int max_anc, float4 *anchors, float *anchors4,
                            cudaStream_t st);
-// status / spin_limit: the persistent form's bounded wait on its W copies (bit 1 of *status on expiry)
+// p1_form: 0 the persistent form with staged inputs (tiles of C columns),
+// 1 one CTA per column tile, 2 the persistent form with tiles of C/2 columns
+// (the persistent form only where it applies; every form gives bit-identical
+// results).  status / spin_limit: the persistent form's bounded wait on its
+// input copies (bit 1 of *status on expiry).
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                          int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
-                         int phase_mode, const double *tmpl, bool allow_pf, int *status, long long spin_limit,
+                         int phase_mode, const double *tmpl, int p1_form, int *status, long long spin_limit,
                          cudaStream_t st);
 cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units,
                          const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
@@ -158,11 +163,12 @@ int pass2_blocks(int log2N);
 // launch_pass1 takes it where it applies
 bool pass1_pf_applies(int log2N, int log2D, int phase_mode);
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
-                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, int *status,
-                            long long spin_limit, cudaStream_t st);
-// tensor map over W (128 bytes at map_out) for the persistent pass 1; false if
-// it does not apply (N outside 2^16..2^21) or cannot be made
-bool make_w_tensor_map(const float2 *W, int log2N, void *map_out);
+                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, bool half_tile,
+                            int *status, long long spin_limit, cudaStream_t st);
+// the two tensor maps over W (2 x 128 bytes at maps_out: boxes of C and C/2
+// columns) for the persistent pass 1; false if it does not apply (N outside
+// 2^16..2^21) or they cannot be made
+bool make_w_tensor_maps(const float2 *W, int log2N, void *maps_out);
 cudaError_t pass1_pf_kernel_attributes();
 // pass 2 with whole rows per warp and bulk-copy prefetch (row length 1024 only)
 bool pass2_rows_applies(int log2N);

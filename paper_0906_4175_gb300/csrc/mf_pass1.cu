@@ -154,8 +154,10 @@ __device__ __forceinline__ void pf_issue(const Pass1PfParams &p, const CUtensorM
     }
 }
 
+// two CTAs per SM with tiles of C = 8192/L columns (256 threads); three with
+// half-width tiles (128 threads, half the column data and W staging)
 template <int L, int C, int LG1, bool TMA>
-__global__ void __launch_bounds__(C *(L / 32), 2)
+__global__ void __launch_bounds__(C *(L / 32), (C * (L / 32) >= 256) ? 2 : 3)
     k_pass1_pf(const Pass1PfParams p, const __grid_constant__ CUtensorMap wmap) {
     using S = FftShape<L>;
     static_assert(S::NST == 2, "two-stage column lengths only");
@@ -254,17 +256,36 @@ __global__ void __launch_bounds__(C *(L / 32), 2)
     }
 }
 
-int g_pf_blocks_per_sm[3] = {0, 0, 0};   // L = 256, 512, 1024
+// resident CTAs per SM of the persistent form: [L = 256, 512, 1024][tile C, C/2]
+int g_pf_blocks_per_sm[3][2] = {{0, 0}, {0, 0}, {0, 0}};
 int g_pf_sms = 0;
-int g_pf_tma = 1;
 
 template <int L>
 constexpr int pf_index() { return L == 256 ? 0 : (L == 512 ? 1 : 2); }
 
+template <int N2, int C, int LG1, bool TMA>
+cudaError_t pf_attrs(int &nb) {
+    constexpr int SM = (int)pf_smem_bytes<N2, C>();
+    cudaError_t e = cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pass1_pf<N2, C, LG1, TMA>, C * (N2 / 32), SM);
+    return e;
+}
+
+template <int N2, int N1, int C, bool TMA>
+cudaError_t pf_launch(const Pass1PfParams &p, const CUtensorMap &map, int n_units, int per_sm, cudaStream_t st) {
+    constexpr int LG1 = cx_ilog2(N1);
+    Pass1PfParams q = p;
+    q.n_items = n_units * (N1 / C);
+    const int grid = (int)std::min<int64_t>(q.n_items, (int64_t)per_sm * g_pf_sms);
+    k_pass1_pf<N2, C, LG1, TMA><<<grid, C * (N2 / 32), pf_smem_bytes<N2, C>(), st>>>(q, map);
+    return cudaGetLastError();
+}
+
 struct PfOp {
     const Pass1PfParams *p;
-    const CUtensorMap *wmap;   // NULL: cp.async staging of W
+    const CUtensorMap *wmaps;   // [2]: boxes of C and C/2 columns; NULL: cp.async staging of W
     int n_units;
+    bool half;                  // tiles of C/2 columns (with a tensor map only)
     cudaStream_t st;
     bool attrs = false;
     template <int N2, int N1>
@@ -272,35 +293,25 @@ struct PfOp {
         if constexpr (N2 >= 256 && N2 <= 1024) {
             constexpr int C = seqs_per_cta<N2>(N1);
             constexpr int LG1 = cx_ilog2(N1);
-            constexpr int SM = (int)pf_smem_bytes<N2, C>();
+            int *nb = g_pf_blocks_per_sm[pf_index<N2>()];
             if (attrs) {
-                cudaError_t e = cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, false>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SM);
+                int a = 0, b = 0, h = 0;
+                cudaError_t e = pf_attrs<N2, C, LG1, false>(a);
+                if (e == cudaSuccess) e = pf_attrs<N2, C, LG1, true>(b);
+                if (e == cudaSuccess) e = pf_attrs<N2, C / 2, LG1, true>(h);
                 if (e != cudaSuccess) return e;
-                int nb = 0, nb2 = 0;
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pass1_pf<N2, C, LG1, false>, C * (N2 / 32), SM);
-                if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_pass1_pf<N2, C, LG1, true>, C * (N2 / 32),
-                                                                      SM);
-                if (e != cudaSuccess) return e;
-                g_pf_blocks_per_sm[pf_index<N2>()] = std::min(nb, nb2);
+                nb[0] = std::min(a, b);
+                nb[1] = h;
                 return cudaSuccess;
             }
-            Pass1PfParams q = *p;
-            q.n_items = n_units * (N1 / C);
-            const int per_sm = g_pf_blocks_per_sm[pf_index<N2>()];
-            const int grid = (int)std::min<int64_t>(q.n_items, (int64_t)per_sm * g_pf_sms);
-            if (wmap != nullptr && g_pf_tma) {
-                k_pass1_pf<N2, C, LG1, true><<<grid, C * (N2 / 32), SM, st>>>(q, *wmap);
-            } else {
-                CUtensorMap none;
-                memset(&none, 0, sizeof(none));
-                k_pass1_pf<N2, C, LG1, false><<<grid, C * (N2 / 32), SM, st>>>(q, none);
+            const char *env = std::getenv("MFGB_P1TMA");   // "0": cp.async staging of W (comparisons)
+            if (wmaps != nullptr && !(env && env[0] == '0')) {
+                if (half && nb[1] >= 1) return pf_launch<N2, N1, C / 2, true>(*p, wmaps[1], n_units, nb[1], st);
+                return pf_launch<N2, N1, C, true>(*p, wmaps[0], n_units, nb[0], st);
             }
-            return cudaGetLastError();
+            CUtensorMap none;
+            memset(&none, 0, sizeof(none));
+            return pf_launch<N2, N1, C, false>(*p, none, n_units, nb[0], st);
         } else {
             return cudaErrorNotSupported;
         }
@@ -339,10 +350,10 @@ bool pass1_pf_applies(int log2N, int log2D, int phase_mode) {
     const int C = (8192 >> log2N2) < (1 << log2N1) ? (8192 >> log2N2) : (1 << log2N1);   // seqs_per_cta
     if ((1 << log2D) < C || log2D > log2N1) return false;
     const int idx = log2N2 == 8 ? 0 : (log2N2 == 9 ? 1 : 2);
-    return g_pf_blocks_per_sm[idx] >= 1;
+    return g_pf_blocks_per_sm[idx][0] >= 1;
 }
 
-bool make_w_tensor_map(const float2 *W, int log2N, void *map_out) {
+bool make_w_tensor_maps(const float2 *W, int log2N, void *maps_out) {
     if (log2N < 16 || log2N > 21 || W == nullptr || ((uintptr_t)W & 15u) != 0) return false;
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
@@ -351,20 +362,24 @@ bool make_w_tensor_map(const float2 *W, int log2N, void *map_out) {
     // W[k], k < N/2, as rows n (k = k1 + n N1) of N1 complex64 (8-byte elements)
     const cuuint64_t dims[2] = {(cuuint64_t)1 << log2N1, (cuuint64_t)1 << (log2N2 - 1)};
     const cuuint64_t strides[1] = {(cuuint64_t)sizeof(float2) << log2N1};
-    const cuuint32_t box[2] = {(cuuint32_t)C, (cuuint32_t)kBoxRows};
     const cuuint32_t estr[2] = {1, 1};
-    CUtensorMap *m = (CUtensorMap *)map_out;
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    CUtensorMap *m = (CUtensorMap *)maps_out;
+    for (int h = 0; h < 2; ++h) {   // boxes of C and C/2 columns x kBoxRows rows
+        const cuuint32_t box[2] = {(cuuint32_t)(C >> h), (cuuint32_t)kBoxRows};
+        if (fn(m + h, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)W, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
 }
 
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
-                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, int *status,
-                            long long spin_limit, cudaStream_t st) {
+                            int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, bool half_tile,
+                            int *status, long long spin_limit, cudaStream_t st) {
     if (n_units <= 0) return cudaSuccess;
     Pass1PfParams p{seg.W, units, anchors, anchors4, exch, max_anc, log2D, seg.log2N, unit0, 0, status, spin_limit};
-    PfOp op{&p, (const CUtensorMap *)seg.w_tmap, n_units, st};
+    PfOp op{&p, (const CUtensorMap *)seg.w_tmap, n_units, half_tile, st};
     return dispatch_split(seg.log2N, op);
 }
 
@@ -375,13 +390,9 @@ cudaError_t pass1_pf_kernel_attributes() {
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_pf_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    {
-        const char *v = std::getenv("MFGB_P1TMA");   // "0": cp.async staging of W (comparisons)
-        g_pf_tma = (v && v[0] == '0') ? 0 : 1;
-    }
     for (int lg = 16; lg <= 21; ++lg) {
         Pass1PfParams p{};
-        PfOp op{&p, nullptr, 0, nullptr, true};
+        PfOp op{&p, nullptr, 0, false, nullptr, true};
         if ((e = dispatch_split(lg, op)) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -161,6 +161,19 @@ def test_uneven_bank_pass1_kernels_agree(mf, uneven_data, monkeypatch):
     assert n_a == n_b
     assert np.array_equal(pk_a.view(np.uint8), pk_b.view(np.uint8))
     assert np.array_equal(tr_a.view(np.uint8), tr_b.view(np.uint8))
+    # the persistent form with half-width column tiles (three CTAs per SM)
+    monkeypatch.setenv("MFGB_P1TILE", "half")
+    _, pk_c, tr_c, n_c = _uneven_call(mf, wl, segs)
+    assert n_c == n_a
+    assert np.array_equal(pk_a.view(np.uint8), pk_c.view(np.uint8))
+    assert np.array_equal(tr_a.view(np.uint8), tr_c.view(np.uint8))
+    # and staging W by per-thread cp.async instead of TMA (the form without a tensor map)
+    monkeypatch.delenv("MFGB_P1TILE")
+    monkeypatch.setenv("MFGB_P1TMA", "0")
+    _, pk_d, tr_d, n_d = _uneven_call(mf, wl, segs)
+    assert n_d == n_a
+    assert np.array_equal(pk_a.view(np.uint8), pk_d.view(np.uint8))
+    assert np.array_equal(tr_a.view(np.uint8), tr_d.view(np.uint8))
 
 
 @pytest.mark.parametrize("sched", ["batch", "persistent"])
