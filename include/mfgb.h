@@ -285,19 +285,26 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
  * (the CTA tile), or one CTA per column tile; pass 2 in warp-owned rows
  * with bulk-copy prefetch, or one CTA per row tile) and keeps the fastest in
  * the bank for later calls (the default is per-batch launches with 1 GiB, the
- * staged pass 1 and the row pass 2 where they apply).  It
+ * staged pass 1 and the row pass 2 where they apply).  Before those it picks,
+ * per segment length N = 2^18 .. 2^21, the four-step split N = N1 x N2 of the
+ * per-batch schedule: the balanced one (N2 = 2^floor(log2 N / 2) columns) or
+ * an alternative (2^18: 1024 x 256, 2^19: 512 x 1024, 2^20: 2048 x 512,
+ * 2^21: 1024 x 2048 as N1 x N2), timing each on that length's segments.  It
  * runs each candidate 1 + repeats times on cuda_stream and synchronises; it
  * allocates temporary outputs and may grow the bank's workspace.  threshold
  * should be the one the search will use (it sets the trigger traffic).  If
  * cache_path is not NULL the choice is written there as one JSON line.
- * Results of mf_filter_bank do not depend on the schedule (bit-identical).
+ * Results of mf_filter_bank do not depend on the schedule, the kernel forms or
+ * the tile (bit-identical); a different split factors the FFT differently, so
+ * its results differ by rounding (within the FP32 path's rho bound).  The
+ * choice goes to the cache line as "n1_x_n2" per segment length.
  * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
 int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold, int repeats,
                 const char *cache_path, void *cuda_stream);
 
 /* Schedule overrides, read from the environment at every mf_filter_bank call
- * (for comparisons and tests; none changes a result, every combination is
- * bit-identical):
+ * (for comparisons and tests; none but MFGB_SPLIT_ALT changes a result, every
+ * other combination is bit-identical):
  *   MFGB_SCHED=batch|persistent  per-batch launches or the persistent
  *                                scheduler, over the bank's (autotuned) choice
  *   MFGB_BATCH=n                 templates per batch of the per-batch launches
@@ -309,6 +316,9 @@ int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold
  *                                columns (three CTAs per SM)
  *   MFGB_P1TMA=0                 the persistent pass 1 stages W with per-thread
  *                                cp.async instead of TMA
+ *   MFGB_SPLIT_ALT=1|0           per-batch schedule on the alternative split
+ *                                of 2^18..2^21 (see mf_autotune) or the
+ *                                balanced one (this one changes rounding)
  *   MFGB_P2ROWS=0                pass 2 one CTA per row tile instead of
  *                                warp-owned rows (FP32 FFT form only)
  *   MFGB_UNIT_ORDER=bank         templates in bank order instead of widest

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -185,6 +186,9 @@ struct mf_bank_s {
     // inputs (0), per tile (1), or persistent with tiles of half the width (2);
     // pass 2 in warp-owned rows (0) or per tile (1)
     int p1_kind = 0, p2_kind = 0;
+    // per segment length 2^i: the per-batch schedule uses the alternative
+    // split N = N1 * N2 (alt_log2n2) instead of the balanced one
+    unsigned char alt_split[23] = {0};
     int *chi_status = nullptr;        // status of the last mf_chisq_series (bit 2: a bounded wait ran out)
 };
 
@@ -219,8 +223,10 @@ struct mf_segment_s {
     float *fac = nullptr;          // a_k = alpha f^(-7/6) dt / S_k: W_k = a_k conj(X_k) for new samples
     float2 *r_exch = nullptr, *r_X = nullptr;
     float *r_s = nullptr;
-    alignas(64) unsigned char w_tmap[256];   // two CUtensorMaps over W for pass 1 (valid when has_tmap)
-    bool has_tmap = false;
+    // CUtensorMaps over W for pass 1 (boxes of C and C/2 columns), for the
+    // balanced split [0] and the alternative one [1] (valid when has_tmap[i])
+    alignas(64) unsigned char w_tmap[2][256];
+    bool has_tmap[2] = {false, false};
     void release() {
         cudaFree(W); cudaFree(P); cudaFree(consts); cudaFree(psd); cudaFree(fac);
         cudaFree(r_exch); cudaFree(r_X); cudaFree(r_s);
@@ -421,7 +427,10 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     double *q = nullptr, *btmp = nullptr, *psd_dev = nullptr;
     const int64_t nbt = prefix_block_tmp_count(half);
     cudaError_t e = cudaMalloc(&g->W, sizeof(float2) * half);
-    if (e == cudaSuccess) g->has_tmap = make_w_tensor_maps(g->W, g->log2N, g->w_tmap);   // pass 1's TMA view of W
+    if (e == cudaSuccess) {   // pass 1's TMA views of W, both splits
+        g->has_tmap[0] = make_w_tensor_maps(g->W, g->log2N, log2_n2(g->log2N), g->w_tmap[0]);
+        g->has_tmap[1] = alt_log2n2(g->log2N) > 0 && make_w_tensor_maps(g->W, g->log2N, alt_log2n2(g->log2N), g->w_tmap[1]);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&g->fac, sizeof(float) * half);
     if (e == cudaSuccess) e = cudaMalloc(&g->P, sizeof(double) * (half + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->consts, sizeof(SegConsts));
@@ -510,7 +519,9 @@ extern "C" int mf_segment_info(mf_segment g, int64_t *N, double *fs) {
     return MF_OK;
 }
 
-static SegDev seg_dev(const mf_segment_s *g) {
+// The segment as the kernels see it, with the split N = N1 * N2 (N2 =
+// 2^log2N2: the balanced split by default, or the alternative one).
+static SegDev seg_dev(const mf_segment_s *g, int log2N2 = -1) {
     SegDev d;
     d.W = g->W;
     d.P = g->P;
@@ -519,9 +530,10 @@ static SegDev seg_dev(const mf_segment_s *g) {
     d.df = g->fs / (double)g->N;
     d.N = g->N;
     d.log2N = g->log2N;
-    d.log2N2 = g->log2N / 2;
+    const int alt = (log2N2 >= 0 && log2N2 != log2_n2(g->log2N) && log2N2 == alt_log2n2(g->log2N)) ? 1 : 0;
+    d.log2N2 = alt ? log2N2 : log2_n2(g->log2N);
     d.log2N1 = g->log2N - d.log2N2;
-    d.w_tmap = g->has_tmap ? (const void *)g->w_tmap : nullptr;
+    d.w_tmap = g->has_tmap[alt] ? (const void *)g->w_tmap[alt] : nullptr;
     return d;
 }
 
@@ -602,13 +614,28 @@ static int p1_form(const mf_bank_s *b) {
     return b->p1_kind;
 }
 
-// Pass 2 as whole rows per warp (row length 1024) unless MFGB_P2ROWS=0.
-static bool use_rows(const mf_bank_s *b, const mf_segment_s *g) {
-    if (!pass2_rows_applies(g->log2N)) return false;
+// Pass 2 as whole rows per warp (row length 1024 or 2048) unless MFGB_P2ROWS=0.
+static bool use_rows(const mf_bank_s *b, const mf_segment_s *g, int log2N1) {
+    (void)g;
+    if (!pass2_rows_applies(log2N1)) return false;
     if (b->params.fft_mode != MF_FFT_FP32) return true;   // the tensor-core stage lives in the rows kernel
     if (b->p2_kind == 1) return false;
     const char *e = getenv("MFGB_P2ROWS");
     return !(e && strcmp(e, "0") == 0);
+}
+
+static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g);
+
+// Column-length exponent of the split the per-batch schedule uses for this
+// segment: the alternative split where the bank chose it (mf_autotune) or
+// MFGB_SPLIT_ALT=1 asks for it, else the balanced one.  The persistent
+// scheduler and the chi^2 paths use the balanced split.
+static int filter_log2n2(const mf_bank_s *b, const mf_segment_s *g) {
+    const int alt = alt_log2n2(g->log2N);
+    if (alt < 0 || use_persistent(b, g) || b->params.fft_mode != MF_FFT_FP32) return log2_n2(g->log2N);
+    const char *e = getenv("MFGB_SPLIT_ALT");
+    if (e) return e[0] == '1' ? alt : log2_n2(g->log2N);
+    return b->alt_split[g->log2N] ? alt : log2_n2(g->log2N);
 }
 
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
@@ -716,9 +743,10 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const int lgD = choose_log2D(b, segs[s]);
         exch_elems = std::max(exch_elems, bt * segs[s]->N);
         anc_elems = std::max(anc_elems, 2 * bt * (((segs[s]->N / 2) >> lgD) + 2));   // two batches in flight
-        nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N));
-        if (!use_persistent(b, segs[s]) && use_rows(b, segs[s]))   // one partial per row and warp
-            nblk = std::max(nblk, (int64_t)pass2_rows_partials(segs[s]->log2N));
+        const int lg2 = filter_log2n2(b, segs[s]);
+        nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N, lg2));
+        if (!use_persistent(b, segs[s]) && use_rows(b, segs[s], segs[s]->log2N - lg2))   // one partial per row and warp
+            nblk = std::max(nblk, (int64_t)pass2_rows_partials(segs[s]->log2N, lg2));
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool capturing = stream_capturing(st);
@@ -736,11 +764,11 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
     const int stall_pos =
         b->stall_unit < 0 ? -1 : (unit_order ? b->pos[(size_t)b->stall_unit] : (int)b->stall_unit);
     for (int s = 0; s < n_seg; ++s) {
-        const SegDev sd = seg_dev(segs[s]);
+        const SegDev sd = seg_dev(segs[s], filter_log2n2(b, segs[s]));
         const int lgD = choose_log2D(b, segs[s]);
         const int man = (int)anchor_slot_records(segs[s]->log2N, lgD);   // records per anchor slot
-        const bool rows = !use_persistent(b, segs[s]) && use_rows(b, segs[s]);
-        const int nbk = rows ? pass2_rows_partials(sd.log2N) : pass2_blocks(sd.log2N);
+        const bool rows = !use_persistent(b, segs[s]) && use_rows(b, segs[s], sd.log2N1);
+        const int nbk = rows ? pass2_rows_partials(sd.log2N, sd.log2N2) : pass2_blocks(sd.log2N, sd.log2N2);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
         // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
         std::vector<double> band_bytes, anc_bytes;
@@ -1177,8 +1205,9 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     bool any_pf = false, any_rows = false;
     for (int s = 0; s < n_seg; ++s) {
         const int lgD = choose_log2D(b, segs[s]);
-        any_pf = any_pf || pass1_pf_applies(segs[s]->log2N, lgD, b->params.phase_mode);
-        any_rows = any_rows || (pass2_rows_applies(segs[s]->log2N) && b->params.fft_mode == MF_FFT_FP32);
+        const int lg2 = log2_n2(segs[s]->log2N);
+        any_pf = any_pf || pass1_pf_applies(segs[s]->log2N, lg2, lgD, b->params.phase_mode);
+        any_rows = any_rows || (pass2_rows_applies(segs[s]->log2N - lg2) && b->params.fft_mode == MF_FFT_FP32);
     }
     for (int64_t mib : {128, 256, 512, 1024}) {
         cands.push_back({1, mib << 20, 0.60, 0, 0});
@@ -1196,6 +1225,54 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // time one configuration of the bank on these segments: 1 + repeats calls, ms per call
+    auto time_calls = [&](const mf_segment *sg, int ns, float &ms) -> int {
+        int r = mf_filter_bank(b, sg, ns, threshold, pk, tr, cap, nt, cuda_stream);   // warm-up, sizes workspace
+        if (r) return r;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < repeats && !r; ++k) r = mf_filter_bank(b, sg, ns, threshold, pk, tr, cap, nt, cuda_stream);
+        cudaEventRecord(e1, st);
+        if (r) return r;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return set_err(MF_ECUDA, "autotune timing");
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)repeats;
+        return MF_OK;
+    };
+    // 1. the four-step split per segment length, on the per-batch schedule with
+    // the default kernel forms: balanced N1 x N2 or the alternative split
+    const int saved_sched0 = b->sched, saved_p1 = b->p1_kind, saved_p2 = b->p2_kind;
+    b->sched = 1;
+    b->p1_kind = 0;
+    b->p2_kind = 0;
+    std::vector<int> lengths;
+    int rc0 = MF_OK;
+    for (int s = 0; s < n_seg && !rc0; ++s) {
+        const int lg = segs[s]->log2N;
+        if (alt_log2n2(lg) < 0 || std::find(lengths.begin(), lengths.end(), lg) != lengths.end()) continue;
+        if (b->params.fft_mode != MF_FFT_FP32) continue;
+        lengths.push_back(lg);
+        std::vector<mf_segment> sub;
+        for (int q = 0; q < n_seg; ++q)
+            if (segs[q]->log2N == lg) sub.push_back(segs[q]);
+        float ms_bal = 0.f, ms_alt = 0.f;
+        b->alt_split[lg] = 0;
+        rc0 = time_calls(sub.data(), (int)sub.size(), ms_bal);
+        if (rc0) break;
+        b->alt_split[lg] = 1;
+        rc0 = time_calls(sub.data(), (int)sub.size(), ms_alt);
+        b->alt_split[lg] = (rc0 == MF_OK && ms_alt < ms_bal) ? 1 : 0;
+    }
+    b->sched = saved_sched0;
+    b->p1_kind = saved_p1;
+    b->p2_kind = saved_p2;
+    if (rc0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(pk);
+        cudaFree(tr);
+        cudaFree(nt);
+        return rc0;
+    }
     const int saved_sched = b->sched;
     const int64_t saved_exch = b->tuned_exch;
     const double saved_split = b->split;
@@ -1208,15 +1285,9 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
         b->split = c.split;
         b->p1_kind = c.p1;
         b->p2_kind = c.p2;
-        rc = mf_filter_bank(b, segs, n_seg, threshold, pk, tr, cap, nt, cuda_stream);   // warm-up, sizes workspace
-        if (rc) break;
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < repeats && !rc; ++r) rc = mf_filter_bank(b, segs, n_seg, threshold, pk, tr, cap, nt, cuda_stream);
-        cudaEventRecord(e1, st);
-        if (rc) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_err(MF_ECUDA, "autotune timing"); break; }
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        rc = time_calls(segs, n_seg, ms);
+        if (rc) break;
         if (ms < best_ms) { best_ms = ms; best = c; }
     }
     cudaEventDestroy(e0);
@@ -1234,15 +1305,30 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
         FILE *f = fopen(cache_path, "w");
         if (!f) return set_err(MF_EINVAL, "cannot write %s", cache_path);
         const int64_t ex = best.exch > 0 ? best.exch : kExchBudget;
+        std::string sp = "{";
+        std::vector<int> all_lg;
+        for (int s = 0; s < n_seg; ++s)
+            if (std::find(all_lg.begin(), all_lg.end(), segs[s]->log2N) == all_lg.end()) all_lg.push_back(segs[s]->log2N);
+        std::sort(all_lg.begin(), all_lg.end());
+        for (size_t i = 0; i < all_lg.size(); ++i) {
+            const int lg = all_lg[i];
+            const int l2 = (best.sched == 1 && b->alt_split[lg] && alt_log2n2(lg) >= 0) ? alt_log2n2(lg) : log2_n2(lg);
+            char buf[96];
+            snprintf(buf, sizeof(buf), "%s\"%lld\": \"%lld x %lld\"", i ? ", " : "", (long long)1 << lg,
+                     (long long)1 << (lg - l2), (long long)1 << l2);
+            sp += buf;
+        }
+        sp += "}";
         fprintf(f, "{\"N\": %lld, \"templates\": %lld, \"segments\": %d, \"scheduler\": \"%s\", "
                    "\"exchange_mib\": %lld, \"batch_at_max_N\": %lld, \"split\": %.3f, \"pass1\": \"%s\", "
-                   "\"pass2\": \"%s\", \"candidates\": %d, \"ms_per_call\": %.4f}\n",
+                   "\"pass2\": \"%s\", \"n1_x_n2\": %s, \"candidates\": %d, \"ms_per_call\": %.4f}\n",
                 (long long)maxN, (long long)b->n, n_seg, best.sched == 0 ? "persistent" : "batch",
                 (long long)(ex >> 20), (long long)choose_batch(maxN, b->n, ex), best.split,
                 best.sched == 0 ? "fused"
                                 : (best.p1 == 0 ? "persistent-staged" : (best.p1 == 2 ? "persistent-staged-half-tile"
                                                                                         : "per-tile")),
-                best.sched == 0 ? "fused" : (best.p2 == 0 ? "rows" : "per-tile"), (int)cands.size(), best_ms / repeats);
+                best.sched == 0 ? "fused" : (best.p2 == 0 ? "rows" : "per-tile"), sp.c_str(),
+                (int)(cands.size() + 2 * lengths.size()), best_ms);
         fclose(f);
     }
     return MF_OK;

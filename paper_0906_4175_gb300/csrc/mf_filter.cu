@@ -161,23 +161,23 @@ struct AttrOp {
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D, int max_anc,
                          const float4 *anchors, const float *anchors4, float2 *exch, int phase_mode,
                          const double *tmpl, int p1_form, int *status, long long spin_limit, cudaStream_t st) {
-    if (p1_form != 1 && pass1_pf_applies(seg.log2N, log2D, phase_mode))
+    if (p1_form != 1 && pass1_pf_applies(seg.log2N, seg.log2N2, log2D, phase_mode))
         return launch_pass1_pf(seg, units, unit0, n_units, log2D, max_anc, anchors, anchors4, exch, p1_form == 2,
                                status, spin_limit, st);
     Pass1Op op{seg, units, unit0, n_units, log2D, max_anc, phase_mode, anchors, anchors4, exch, tmpl, st};
-    return dispatch_split(seg.log2N, op);
+    return dispatch_split2(seg.log2N, seg.log2N2, op);
 }
 
 cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                          float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                          unsigned long long *counter, int64_t cap, cudaStream_t st) {
     Pass2Op op{seg, units, unit0, n_units, exch, partials, seg_idx, kl, staged, keys, counter, cap, st};
-    return dispatch_split(seg.log2N, op);
+    return dispatch_split2(seg.log2N, seg.log2N2, op);
 }
 
-int pass2_blocks(int log2N) {
+int pass2_blocks(int log2N, int log2N2) {
     BlocksOp op;
-    dispatch_split(log2N, op);
+    dispatch_split2(log2N, log2N2, op);
     return op.nblk;
 }
 
@@ -189,6 +189,7 @@ cudaError_t filter_kernel_attributes() {
     for (int lg = 10; lg <= 22; ++lg) {
         AttrOp op;
         cudaError_t e = dispatch_split(lg, op);
+        if (e == cudaSuccess && alt_log2n2(lg) > 0) e = dispatch_split2(lg, alt_log2n2(lg), op);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -46,6 +46,24 @@ struct UnitInfo {
 };
 static_assert(sizeof(UnitInfo) == 32, "the persistent pass 1 reads the band fields as one int4");
 
+// Four-step split N = N1 * N2, N2 the column (pass-1) length: the balanced
+// one, N2 = 2^floor(log2 N / 2).
+__host__ __device__ inline int log2_n2(int log2N) { return log2N / 2; }
+
+// The filter's alternative split of N = 2^log2N (the autotuner's second
+// candidate): column length 2^alt_log2n2, or -1 where there is none.
+//   2^18: 256 x 1024 (balanced 512 x 512)     2^19: 1024 x 512 (512 x 1024)
+//   2^20: 512 x 2048 (1024 x 1024)            2^21: 2048 x 1024 (1024 x 2048)
+__host__ __device__ inline int alt_log2n2(int log2N) {
+    switch (log2N) {
+        case 18: return 8;
+        case 19: return 10;
+        case 20: return 9;
+        case 21: return 11;
+        default: return -1;
+    }
+}
+
 // Anchor slot layout.  A template's G = (N/2)/D anchor groups g (bins
 // [g D, g D + D)) are stored column-major over gs = max(1, N1/D) anchor
 // columns: g -> (g mod gs) R + g / gs with R = G / gs (= N2/2 when D <= N1).
@@ -158,21 +176,21 @@ cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, in
                          const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
                          mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
                          cudaStream_t st);
-int pass2_blocks(int log2N);
+int pass2_blocks(int log2N, int log2N2);   // pass-2 tiles per unit for the split N2 = 2^log2N2
 // pass 1 as a persistent kernel with cp.async staging of the next tile (mf_pass1.cu);
 // launch_pass1 takes it where it applies
-bool pass1_pf_applies(int log2N, int log2D, int phase_mode);
+bool pass1_pf_applies(int log2N, int log2N2, int log2D, int phase_mode);
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                             int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, bool half_tile,
                             int *status, long long spin_limit, cudaStream_t st);
 // the two tensor maps over W (2 x 128 bytes at maps_out: boxes of C and C/2
 // columns) for the persistent pass 1; false if it does not apply (N outside
 // 2^16..2^21) or they cannot be made
-bool make_w_tensor_maps(const float2 *W, int log2N, void *maps_out);
+bool make_w_tensor_maps(const float2 *W, int log2N, int log2N2, void *maps_out);
 cudaError_t pass1_pf_kernel_attributes();
 // pass 2 with whole rows per warp and bulk-copy prefetch (row length 1024 only)
-bool pass2_rows_applies(int log2N);
-int pass2_rows_partials(int log2N);
+bool pass2_rows_applies(int log2N1);                 // row length N1 = 2^log2N1
+int pass2_rows_partials(int log2N, int log2N2);        // partials per unit: one per row and warp
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,

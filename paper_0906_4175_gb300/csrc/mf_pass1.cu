@@ -341,23 +341,24 @@ EncodeTiledFn encode_tiled() {
 
 }  // namespace
 
-bool pass1_pf_applies(int log2N, int log2D, int phase_mode) {
+bool pass1_pf_applies(int log2N, int log2N2, int log2D, int phase_mode) {
     if (g_pf_sms <= 0 || phase_mode == MF_PHASE_FP32) return false;
     const char *env = std::getenv("MFGB_P1PF");   // "0": the per-tile kernel (comparisons)
     if (env && env[0] == '0') return false;
-    if (log2N < 16 || log2N > 21) return false;
-    const int log2N2 = log2_n2(log2N), log2N1 = log2N - log2N2;
+    if (log2N < 16 || log2N > 21 || log2N2 < 8 || log2N2 > 10) return false;
+    const int log2N1 = log2N - log2N2;
     const int C = (8192 >> log2N2) < (1 << log2N1) ? (8192 >> log2N2) : (1 << log2N1);   // seqs_per_cta
     if ((1 << log2D) < C || log2D > log2N1) return false;
     const int idx = log2N2 == 8 ? 0 : (log2N2 == 9 ? 1 : 2);
     return g_pf_blocks_per_sm[idx][0] >= 1;
 }
 
-bool make_w_tensor_maps(const float2 *W, int log2N, void *maps_out) {
-    if (log2N < 16 || log2N > 21 || W == nullptr || ((uintptr_t)W & 15u) != 0) return false;
+bool make_w_tensor_maps(const float2 *W, int log2N, int log2N2, void *maps_out) {
+    if (log2N < 16 || log2N > 21 || log2N2 < 8 || log2N2 > 10 || W == nullptr || ((uintptr_t)W & 15u) != 0)
+        return false;
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
-    const int log2N2 = log2_n2(log2N), log2N1 = log2N - log2N2;
+    const int log2N1 = log2N - log2N2;
     const int C = (8192 >> log2N2) < (1 << log2N1) ? (8192 >> log2N2) : (1 << log2N1);   // seqs_per_cta
     // W[k], k < N/2, as rows n (k = k1 + n N1) of N1 complex64 (8-byte elements)
     const cuuint64_t dims[2] = {(cuuint64_t)1 << log2N1, (cuuint64_t)1 << (log2N2 - 1)};
@@ -380,7 +381,7 @@ cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0,
     if (n_units <= 0) return cudaSuccess;
     Pass1PfParams p{seg.W, units, anchors, anchors4, exch, max_anc, log2D, seg.log2N, unit0, 0, status, spin_limit};
     PfOp op{&p, (const CUtensorMap *)seg.w_tmap, n_units, half_tile, st};
-    return dispatch_split(seg.log2N, op);
+    return dispatch_split2(seg.log2N, seg.log2N2, op);
 }
 
 cudaError_t pass1_pf_kernel_attributes() {
@@ -394,6 +395,8 @@ cudaError_t pass1_pf_kernel_attributes() {
         Pass1PfParams p{};
         PfOp op{&p, nullptr, 0, false, nullptr, true};
         if ((e = dispatch_split(lg, op)) != cudaSuccess) return e;
+        if (alt_log2n2(lg) >= 8 && alt_log2n2(lg) <= 10 && (e = dispatch_split2(lg, alt_log2n2(lg), op)) != cudaSuccess)
+            return e;
     }
     return cudaSuccess;
 }

@@ -79,7 +79,20 @@ cudaError_t dispatch_split(int log2N, Op &op) {
     }
 }
 
-__host__ __device__ inline int log2_n2(int log2N) { return log2N / 2; }
+// op.template run<N2, N1>() for the split N = N1 * N2 with N2 = 2^log2N2:
+// the balanced split of dispatch_split or the alternative one.
+template <class Op>
+cudaError_t dispatch_split2(int log2N, int log2N2, Op &op) {
+    if (log2N2 == log2_n2(log2N)) return dispatch_split(log2N, op);
+    if (log2N2 != alt_log2n2(log2N)) return cudaErrorInvalidValue;
+    switch (log2N) {
+        case 18: return op.template run<256, 1024>();
+        case 19: return op.template run<1024, 512>();
+        case 20: return op.template run<512, 2048>();
+        case 21: return op.template run<2048, 1024>();
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // Deferred release of a work counter by thread 0 (persistent scheduler): the
 // device-scope fence orders the block's writes of the previous item, which

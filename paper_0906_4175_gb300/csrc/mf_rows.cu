@@ -500,21 +500,18 @@ static size_t rows_smem() {
            (size_t)TwTable<L>::SIZE * sizeof(float2) + kWarps * sizeof(uint64_t);
 }
 
-bool pass2_rows_applies(int log2N) {
-    const int lg1 = log2N - log2_n2(log2N);
-    return lg1 == 10 || lg1 == 11;
-}
+bool pass2_rows_applies(int log2N1) { return log2N1 == 10 || log2N1 == 11; }
 
-int pass2_rows_partials(int log2N) {   // partials per unit: one per row and warp
-    const int lg1 = log2N - log2_n2(log2N);
-    return (1 << log2_n2(log2N)) * (lg1 == 11 ? 2 : 1);
+int pass2_rows_partials(int log2N, int log2N2) {   // partials per unit: one per row and warp
+    const int lg1 = log2N - log2N2;
+    return (1 << log2N2) * (lg1 == 11 ? 2 : 1);
 }
 
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,
                               int fft_mode, int stall_unit, cudaStream_t st) {
-    if (!pass2_rows_applies(seg.log2N)) return cudaErrorInvalidValue;
+    if (!pass2_rows_applies(seg.log2N1)) return cudaErrorInvalidValue;
     if (fft_mode != MF_FFT_FP32 && seg.log2N1 != 10) return cudaErrorInvalidValue;
     RowsParams p;
     p.exch = exch;

@@ -65,6 +65,23 @@ def test_sizes_full_series(mf, lg, fs):
     _full_compare(mf, wl.m1, wl.m2, wl.segments[0])
 
 
+@pytest.mark.parametrize("lg", [18, 19, 20, 21])
+def test_alternative_split_full_series(mf, monkeypatch, lg):
+    """The autotuner's alternative four-step split of N (2^18: 256 x 1024,
+    2^19: 1024 x 512, 2^20: 512 x 2048, 2^21: 2048 x 1024 columns x rows)
+    through every kernel form of the per-batch schedule: every rho_j and z
+    against the oracle."""
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    monkeypatch.setenv("MFGB_SPLIT_ALT", "1")
+    wl = workloads.small(seed=100 + lg, N=1 << lg, fs=4096.0, n_templates=2 if lg >= 20 else 3,
+                         m_lo=1.2, m_hi=9.0)
+    _full_compare(mf, wl.m1, wl.m2, wl.segments[0])
+    if lg <= 19:
+        monkeypatch.setenv("MFGB_P1PF", "0")   # per-tile pass 1 on the same split
+        monkeypatch.setenv("MFGB_P2ROWS", "0")
+        _full_compare(mf, wl.m1, wl.m2, wl.segments[0])
+
+
 def test_largest_segments_sampled(mf):
     """N = 2^21 and 2^22 (1024x2048, 2048x2048 splits), two templates each."""
     import torch
@@ -533,6 +550,7 @@ def test_autotune_keeps_results(mf, tmp_path):
     assert rec["scheduler"] in ("persistent", "batch") and rec["templates"] == 9
     assert rec["pass1"] in ("fused", "persistent-staged", "persistent-staged-half-tile", "per-tile")
     assert rec["pass2"] in ("fused", "rows", "per-tile")
+    assert rec["n1_x_n2"]["32768"] in ("256 x 128", "128 x 256")   # no alternative split below 2^18
     assert rec["candidates"] >= 7
     b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 4.0, trig_cap=1 << 16)]
     n = int(a[2][0])
