@@ -55,6 +55,8 @@ def _args():
                     help="use only the first T templates of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (MFGB_SCHED may force one)")
     ap.add_argument("--eager", action="store_true", help="time eager calls instead of CUDA-graph replays")
+    ap.add_argument("--conditioning", default="fp64", choices=["fp64", "fp32"],
+                    help="precision of the forward FFT of the per-step segment refresh (mf_segment_set_conditioning)")
     ap.add_argument("--fft-mode", default="fp32", choices=["fp32", "tc_fp16", "tc_bf16"],
                     help="FFT form of the scale workload: FP32 butterflies (the benchmark line) or the tensor-core "
                          "DFT stage of pass 2 with FP16 / BF16 splits (precision-sweep forms)")
@@ -951,6 +953,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # one segment handle: every step re-conditions the resident samples into it
     seg = mf.Segment(s_dev, spec.fs)
+    seg.set_conditioning(args.conditioning)
     seg.refresh(s_dev)
 
     def step():
@@ -1183,6 +1186,7 @@ def main():
                        "launch": launch_mode,
                        "conditioning": conditioning,
                        "schedule": schedule,
+                       "segment_fft": args.conditioning.upper() + " forward FFT in mf_segment_refresh",
                        "phase": "FP64 anchors + FP32 Taylor; FFT " + {
                            "fp32": "FP32", "tc_fp16": "FP32 but pass 2's first radix-32 stage on the tensor cores "
                            "(FP16 hi + lo splits)", "tc_bf16": "FP32 but pass 2's first radix-32 stage on the tensor "

@@ -151,11 +151,14 @@ int mf_bank_create_shard(const double *m1, const double *m2, int64_t n, const mf
  * psd: NULL -> Eq. (2) with f0 = psd_f0 and overall scale psd_S0 (the paper
  *      prints no scale; S0 = 1 gives whitened units, rho does not depend on it);
  *      else a host array of N/2+1 FP64 values S_k at f_k = k fs/N (> 0).
- * Queues on cuda_stream: the forward FFT s~_k = dt sum s_n e^{-2 pi i n k/N},
- * the weighting W_k = f_k^(-7/6) conj(s~_k)/S_k (scaled so that rho is O(1) for
- * any PSD scale) and the FP64 prefix table of f^(-7/3)/S_k that gives sigma^2
- * of Eq. (4) for any band in O(1).  *out owns that device memory.
- * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+ * Queues on cuda_stream: the forward FFT s~_k = dt sum s_n e^{-2 pi i n k/N}
+ * (in FP64, each bin then rounded to complex64: the round-off of the transform
+ * stays below 1e-16 of the data's total power, so a band far weaker than the
+ * data's content outside it, such as detector noise below f_low, keeps FP32
+ * precision), the weighting W_k = f_k^(-7/6) conj(s~_k)/S_k (scaled so that
+ * rho is O(1) for any PSD scale) and the FP64 prefix table of f^(-7/3)/S_k
+ * that gives sigma^2 of Eq. (4) for any band in O(1).  *out owns that device
+ * memory.  Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
 int mf_segment_upload(const float *s, int64_t N, double fs, const double *psd,
                       double psd_f0, double psd_S0, int s_on_device, void *cuda_stream,
                       mf_segment *out);
@@ -175,6 +178,18 @@ int mf_segment_destroy(mf_segment seg);
  * Errors: MF_EINVAL (NULL, wrong device, first call or host samples inside a
  * capture), MF_ENOMEM, MF_ECUDA. */
 int mf_segment_refresh(mf_segment seg, const float *s, int s_on_device, void *cuda_stream);
+
+/* Precision of the forward FFT in later mf_segment_refresh calls of a
+ * segment (mf_segment_upload always uses FP64):
+ *   MF_COND_FP64  default: as mf_segment_upload;
+ *   MF_COND_FP32  the library's FP32 four-step FFT, about a third of the time,
+ *                 with round-off proportional to the data's total power: for
+ *                 data whose power outside the band does not dwarf the band's
+ *                 (high-passed data).
+ * Host only.  Errors: MF_EINVAL (NULL segment, unknown mode). */
+#define MF_COND_FP64 0
+#define MF_COND_FP32 1
+int mf_segment_set_conditioning(mf_segment seg, int mode);
 /* Segment length and sample rate (host outs; either may be NULL). */
 int mf_segment_info(mf_segment seg, int64_t *N, double *fs);
 

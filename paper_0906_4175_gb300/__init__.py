@@ -149,6 +149,12 @@ class Segment:
     def handle(self):
         return self._h
 
+    def set_conditioning(self, mode: str):
+        """mf_segment_set_conditioning: 'fp64' (default) or 'fp32' forward FFT
+        in later refresh() calls."""
+        m = {"fp64": _native.MF_COND_FP64, "fp32": _native.MF_COND_FP32}[mode]
+        check(_native.lib().mf_segment_set_conditioning(self._h, m))
+
     def refresh(self, s, stream=None):
         """mf_segment_refresh: condition new samples (same N, fs and PSD) into
         this segment's device memory; capturable in a CUDA graph for device s

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libmfgb.so")
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ETIMEOUT, MF_ENOTSUP = range(7)
 MF_PHASE_ANCHOR, MF_PHASE_FP64, MF_PHASE_FP32 = 0, 1, 2
 MF_FFT_FP32, MF_FFT_TC_FP16, MF_FFT_TC_BF16 = 0, 1, 2
+MF_COND_FP64, MF_COND_FP32 = 0, 1
 _NAMES = {0: "MF_OK", 1: "MF_EINVAL", 2: "MF_ENOMEM", 3: "MF_ECUDA", 4: "MF_EOVERFLOW",
           5: "MF_ETIMEOUT", 6: "MF_ENOTSUP"}
 
@@ -38,6 +39,7 @@ SIGNATURES = {
     "mf_segment_upload": (_I, [_P, _I64, _D, _P, _D, _D, _I, _P, _P]),
     "mf_segment_destroy": (_I, [_P]),
     "mf_segment_refresh": (_I, [_P, _P, _I, _P]),
+    "mf_segment_set_conditioning": (_I, [_P, _I]),
     "mf_segment_info": (_I, [_P, _P, _P]),
     "mf_filter_bank": (_I, [_P, _P, _I, _F, _P, _P, _I64, _P, _P]),
     "mf_bank_check": (_I, [_P, _P]),

@@ -87,6 +87,7 @@ static int ensure_device_init() {
     MF_CUDA(chisq_kernel_attributes());
     MF_CUDA(rows_kernel_attributes());
     MF_CUDA(pass1_pf_kernel_attributes());
+    MF_CUDA(prep64_kernel_attributes());
     done.push_back(dev);
     return MF_OK;
 }
@@ -223,6 +224,7 @@ struct mf_segment_s {
     float *fac = nullptr;          // a_k = alpha f^(-7/6) dt / S_k: W_k = a_k conj(X_k) for new samples
     float2 *r_exch = nullptr, *r_X = nullptr;
     float *r_s = nullptr;
+    int cond = MF_COND_FP64;       // precision of the forward DFT in mf_segment_refresh
     // CUtensorMaps over W for pass 1 (boxes of C and C/2 columns), for the
     // balanced split [0] and the alternative one [1] (valid when has_tmap[i])
     alignas(64) unsigned char w_tmap[2][256];
@@ -449,11 +451,11 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
         psd_dev = g->psd;
     }
     const float *s_use = s_on_device ? s : s_dev;
-    if (e == cudaSuccess) e = launch_forward_fft(s_use, N, exch, X, st);
+    if (e == cudaSuccess) e = launch_forward_fft64(s_use, N, exch, X, st);   // exch: 8 N bytes = N/2 complex128
     if (e == cudaSuccess) e = launch_psd_weights(X, psd_dev, psd_f0, psd_S0, N, fs, q, st);
     if (e == cudaSuccess) e = launch_prefix_f64(q, half, g->P, btmp, st);
     if (e == cudaSuccess) e = launch_weight_data(X, psd_dev, psd_f0, psd_S0, N, fs, g->P, g->consts, g->W, g->fac, st);
-    if (e == cudaSuccess) count_launches(7);   // 2 FFT passes, weights, 3 scan kernels, weighting
+    if (e == cudaSuccess) count_launches(8);   // 3 FFT kernels, weights, 3 scan kernels, weighting
     if (s_dev) cudaFreeAsync(s_dev, st);
     if (exch) cudaFreeAsync(exch, st);
     if (X) cudaFreeAsync(X, st);
@@ -498,10 +500,23 @@ extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device,
         s_use = g->r_s;
     }
     // the PSD and with it P, sigma's normalisation and the factors a_k are unchanged
-    MF_CUDA(launch_forward_fft(s_use, N, g->r_exch, g->r_X, st));
+    if (g->cond == MF_COND_FP32) {
+        MF_CUDA(launch_forward_fft(s_use, N, g->r_exch, g->r_X, st));
+        count_launches(2);
+    } else {
+        MF_CUDA(launch_forward_fft64(s_use, N, g->r_exch, g->r_X, st));
+        count_launches(3);
+    }
     MF_CUDA(launch_apply_weights(g->r_X, g->fac, N, g->W, st));
-    count_launches(3);
+    count_launches(1);
     if (!s_on_device) MF_CUDA(cudaStreamSynchronize(st));   // host s consumed before return
+    return MF_OK;
+}
+
+extern "C" int mf_segment_set_conditioning(mf_segment g, int mode) {
+    if (!g) return set_err(MF_EINVAL, "NULL segment");
+    if (mode != MF_COND_FP64 && mode != MF_COND_FP32) return set_err(MF_EINVAL, "unknown conditioning mode %d", mode);
+    g->cond = mode;
     return MF_OK;
 }
 

@@ -137,6 +137,9 @@ struct PersistParams {
 
 // segment preparation (mf_prep.cu)
 cudaError_t launch_forward_fft(const float *s, int64_t N, float2 *exch, float2 *X, cudaStream_t st);
+// the same DFT in FP64 (mf_prep64.cu): scratch of N/2 complex128 (8 N bytes), three kernels
+cudaError_t launch_forward_fft64(const float *s, int64_t N, void *scratch, float2 *X, cudaStream_t st);
+cudaError_t prep64_kernel_attributes();
 // batch <= 65535 transforms of N points, x and y batch entries N apart, exch batch * N
 cudaError_t launch_fft_c2c(const float2 *x, float2 *y, int64_t N, int batch, int sign, float2 *exch,
                            cudaStream_t st);

@@ -241,10 +241,8 @@ def test_mixed_rates_and_f_low_one_call(mf, f_low):
     k_lo = ceil(f_low N / fs), f_cut = min(f_isco, fs/2), so the heavier
     templates end below Nyquist at 4096 Hz and the lighter ones are cut at
     Nyquist at 1024 Hz): every rho_j and z_j of every (template, segment)
-    against the oracle run at that f_low.  (Below about 28 Hz the Eq. 2 noise
-    between f_low and the seismic wall dominates the FP32 samples, and the
-    FP32 transforms' round-off, relative to that amplitude, reaches the 1e-4
-    bound: 1.2e-4 was seen at f_low = 25 Hz, fs = 1024 Hz.)"""
+    against the oracle run at that f_low.  (Data with content below f_low:
+    test_data_content_far_below_f_low.)"""
     import torch
     m1 = np.array([1.25, 1.6, 2.9, 4.8, 9.0, 1.4])
     m2 = np.array([1.2, 1.45, 2.1, 3.5, 7.5, 1.4])
@@ -271,6 +269,41 @@ def test_mixed_rates_and_f_low_one_call(mf, f_low):
             assert ez.max() <= RHO_TOL, (si, ti, float(ez.max()))
             jr = int(np.argmax(r["rho"]))
             assert peak_index_agrees(r["rho"], int(pk[ti, si]["j"]), jr), (si, ti)
+
+
+@pytest.mark.parametrize("f_noise,N,fs", [(20.0, 1 << 16, 4096.0), (15.0, 1 << 17, 2048.0)])
+def test_data_content_far_below_f_low(mf, f_noise, N, fs):
+    """Eq. (2)-coloured noise from f_noise = 15-20 Hz, below the filter's
+    f_low = 40 Hz: the seismic wall of Eq. (2) makes that content 10^5 - 10^8
+    times the in-band amplitude, yet every rho_j and z_j stays within the FP32
+    path's bound of the oracle (run on the same float32 samples) because the
+    segment's forward FFT runs in FP64.  The FP32 forward FFT (MF_COND_FP32
+    refresh) on the same samples misses the bound by orders of magnitude."""
+    import torch
+    m1 = np.array([1.3, 2.2, 5.0])
+    m2 = np.array([1.25, 1.9, 3.0])
+    inj = np.zeros(1, dtype=oracle.INJ_DTYPE)
+    inj[0] = (2.2, 1.9, 12.0, N // 3, 0.4)
+    spec = workloads.SegmentSpec(N, fs, int(f_noise) * 7 + 3, inj)
+    s32 = oracle.synth(spec.normals(), N, fs, f_noise, spec.injections).astype(np.float32)
+    s64 = s32.astype(np.float64)
+    bank = mf.Bank(m1, m2)
+    s_dev = torch.from_numpy(s32).cuda()
+    seg = mf.Segment(s_dev, fs)
+    rho_g, z_g, pk = gpu_rho_series(mf, bank, seg, len(m1), N)
+    ref = oracle_rho_series(m1, m2, s64, fs, 40.0)
+    errs = []
+    for t, r in enumerate(ref):
+        e = rho_err(rho_g[t], r["rho"])
+        assert e.max() <= RHO_TOL, (t, float(e.max()))
+        assert (np.abs(z_g[t] - r["z"]) / r["sigma"]).max() <= RHO_TOL
+        assert peak_index_agrees(r["rho"], int(pk["j"][t]), int(np.argmax(r["rho"])))
+        errs.append(float(e.max()))
+    seg.set_conditioning("fp32")
+    seg.refresh(s_dev)
+    rho_32, _, _ = gpu_rho_series(mf, bank, seg, len(m1), N)
+    e32 = max(float(rho_err(rho_32[t], r["rho"]).max()) for t, r in enumerate(ref))
+    assert e32 > 10 * RHO_TOL and e32 > 100 * max(errs), (e32, errs)
 
 
 @pytest.mark.parametrize("lg", [12, 20])
