@@ -402,6 +402,18 @@ int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *params, cons
 
 /* ---- measurement hooks (not part of the paper's method) ------------------ */
 
+/* mf_debug_status -- index checks of a debug build.  A library built with
+ * MFGB_DEBUG defined (paper_0906_4175_gb300/build.py --debug) range-checks the
+ * computed indices of the exchange stores and loads, the anchor reads and
+ * writes, the TMA and bulk copies, the row kernels, the persistent scheduler's
+ * decoded items and the trigger sort's scatter; a failed check skips the access
+ * and sets a bit: 1 exchange, 2 anchor record, 4 copy range, 8 row kernel,
+ * 16 persistent queue item, 32 sort scatter, 64 peaks / partials / trigger
+ * record.  Synchronises the device, ORs the bits set since the last call into
+ * *word (host) and clears them; *enabled (host, may be NULL) is 1 in a debug
+ * build, 0 otherwise (where *word is always 0).  Errors: MF_EINVAL, MF_ECUDA. */
+int mf_debug_status(uint32_t *word, int *enabled);
+
 /* Total number of kernels this library has launched in this process (host
  * counter, incremented at every launch on any stream). */
 int mf_launch_count(int64_t *n);

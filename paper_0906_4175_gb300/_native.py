@@ -13,7 +13,8 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libmfgb.so")
+# MFGB_DEBUG_LIB=1 loads the debug build (index checks, build.py --debug) instead
+LIB_PATH = os.path.join(_PKG, "_build_debug" if os.environ.get("MFGB_DEBUG_LIB") == "1" else "_build", "libmfgb.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ETIMEOUT, MF_ENOTSUP = range(7)
 MF_PHASE_ANCHOR, MF_PHASE_FP64, MF_PHASE_FP32 = 0, 1, 2
@@ -52,6 +53,7 @@ SIGNATURES = {
     "mf_refine_triggers_multi": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "mf_refine_triggers_static": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "mf_launch_count": (_I, [_P]),
+    "mf_debug_status": (_I, [_P, _P]),
     "mf_bank_profile": (_I, [_P, _I]),
     "mf_bank_profile_read": (_I, [_P, _P, _P, _P]),
     "mf_bank_debug_stall": (_I, [_P, _I64, _I64]),

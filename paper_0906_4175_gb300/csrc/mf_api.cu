@@ -1153,6 +1153,27 @@ extern "C" int mf_chisq_points(mf_bank b, const mf_segment *segs, int n_seg, con
     return MF_OK;
 }
 
+extern "C" int mf_debug_status(uint32_t *word, int *enabled) {
+    if (!word) return set_err(MF_EINVAL, "NULL argument");
+#ifdef MFGB_DEBUG
+    if (enabled) *enabled = 1;
+#else
+    if (enabled) *enabled = 0;
+#endif
+    int r0 = ensure_device_init();
+    if (r0) return r0;
+    MF_CUDA(cudaDeviceSynchronize());
+    unsigned all = 0, w = 0;
+    cudaError_t (*readers[])(unsigned *) = {dbg_read_filter, dbg_read_pass1, dbg_read_rows,
+                                            dbg_read_persist, dbg_read_chisq, dbg_read_prep};
+    for (auto rd : readers) {
+        MF_CUDA(rd(&w));
+        all |= w;
+    }
+    *word = all;
+    return MF_OK;
+}
+
 extern "C" int mf_bank_debug_stall(mf_bank b, int64_t unit, int64_t spin_limit) {
     if (!b) return set_err(MF_EINVAL, "NULL bank");
     if (unit >= b->n) return set_err(MF_EINVAL, "unit out of range");

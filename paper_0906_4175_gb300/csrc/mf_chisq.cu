@@ -246,6 +246,7 @@ __device__ __forceinline__ bool chi_withheld(const ChiRowsParams &p, int64_t r) 
 
 __device__ __forceinline__ const float2 *chi_row_src(const ChiRowsParams &p, int64_t r, int l) {
     const int64_t b = r >> p.log2N2, j2 = r & (((int64_t)1 << p.log2N2) - 1);
+    if (!MF_DBG(b < p.nb && l <= p.p && ((j2 + 1) << 10) <= ((int64_t)1 << p.log2N), kDbgRows)) return p.exch;
     return p.exch + (((int64_t)l * p.nb + b) << p.log2N) + (j2 << 10);
 }
 
@@ -386,6 +387,8 @@ cudaError_t launch_chisq_rows(const SegDev &seg, const float2 *exch, const UnitI
     k_chisq_rows<<<grid, kChiWarps * 32, chi_rows_smem_bytes(), st>>>(q);
     return cudaGetLastError();
 }
+
+MF_DEBUG_READER(dbg_read_chisq)
 
 cudaError_t chisq_kernel_attributes() {
     {

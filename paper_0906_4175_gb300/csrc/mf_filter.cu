@@ -65,6 +65,7 @@ __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const Uni
         const int64_t g = (int64_t)u.g_lo + i;
         anchor_record(c1, c2, c3, c5, g, log2D, seg.df, r, r4);
         const int64_t a = anchor_slot_index(g, seg.log2N, seg.log2N1, log2D);
+        if (!MF_DBG(a >= 0 && a < max_anc, kDbgAnchor)) continue;
         out[a] = r;
         out4[a] = r4;
     }
@@ -73,6 +74,8 @@ __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const Uni
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
+MF_DEBUG_READER(dbg_read_filter)
+
 cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double f_low, float thr, int log2D,
                          const int *order, UnitInfo *units, cudaStream_t st) {
     k_units<<<(n_t + 255) / 256, 256, 0, st>>>(seg, tmpl, n_t, f_low, thr, log2D, order, units);
@@ -227,7 +230,8 @@ __global__ void k_reduce_peaks(const UnitInfo *__restrict__ units, int n_units, 
         pk.j = bj;
         pk.z_re = bx * u.z_scale;
         pk.z_im = by * u.z_scale;
-        peaks[(int64_t)u.tmpl * n_seg + seg_idx] = pk;
+        if (MF_DBG(u.tmpl >= 0 && u.tmpl < n_units && seg_idx < n_seg, kDbgOut))
+            peaks[(int64_t)u.tmpl * n_seg + seg_idx] = pk;
     }
 }
 
@@ -409,6 +413,7 @@ __global__ void __launch_bounds__(kSortThreads)
         for (int r = 0; r < kSortRows; ++r) {
             if (dg[r] < 256u) {
                 const uint32_t pos = base[dg[r]] + whist[warp][dg[r]] + lr[r];
+                if (!MF_DBG(pos < (uint64_t)n, kDbgSort)) continue;
                 if (last) {
                     out[pos] = staged[id[r]];
                     if (perm_out) perm_out[pos] = id[r];

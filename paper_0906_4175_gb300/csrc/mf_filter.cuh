@@ -94,7 +94,8 @@ struct TemplateSrc {
             const float *acol4 = anc40 + ((int64_t)gcol << (LGL - 1));
             for (int n = threadIdx.x; n < L / 2; n += blockDim.x) {
                 const int a = gbase + n * gstep;
-                if (a >= 0 && a < u.n_anc) {
+                if (a >= 0 && a < u.n_anc &&
+                    MF_DBG(((int64_t)gcol << (LGL - 1)) + n < p.anc_stride, kDbgAnchor)) {
                     sa[n] = __ldcg(&acol[n]);   // anchors may be rewritten in the same launch (ring)
                     sa4[n] = __ldcg(&acol4[n]);
                 }
@@ -126,7 +127,8 @@ struct TemplateSrc {
                 const int k = k0 + ((r * T) << LG1);
                 const int kk = in[r] ? k : u.k_lo;
                 const int g = kk >> p.log2D;
-                const int64_t ai = anchor_slot_index(g, LGL + LG1, LG1, p.log2D);
+                int64_t ai = anchor_slot_index(g, LGL + LG1, LG1, p.log2D);
+                if (!MF_DBG(ai >= 0 && ai < p.anc_stride, kDbgAnchor)) ai = 0;
                 const float4 a = __ldcg(&anc0[ai]);
                 const float a4 = __ldcg(&anc40[ai]);
                 const float d = (float)(kk - ((g << p.log2D) + half));
@@ -258,7 +260,8 @@ struct RhoSink {
                 base = __shfl_sync(0xffffffffu, base, leader);
                 if (pred) {
                     const unsigned long long slot = base + (unsigned long long)__popc(msk & ((1u << lane) - 1u));
-                    if (slot < (unsigned long long)p.cap) {
+                    if (slot < (unsigned long long)p.cap &&
+                        MF_DBG(j2 + ((b + r * stride) << p.log2N2) < (1 << p.kl.j_bits), kDbgOut)) {
                         const int j = j2 + ((b + r * stride) << p.log2N2);
                         mf_trigger tr;
                         tr.tmpl = u.tmpl;

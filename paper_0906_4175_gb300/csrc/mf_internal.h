@@ -85,6 +85,51 @@ __host__ __device__ __forceinline__ int64_t anchor_slot_records(int log2N, int l
     return (int64_t)1 << (log2N - 1 - log2D);
 }
 
+// Debug builds (nvcc -DMFGB_DEBUG, build.py --debug): the computed indices of
+// the exchange stores and loads, the anchor reads and writes, the bulk and TMA
+// copies, the row kernels, the persistent queues and the trigger-sort scatter
+// are range-checked; a failed check sets its bit in the translation unit's
+// status word and the access is skipped.  mf_debug_status reads and clears the
+// words.  Release builds compile the checks away.
+enum DbgBit : unsigned {
+    kDbgExch = 1u,      // exchange index outside the batch slot
+    kDbgAnchor = 2u,    // anchor record outside the slot
+    kDbgCopy = 4u,      // bulk / TMA copy range outside its source or destination
+    kDbgRows = 8u,      // row kernel: row, partial or region index
+    kDbgQueue = 16u,    // persistent scheduler: decoded item outside its queue
+    kDbgSort = 32u,     // trigger sort: scatter position outside the key count
+    kDbgOut = 64u,      // peaks, partials or trigger records outside their arrays
+};
+#ifdef MFGB_DEBUG
+static __device__ unsigned g_dbg_word;
+__device__ __forceinline__ bool mf_dbg_ok(bool c, unsigned bit) {
+    if (!c) atomicOr(&g_dbg_word, bit);
+    return c;
+}
+#define MF_DBG(cond, bit) mf_dbg_ok((cond), (bit))
+#define MF_DEBUG_READER(name)                                                           \
+    cudaError_t name(unsigned *w) {                                                     \
+        unsigned z = 0;                                                                 \
+        cudaError_t e = cudaMemcpyFromSymbol(w, g_dbg_word, sizeof(unsigned));          \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_word, &z, sizeof(unsigned)); \
+        return e;                                                                       \
+    }
+#else
+#define MF_DBG(cond, bit) true
+#define MF_DEBUG_READER(name)         \
+    cudaError_t name(unsigned *w) {   \
+        *w = 0;                       \
+        return cudaSuccess;           \
+    }
+#endif
+// the status word of each translation unit that launches kernels
+cudaError_t dbg_read_filter(unsigned *w);
+cudaError_t dbg_read_pass1(unsigned *w);
+cudaError_t dbg_read_rows(unsigned *w);
+cudaError_t dbg_read_persist(unsigned *w);
+cudaError_t dbg_read_chisq(unsigned *w);
+cudaError_t dbg_read_prep(unsigned *w);
+
 // Stable trigger keys: (tmpl, seg, j) packed into 64 bits.
 struct KeyLayout {
     int j_bits, seg_bits, tmpl_bits;

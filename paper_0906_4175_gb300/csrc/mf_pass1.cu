@@ -120,7 +120,9 @@ __device__ __forceinline__ void pf_issue(const Pass1PfParams &p, const CUtensorM
             const int n_lo = lo_num <= 0 ? 0 : (lo_num + (1 << LG1) - 1) >> LG1;
             const int n_hi = hi_num <= 0 ? 0 : min(L / 2, (hi_num + (1 << LG1) - 1) >> LG1);
             fence_proxy_async();
-            if (n_hi > n_lo) {
+            const bool in_range = MF_DBG(kc + C <= (1 << LG1) && ((int64_t)(gcol + 1) << (cx_ilog2(L) - 1)) <= p.anc_stride,
+                                         kDbgCopy);
+            if (n_hi > n_lo && in_range) {
                 const int b0 = n_lo / kBoxRows, b1 = (n_hi + kBoxRows - 1) / kBoxRows;
                 const int a0 = n_lo & ~3, a1 = (n_hi + 3) & ~3;   // 16-byte runs of the FP32 q4 terms
                 mbar_expect_tx(bar, (uint32_t)((b1 - b0) * kBoxRows * C * sizeof(float2) +
@@ -145,7 +147,7 @@ __device__ __forceinline__ void pf_issue(const Pass1PfParams &p, const CUtensorM
         const int gbase = gcol - g_lo;
         for (int n = threadIdx.x; n < L / 2; n += NT) {
             const int a = gbase + n * gstep;
-            if (a >= 0 && a < n_anc) {
+            if (a >= 0 && a < n_anc && MF_DBG(((int64_t)gcol << (cx_ilog2(L) - 1)) + n < p.anc_stride, kDbgAnchor)) {
                 cp_async16(abuf + n, acol + n);
                 cp_async4(abuf4 + n, acol4 + n);
             }
@@ -340,6 +342,8 @@ EncodeTiledFn encode_tiled() {
 }
 
 }  // namespace
+
+MF_DEBUG_READER(dbg_read_pass1)
 
 bool pass1_pf_applies(int log2N, int log2N2, int log2D, int phase_mode) {
     if (g_pf_sms <= 0 || phase_mode == MF_PHASE_FP32) return false;

@@ -157,6 +157,7 @@ struct ExchSink {
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
         const int k1 = tile * C + seq;
         float2 *E = p.E + ((int64_t)slot << p.log2N) + ((int64_t)b << LG1) + k1;   // row j2 = b
+        if (!MF_DBG(k1 < (1 << LG1) && b + (R - 1) * stride < (1 << (p.log2N - LG1)), kDbgExch)) return;
         float2 w = unit_root<SIGN>((uint32_t)(b * k1), p.log2N);
         const float2 step = unit_root<SIGN>((uint32_t)(stride * k1), p.log2N);
 #pragma unroll
@@ -186,6 +187,7 @@ struct RowSrc {
         const int j2 = tile * C + seq;
         const float2 *row = E + ((int64_t)j2 << p.log2N1);
         constexpr int T = L / 32;
+        if (!MF_DBG(j2 < (1 << (p.log2N - p.log2N1)) && p.log2N1 == cx_ilog2(L), kDbgExch)) row = E;
 #pragma unroll
         for (int r = 0; r < 32; ++r) v[r] = __ldcg(&row[t + r * T]);
         release_hook(rel);

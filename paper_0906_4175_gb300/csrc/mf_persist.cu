@@ -110,6 +110,7 @@ __device__ __noinline__ void persist_anchors(const PersistParams &P, int u, int 
         const int64_t g = (int64_t)ui.g_lo + i;
         anchor_record(c1, c2, c3, c5, g, P.log2D, P.seg.df, r, r4);
         const int64_t a = anchor_slot_index(g, P.seg.log2N, P.seg.log2N1, P.log2D);
+        if (!MF_DBG(a >= 0 && a < P.max_anc, kDbgAnchor)) continue;
         out[a] = r;
         out4[a] = r4;
     }
@@ -236,6 +237,12 @@ __global__ void __launch_bounds__(256, 2)
                 break;
             }
             const int u = d.x, phase = d.y, tile = d.z;
+            if (!MF_DBG(u >= 0 && (int64_t)u * n2 < P.n_items2 &&
+                            tile >= 0 && tile < (phase == kItemA ? P.nA : (phase == kItemP1 ? n1 : n2)),
+                        kDbgQueue)) {
+                aborted = true;   // a decoding error: stop the block (the debug word reports it)
+                break;
+            }
             // look-ahead (thread 0)
             unsigned nv0 = 0u, nv1 = 0u, nab = 0u;
             int qn2 = 0;
@@ -357,6 +364,8 @@ struct TilesOp {
 };
 int g_blocks_per_sm[32];
 }  // namespace
+
+MF_DEBUG_READER(dbg_read_persist)
 
 cudaError_t persist_kernel_attributes() {
     {

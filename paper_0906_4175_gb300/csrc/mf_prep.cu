@@ -155,6 +155,8 @@ static int ilog2_i64(int64_t n) {
     return r;
 }
 
+MF_DEBUG_READER(dbg_read_prep)
+
 cudaError_t launch_forward_fft(const float *s, int64_t N, float2 *exch, float2 *X, cudaStream_t st) {
     FwdOp op{s, exch, X, ilog2_i64(N), st};
     return dispatch_split(op.log2N, op);

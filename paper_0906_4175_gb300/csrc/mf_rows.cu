@@ -155,6 +155,8 @@ template <int L>
 __device__ __forceinline__ const float2 *row_src(const RowsParams &p, int64_t r) {
     const int64_t n2 = (int64_t)1 << p.log2N2;
     const int64_t slot = r >> p.log2N2, j2 = r & (n2 - 1);
+    if (!MF_DBG(slot < p.n_units && r >= 0 && (j2 + 1) * L <= ((int64_t)1 << p.log2N), kDbgRows))
+        return p.exch;   // a valid row, so the copy stays inside the exchange
     return p.exch + (slot << p.log2N) + j2 * L;
 }
 
@@ -233,7 +235,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
             stockham_stage<L, S::R2, 32 * S::R1, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(
                 region, tw + TwTable<L>::S1, 0, t, snk);
         }
-        snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + wig]);
+        if (MF_DBG(slot < p.n_units && j2 < (1 << p.log2N2), kDbgRows))
+            snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + wig]);
     }
 }
 
@@ -499,6 +502,8 @@ static size_t rows_smem() {
     return (size_t)(kWarps / (L / 1024)) * FftShape<L>::STRIDE * sizeof(float2) +
            (size_t)TwTable<L>::SIZE * sizeof(float2) + kWarps * sizeof(uint64_t);
 }
+
+MF_DEBUG_READER(dbg_read_rows)
 
 bool pass2_rows_applies(int log2N1) { return log2N1 == 10 || log2N1 == 11; }
 
