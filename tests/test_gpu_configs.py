@@ -14,7 +14,8 @@ import pytest
 
 import oracle
 import workloads
-from mfgb_testutil import RHO_TOL, oracle_segment, peak_index_agrees, rho_err, trigger_sets_agree
+from mfgb_testutil import (REF_GRAD_ATOL, REF_GRAD_RTOL, REF_OBJ_TOL, RHO_TOL, oracle_segment, peak_index_agrees,
+                           rho_err, trigger_sets_agree)
 
 pytestmark = pytest.mark.gpu
 
@@ -320,9 +321,9 @@ def test_refinement_of_coarse_triggers(mf):
         thn = th.cpu().numpy()
         lo_hi = [oracle.band(N, fs, 40.0, oracle.f_isco(a, b)) for a, b, _ in thn]
         ref_obj, ref_grad = oracle.refine(thn, s64, fs, 40.0, bands=np.array(lo_hi))
-        assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < 2e-4), (obj, ref_obj)
+        assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < REF_OBJ_TOL), (obj, ref_obj)
         gs = np.abs(ref_grad).max(axis=0)
-        assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * gs)
+        assert np.all(np.abs(grad - ref_grad) <= REF_GRAD_RTOL * np.abs(ref_grad) + REF_GRAD_ATOL * gs)
         assert np.all(np.sqrt(obj) >= rho0 * (1 - 1e-4)), (np.sqrt(obj), rho0)
 
 

@@ -10,8 +10,8 @@ import pytest
 
 import oracle
 import workloads
-from mfgb_testutil import (RHO_TOL, gpu_rho_series, oracle_rho_series, oracle_segment, peak_index_agrees,
-                           rho_err, trigger_sets_agree)
+from mfgb_testutil import (REF_GRAD_ATOL, REF_GRAD_RTOL, REF_OBJ_TOL, RHO_TOL, gpu_rho_series, oracle_rho_series,
+                           oracle_segment, peak_index_agrees, rho_err, trigger_sets_agree)
 
 pytestmark = pytest.mark.gpu
 
@@ -448,8 +448,9 @@ def test_refine_matches_oracle(mf, lg, fs, f_low):
         obj, grad = mf.refine(seg, th, f_low=f_low, phase_mode=mode)
         obj = obj.cpu().numpy()
         grad = grad.cpu().numpy()
-        assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < 2e-4), (mode, obj, ref_obj)
-        assert np.all(np.abs(grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * scale), (mode, grad, ref_grad)
+        assert np.all(np.abs(obj - ref_obj) / np.maximum(ref_obj, 1.0) < REF_OBJ_TOL), (mode, obj, ref_obj)
+        assert np.all(np.abs(grad - ref_grad) <= REF_GRAD_RTOL * np.abs(ref_grad) + REF_GRAD_ATOL * scale), (
+            mode, grad, ref_grad)
     # explicit band gives the same as the default band at the same masses
     band = torch.tensor(np.array(lo_hi), dtype=torch.int64, device="cuda")
     obj2, grad2 = mf.refine(seg, th, band=band, f_low=f_low)

@@ -16,11 +16,10 @@ import pytest
 
 import oracle
 import workloads
-from mfgb_testutil import oracle_segment
+from mfgb_testutil import REF_GRAD_ATOL, REF_GRAD_RTOL, REF_OBJ_TOL, oracle_segment
 
 pytestmark = pytest.mark.gpu
 
-OBJ_TOL = 2e-4   # relative, as in the refinement parity test
 MAX_ROWS = 4096  # the entry point's fixed scratch holds this many rows
 
 CU_MEMPOOL_ATTR_USED_MEM_CURRENT = 7
@@ -106,9 +105,9 @@ def _theta(rng, n, t0, fs):
 
 def _assert_close(got_obj, got_grad, ref_obj, ref_grad):
     assert np.all(np.isfinite(got_obj)) and np.all(np.isfinite(got_grad))
-    assert np.all(np.abs(got_obj - ref_obj) <= OBJ_TOL * np.maximum(np.abs(ref_obj), 1.0))
+    assert np.all(np.abs(got_obj - ref_obj) <= REF_OBJ_TOL * np.maximum(np.abs(ref_obj), 1.0))
     scale = np.abs(ref_grad).max(axis=0)
-    assert np.all(np.abs(got_grad - ref_grad) <= 2e-3 * np.abs(ref_grad) + 1e-4 * scale)
+    assert np.all(np.abs(got_grad - ref_grad) <= REF_GRAD_RTOL * np.abs(ref_grad) + REF_GRAD_ATOL * scale)
 
 
 def test_static_refine_matches_allocating_refine_and_oracle_twice(mf):
