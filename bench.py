@@ -39,7 +39,11 @@ UNIT = "templates/s"
 WORKLOAD = "1024 templates (32x32 lattice, m1,m2 in [1,3] Msun), 1 segment N=2^20 at 4096 Hz, 8 injections, thr 6"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu", "mf_rows.cu", "mf_pass1.cu", "mf_internal.h"]
+KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu", "mf_rows.cu", "mf_pass1.cu",
+                  "mf_internal.h", "mf_async.cuh"]
+# the sources each profiled stage's kernel is built from (its ncu figures stay valid while they do not change)
+STAGE_SOURCES = {"pass1": ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_pass1.cu", "mf_async.cuh"],
+                 "pass2": ["mf_fft.cuh", "mf_filter.cuh", "mf_rows.cu", "mf_async.cuh"]}
 
 
 def _args():
@@ -98,9 +102,9 @@ def _hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (files or KERNEL_SOURCES):
         with open(os.path.join(ROOT, "paper_0906_4175_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -114,7 +118,7 @@ def _ncu_traffic(kernel_stage: str):
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(kernel_stage)
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(STAGE_SOURCES.get(kernel_stage)):
             return float(e["dram_bytes_per_launch"]), float(e.get("templates_per_launch", 0)) or None
     except Exception:
         pass
