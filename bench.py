@@ -42,8 +42,9 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_persist.cu", "mf_rows.cu", "mf_pass1.cu",
                   "mf_internal.h", "mf_async.cuh"]
 # the sources each profiled stage's kernel is built from (its ncu figures stay valid while they do not change)
-STAGE_SOURCES = {"pass1": ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_pass1.cu", "mf_async.cuh"],
-                 "pass2": ["mf_fft.cuh", "mf_filter.cuh", "mf_rows.cu", "mf_async.cuh"]}
+STAGE_SOURCES = {"pass1": ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_pass1.cuh", "mf_pass1.cu",
+                           "mf_async.cuh"],
+                 "pass2": ["mf_fft.cuh", "mf_filter.cuh", "mf_rows.cuh", "mf_rows.cu", "mf_async.cuh"]}
 
 
 def _args():
@@ -304,8 +305,9 @@ def run_uneven(args, mf, torch, dev):
     """4096 templates (m1, m2 in [1, 34], M <= 35, each cut at its own ISCO
     frequency) over 8 segments of 2^18, 2^18, 2^19, 2^19, 2^20, 2^20, 2^21,
     2^21 samples in one mf_filter_bank call: the per-segment persistent
-    launches as one CUDA graph, the per-batch launches, per-template
-    launches, and the autotuner's choice."""
+    launches as one CUDA graph, the per-batch launches, the fused scheduler
+    (2^19 and 2^20 segments; the others per batch), per-template launches,
+    and the autotuner's choice."""
     import workloads
     wl = workloads.uneven(0)
     segs = [mf.Segment(mf.synth_segment(sp.normals(), sp.N, sp.fs, wl.f_low, sp.injections), sp.fs)
@@ -324,6 +326,7 @@ def run_uneven(args, mf, torch, dev):
     res = {}
     # units run widest band first by default; the *_bank_order runs keep bank order for comparison
     for name, env in (("persistent_graph", {"MFGB_SCHED": "persistent"}), ("batch_graph", {"MFGB_SCHED": "batch"}),
+                      ("fused_graph", {"MFGB_SCHED": "fused"}),
                       ("persistent_graph_bank_order", {"MFGB_SCHED": "persistent", "MFGB_UNIT_ORDER": "bank"}),
                       ("batch_graph_bank_order", {"MFGB_SCHED": "batch", "MFGB_UNIT_ORDER": "bank"}),
                       ("per_template_eager", {"MFGB_SCHED": "batch", "MFGB_BATCH": "1"})):

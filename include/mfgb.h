@@ -292,7 +292,9 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
 
 /* mf_autotune -- times the candidate schedules of mf_filter_bank for this
  * bank on these segments (the persistent scheduler with 55/60/65% of the SMs
- * starting on template generation + column FFTs, and per-batch launches with
+ * starting on template generation + column FFTs; where some segment is
+ * N = 2^19 or 2^20, the fused scheduler with 55/60/65% of the SMs on pass 1;
+ * and per-batch launches with
  * 128 MiB..1 GiB of exchange in flight, i.e. 16..128 templates per batch at
  * N = 2^20 and proportionally more at shorter segments, each with the kernel
  * forms of the two passes: pass 1 persistent with the next tile's inputs
@@ -320,11 +322,19 @@ int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold
 /* Schedule overrides, read from the environment at every mf_filter_bank call
  * (for comparisons and tests; none but MFGB_SPLIT_ALT changes a result, every
  * other combination is bit-identical):
- *   MFGB_SCHED=batch|persistent  per-batch launches or the persistent
- *                                scheduler, over the bank's (autotuned) choice
+ *   MFGB_SCHED=batch|persistent|fused
+ *                                per-batch launches, the persistent scheduler,
+ *                                or the fused scheduler (N = 2^19, 2^20 with
+ *                                the FP64-anchor phase and FP32 FFT: after
+ *                                one anchor launch, the staged pass 1 and the
+ *                                row pass 2 in one launch, exchanging through
+ *                                a ring of 64 MiB that stays in L2; other
+ *                                segments per batch),
+ *                                over the bank's (autotuned) choice
  *   MFGB_BATCH=n                 templates per batch of the per-batch launches
  *   MFGB_SPLIT=x                 fraction of the SMs the persistent scheduler
- *                                starts on queue 1 (anchors + pass 1)
+ *                                starts on queue 1 (anchors + pass 1), or the
+ *                                fused scheduler gives to pass 1
  *   MFGB_P1PF=0                  pass 1 one CTA per column tile instead of the
  *                                persistent kernel with staged inputs
  *   MFGB_P1TILE=half             the persistent pass 1 with tiles of half the
@@ -424,7 +434,7 @@ int mf_launch_count(int64_t *n);
 #define MF_STAGE_PASS1   2  /* template generation + weighting + column IFFTs */
 #define MF_STAGE_PASS2   3  /* row IFFTs + rho epilogue */
 #define MF_STAGE_FINAL   4  /* peak reduction + trigger sort */
-#define MF_STAGE_FUSED   5  /* persistent scheduler: anchors + pass 1 + pass 2 + peaks in one launch */
+#define MF_STAGE_FUSED   5  /* persistent scheduler (anchors + pass 1 + pass 2 + peaks) or fused (pass 1 + pass 2) in one launch */
 #define MF_N_STAGES      6
 
 /* mf_bank_profile -- when on != 0, later mf_filter_bank calls on this bank

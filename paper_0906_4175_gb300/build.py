@@ -18,8 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmfgb.so")
 BUILD_DEBUG = os.path.join(PKG, "_build_debug")
-SOURCES = ["mf_filter.cu", "mf_persist.cu", "mf_prep.cu", "mf_synth.cu", "mf_refine.cu", "mf_chisq.cu", "mf_events.cu", "mf_rows.cu", "mf_pass1.cu", "mf_prep64.cu", "mf_api.cu"]
-HEADERS = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_internal.h", "mf_tmpl.cuh", "mf_async.cuh"]
+SOURCES = ["mf_filter.cu", "mf_persist.cu", "mf_prep.cu", "mf_synth.cu", "mf_refine.cu", "mf_chisq.cu", "mf_events.cu", "mf_rows.cu", "mf_pass1.cu", "mf_prep64.cu", "mf_fused.cu", "mf_api.cu"]
+HEADERS = ["mf_fft.cuh", "mf_passes.cuh", "mf_filter.cuh", "mf_internal.h", "mf_tmpl.cuh", "mf_async.cuh", "mf_pass1.cuh", "mf_rows.cuh"]
 
 
 def _cuda_home() -> str:

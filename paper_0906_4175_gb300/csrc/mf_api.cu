@@ -88,6 +88,7 @@ static int ensure_device_init() {
     MF_CUDA(rows_kernel_attributes());
     MF_CUDA(pass1_pf_kernel_attributes());
     MF_CUDA(prep64_kernel_attributes());
+    MF_CUDA(fused_kernel_attributes());
     done.push_back(dev);
     return MF_OK;
 }
@@ -177,7 +178,8 @@ struct mf_bank_s {
     int64_t stall_unit = -1;          // test hook (mf_bank_debug_stall)
     long long spin_limit = 4000000;   // bounded-wait iterations, back-off <= ~1 us each
     // schedule (defaults until mf_autotune measures this bank): 0 = persistent
-    // scheduler, 1 = per-batch launches; exchange bytes in flight per batch
+    // scheduler, 1 = per-batch launches, 2 = fused scheduler (N = 2^19, 2^20;
+    // other lengths per batch); exchange bytes in flight per batch
     // (templates per batch = tuned_exch / (8 N), 0 = the default budget);
     // fraction of SMs that start on queue 1
     int sched = 1;
@@ -640,6 +642,7 @@ static bool use_rows(const mf_bank_s *b, const mf_segment_s *g, int log2N1) {
 }
 
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g);
+static bool use_fused(const mf_bank_s *b, const mf_segment_s *g);
 
 // Column-length exponent of the split the per-batch schedule uses for this
 // segment: the alternative split where the bank chose it (mf_autotune) or
@@ -647,7 +650,7 @@ static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g);
 // scheduler and the chi^2 paths use the balanced split.
 static int filter_log2n2(const mf_bank_s *b, const mf_segment_s *g) {
     const int alt = alt_log2n2(g->log2N);
-    if (alt < 0 || use_persistent(b, g) || b->params.fft_mode != MF_FFT_FP32) return log2_n2(g->log2N);
+    if (alt < 0 || use_persistent(b, g) || use_fused(b, g) || b->params.fft_mode != MF_FFT_FP32) return log2_n2(g->log2N);
     const char *e = getenv("MFGB_SPLIT_ALT");
     if (e) return e[0] == '1' ? alt : log2_n2(g->log2N);
     return b->alt_split[g->log2N] ? alt : log2_n2(g->log2N);
@@ -656,11 +659,26 @@ static int filter_log2n2(const mf_bank_s *b, const mf_segment_s *g) {
 static bool use_persistent(const mf_bank_s *b, const mf_segment_s *g) {
     if (g->log2N < 13 || b->params.phase_mode == MF_PHASE_FP32 || b->params.fft_mode != MF_FFT_FP32) return false;
     if (const char *e = getenv("MFGB_SCHED")) {
-        if (strcmp(e, "batch") == 0) return false;
+        if (strcmp(e, "batch") == 0 || strcmp(e, "fused") == 0) return false;
         if (strcmp(e, "persistent") == 0) return true;
     }
     return b->sched == 0;
 }
+
+// The fused scheduler (one launch of both passes through an L2-resident
+// exchange ring) where it applies: N = 2^19, 2^20 on the balanced split, the
+// FP64-anchor phase, FP32 FFT, a tensor map over W, the staged pass 1.
+static bool use_fused(const mf_bank_s *b, const mf_segment_s *g) {
+    if (b->params.phase_mode != MF_PHASE_ANCHOR || b->params.fft_mode != MF_FFT_FP32 || !g->has_tmap[0]) return false;
+    if (b->n > 65535) return false;   // the anchors of every unit come from one launch (grid y)
+    if (!fused_applies(g->log2N, log2_n2(g->log2N))) return false;
+    if (!pass1_pf_applies(g->log2N, log2_n2(g->log2N), choose_log2D(b, g), b->params.phase_mode)) return false;
+    if (const char *e = getenv("MFGB_SCHED")) return strcmp(e, "fused") == 0;
+    return b->sched == 2;
+}
+
+// ring slots of the fused scheduler: 64 MiB of exchange, resident in L2
+static int fused_slots(int64_t N) { return (int)std::max<int64_t>(2, ((int64_t)64 << 20) / (8 * N)); }
 
 // Queue 1: rounds rho = -LA .. U - 1; round rho holds the anchor chunks of
 // unit rho + LA and the pass-1 tiles of unit rho (those units that exist);
@@ -758,10 +776,14 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const int lgD = choose_log2D(b, segs[s]);
         exch_elems = std::max(exch_elems, bt * segs[s]->N);
         anc_elems = std::max(anc_elems, 2 * bt * (((segs[s]->N / 2) >> lgD) + 2));   // two batches in flight
+        if (use_fused(b, segs[s])) {   // the ring, and the anchors of every unit
+            exch_elems = std::max(exch_elems, (int64_t)fused_slots(segs[s]->N) * segs[s]->N);
+            anc_elems = std::max(anc_elems, b->n * anchor_slot_records(segs[s]->log2N, lgD));
+        }
         const int lg2 = filter_log2n2(b, segs[s]);
         nblk = std::max(nblk, (int64_t)pass2_blocks(segs[s]->log2N, lg2));
-        if (!use_persistent(b, segs[s]) && use_rows(b, segs[s], segs[s]->log2N - lg2))   // one partial per row and warp
-            nblk = std::max(nblk, (int64_t)pass2_rows_partials(segs[s]->log2N, lg2));
+        if ((!use_persistent(b, segs[s]) && use_rows(b, segs[s], segs[s]->log2N - lg2)) || use_fused(b, segs[s]))
+            nblk = std::max(nblk, (int64_t)pass2_rows_partials(segs[s]->log2N, lg2));   // one partial per row and warp
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool capturing = stream_capturing(st);
@@ -782,7 +804,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const SegDev sd = seg_dev(segs[s], filter_log2n2(b, segs[s]));
         const int lgD = choose_log2D(b, segs[s]);
         const int man = (int)anchor_slot_records(segs[s]->log2N, lgD);   // records per anchor slot
-        const bool rows = !use_persistent(b, segs[s]) && use_rows(b, segs[s], sd.log2N1);
+        const bool rows = (!use_persistent(b, segs[s]) && use_rows(b, segs[s], sd.log2N1)) || use_fused(b, segs[s]);
         const int nbk = rows ? pass2_rows_partials(sd.log2N, sd.log2N2) : pass2_blocks(sd.log2N, sd.log2N2);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
         // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
@@ -803,6 +825,30 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         MF_CUDA(launch_units(sd, b->d_tmpl, n_t, b->params.f_low, threshold, lgD, unit_order, w.units, st));
         prof_end(b, pi, st);
         count_launches(1);
+        if (use_fused(b, segs[s])) {
+            double by_band = 0.0, by_anc = 0.0;
+            if (b->prof_on)
+                for (int t = 0; t < n_t; ++t) {
+                    by_band += band_bytes[(size_t)t];
+                    by_anc += anc_bytes[(size_t)t];
+                }
+            pi = prof_begin(b, MF_STAGE_ANCHORS, by_anc, st);
+            MF_CUDA(launch_anchors(sd, b->d_tmpl, w.units, 0, n_t, lgD, man, w.anchors, w.anchors4, st));
+            prof_end(b, pi, st);
+            MF_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(unsigned) * (4 + 2 * (size_t)n_t), st));
+            double split = b->split > 0.0 ? b->split : kSplit;
+            if (const char *e = getenv("MFGB_SPLIT")) split = atof(e);
+            pi = prof_begin(b, MF_STAGE_FUSED, by_band + by_anc + 16.0 * (double)sd.N * n_t, st);
+            MF_CUDA(launch_fused(sd, w.units, n_t, lgD, man, w.anchors, w.anchors4, w.exch, fused_slots(sd.N), split,
+                                 w.ctl, w.ctl + 4, w.ctl + 4 + n_t, w.partials, s, kl, w.staged, w.keys, w.counter,
+                                 std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, stall_pos, st));
+            prof_end(b, pi, st);
+            pi = prof_begin(b, MF_STAGE_FINAL, 16.0 * nbk * n_t, st);
+            MF_CUDA(launch_reduce_peaks(sd, w.units, n_t, w.partials, nbk, s, n_seg, peaks, st));
+            prof_end(b, pi, st);
+            count_launches(3);
+            continue;
+        }
         PersistParams P;
         int n1 = 0, n2 = 0, nA = 0;
         bool persist = use_persistent(b, segs[s]);
@@ -1165,7 +1211,7 @@ extern "C" int mf_debug_status(uint32_t *word, int *enabled) {
     MF_CUDA(cudaDeviceSynchronize());
     unsigned all = 0, w = 0;
     cudaError_t (*readers[])(unsigned *) = {dbg_read_filter, dbg_read_pass1, dbg_read_rows,
-                                            dbg_read_persist, dbg_read_chisq, dbg_read_prep};
+                                            dbg_read_persist, dbg_read_chisq, dbg_read_prep, dbg_read_fused};
     for (auto rd : readers) {
         MF_CUDA(rd(&w));
         all |= w;
@@ -1245,6 +1291,16 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
         any_pf = any_pf || pass1_pf_applies(segs[s]->log2N, lg2, lgD, b->params.phase_mode);
         any_rows = any_rows || (pass2_rows_applies(segs[s]->log2N - lg2) && b->params.fft_mode == MF_FFT_FP32);
     }
+    // the fused scheduler, where it applies to some segment of the call
+    bool any_fused = false;
+    for (int s = 0; s < n_seg; ++s) {
+        const int saved = b->sched;
+        b->sched = 2;
+        any_fused = any_fused || use_fused(b, segs[s]);
+        b->sched = saved;
+    }
+    if (any_fused)
+        for (double sp : {0.55, 0.60, 0.65}) cands.push_back({2, 0, sp, 0, 0});
     for (int64_t mib : {128, 256, 512, 1024}) {
         cands.push_back({1, mib << 20, 0.60, 0, 0});
         if (any_pf) cands.push_back({1, mib << 20, 0.60, 1, 0});
@@ -1342,13 +1398,17 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
         if (!f) return set_err(MF_EINVAL, "cannot write %s", cache_path);
         const int64_t ex = best.exch > 0 ? best.exch : kExchBudget;
         std::string sp = "{";
-        std::vector<int> all_lg;
-        for (int s = 0; s < n_seg; ++s)
-            if (std::find(all_lg.begin(), all_lg.end(), segs[s]->log2N) == all_lg.end()) all_lg.push_back(segs[s]->log2N);
+        std::vector<std::pair<int, int>> all_lg;   // (log2 N, the column length the tuned bank uses)
+        for (int s = 0; s < n_seg; ++s) {
+            const int lg = segs[s]->log2N;
+            bool seen = false;
+            for (const auto &q : all_lg) seen = seen || q.first == lg;
+            if (!seen) all_lg.push_back({lg, filter_log2n2(b, segs[s])});
+        }
         std::sort(all_lg.begin(), all_lg.end());
         for (size_t i = 0; i < all_lg.size(); ++i) {
-            const int lg = all_lg[i];
-            const int l2 = (best.sched == 1 && b->alt_split[lg] && alt_log2n2(lg) >= 0) ? alt_log2n2(lg) : log2_n2(lg);
+            const int lg = all_lg[i].first;
+            const int l2 = all_lg[i].second;
             char buf[96];
             snprintf(buf, sizeof(buf), "%s\"%lld\": \"%lld x %lld\"", i ? ", " : "", (long long)1 << lg,
                      (long long)1 << (lg - l2), (long long)1 << l2);
@@ -1358,12 +1418,13 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
         fprintf(f, "{\"N\": %lld, \"templates\": %lld, \"segments\": %d, \"scheduler\": \"%s\", "
                    "\"exchange_mib\": %lld, \"batch_at_max_N\": %lld, \"split\": %.3f, \"pass1\": \"%s\", "
                    "\"pass2\": \"%s\", \"n1_x_n2\": %s, \"candidates\": %d, \"ms_per_call\": %.4f}\n",
-                (long long)maxN, (long long)b->n, n_seg, best.sched == 0 ? "persistent" : "batch",
+                (long long)maxN, (long long)b->n, n_seg,
+                best.sched == 0 ? "persistent" : (best.sched == 2 ? "fused" : "batch"),
                 (long long)(ex >> 20), (long long)choose_batch(maxN, b->n, ex), best.split,
-                best.sched == 0 ? "fused"
+                best.sched != 1 ? "fused"
                                 : (best.p1 == 0 ? "persistent-staged" : (best.p1 == 2 ? "persistent-staged-half-tile"
                                                                                         : "per-tile")),
-                best.sched == 0 ? "fused" : (best.p2 == 0 ? "rows" : "per-tile"), sp.c_str(),
+                best.sched != 1 ? "fused" : (best.p2 == 0 ? "rows" : "per-tile"), sp.c_str(),
                 (int)(cands.size() + 2 * lengths.size()), best_ms);
         fclose(f);
     }

@@ -129,6 +129,7 @@ cudaError_t dbg_read_rows(unsigned *w);
 cudaError_t dbg_read_persist(unsigned *w);
 cudaError_t dbg_read_chisq(unsigned *w);
 cudaError_t dbg_read_prep(unsigned *w);
+cudaError_t dbg_read_fused(unsigned *w);
 
 // Stable trigger keys: (tmpl, seg, j) packed into 64 bits.
 struct KeyLayout {
@@ -298,6 +299,17 @@ int refine_blocks_for(int64_t n, int n_sm);   // blocks per row that fill the GP
 // kernels queued by one refinement call of n rows: the row set-up, the
 // partial sums in chunks of at most 65535 rows (grid y limit), the totals
 inline int refine_launches(int64_t n) { return 2 + (int)((n + 65534) / 65535); }
+
+// fused persistent scheduler (mf_fused.cu): N = 2^19, 2^20 on the balanced split;
+// anchors of all units precomputed (slot u = unit u); ring of S exchange slots;
+// ctl[0..2] zeroed, done1 / done2 n_units counters each, zeroed
+bool fused_applies(int log2N, int log2N2);
+cudaError_t launch_fused(const SegDev &seg, const UnitInfo *units, int n_units, int log2D, int max_anc,
+                         const float4 *anchors, const float *anchors4, float2 *ring, int S, double split,
+                         unsigned *ctl, unsigned *done1, unsigned *done2, float4 *partials, int seg_idx, KeyLayout kl,
+                         mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap, int *status,
+                         long long spin_limit, int stall_unit, cudaStream_t st);
+cudaError_t fused_kernel_attributes();
 
 // persistent scheduler (mf_persist.cu): segments with N >= 2^13
 cudaError_t launch_persistent(const PersistParams &P, int grid, cudaStream_t st);

@@ -117,6 +117,14 @@ def test_uneven_bank_schedules_and_graph_agree(mf, uneven_data, monkeypatch):
     assert n_a == n_b
     assert np.array_equal(pk_a.view(np.uint8), pk_b.view(np.uint8))
     assert np.array_equal(tr_a.view(np.uint8), tr_b.view(np.uint8))
+    # the fused scheduler (one launch per 2^19 / 2^20 segment, L2-resident exchange ring;
+    # the other lengths fall back to per-batch launches)
+    monkeypatch.setenv("MFGB_SCHED", "fused")
+    _, pk_f, tr_f, n_f = _uneven_call(mf, wl, segs)
+    assert n_f == n_a
+    assert np.array_equal(pk_a.view(np.uint8), pk_f.view(np.uint8))
+    assert np.array_equal(tr_a.view(np.uint8), tr_f.view(np.uint8))
+    monkeypatch.setenv("MFGB_SCHED", "batch")
     # per-template launches on a prefix of the bank
     sub = workloads.Workload("prefix", wl.m1[:256], wl.m2[:256], wl.segments, threshold=wl.threshold)
     monkeypatch.setenv("MFGB_BATCH", "1")
@@ -177,7 +185,7 @@ def test_uneven_bank_pass1_kernels_agree(mf, uneven_data, monkeypatch):
     assert np.array_equal(tr_a.view(np.uint8), tr_d.view(np.uint8))
 
 
-@pytest.mark.parametrize("sched", ["batch", "persistent"])
+@pytest.mark.parametrize("sched", ["batch", "persistent", "fused"])
 def test_uneven_bank_unit_order_agrees(mf, uneven_data, monkeypatch, sched):
     """Units run in descending band width (widest first); bank order gives
     bit-identical peaks and triggers under both schedulers, and the outputs

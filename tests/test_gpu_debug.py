@@ -26,6 +26,8 @@ CASES = [
     ("n20_half_tile", 1 << 20, 4096.0, 6, {"MFGB_SCHED": "batch", "MFGB_P1TILE": "half"}),
     ("n20_cpasync_pertile_p2", 1 << 20, 4096.0, 6, {"MFGB_SCHED": "batch", "MFGB_P1TMA": "0", "MFGB_P2ROWS": "0"}),
     ("n20_persistent", 1 << 20, 4096.0, 6, {"MFGB_SCHED": "persistent"}),
+    ("n19_fused", 1 << 19, 4096.0, 7, {"MFGB_SCHED": "fused"}),
+    ("n20_fused", 1 << 20, 4096.0, 6, {"MFGB_SCHED": "fused"}),
     ("n21", 1 << 21, 4096.0, 3, {"MFGB_SCHED": "batch"}),
     ("n22", 1 << 22, 4096.0, 2, {"MFGB_SCHED": "batch"}),
 ]

@@ -70,7 +70,7 @@ def test_refresh_keeps_psd_table(mf):
     _same(_filter(mf, bank, seg, 4.0, 1 << 12), ref)
 
 
-@pytest.mark.parametrize("sched", ["persistent", "batch"])
+@pytest.mark.parametrize("sched", ["persistent", "batch", "fused"])
 def test_graph_replay_equals_eager(mf, monkeypatch, sched):
     import torch
     monkeypatch.setenv("MFGB_SCHED", sched)

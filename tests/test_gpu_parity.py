@@ -538,6 +538,42 @@ def test_bounded_wait_timeout_reports_and_recovers(mf, monkeypatch):
     assert np.array_equal(ref.view(np.uint8), got.view(np.uint8))
 
 
+@pytest.mark.parametrize("lg", [19, 20])
+def test_fused_scheduler_matches_batches_and_recovers(mf, monkeypatch, lg):
+    """The fused scheduler (pass-1 CTAs and pass-2 warps in one launch, units
+    streamed through a ring of exchange slots, here wrapped several times)
+    gives peaks and triggers bit-identical to the per-batch launches; a
+    dependency wait that can never be satisfied (test hook) runs out, the call
+    reports MF_ETIMEOUT, nothing faults, and the next call is bit-identical."""
+    import torch
+    wl = workloads.small(seed=70 + lg, N=1 << lg, fs=4096.0, n_templates=37, m_lo=1.1, m_hi=6.0)
+    spec = wl.segments[0]
+    s32, _ = oracle_segment(spec)
+    seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
+    bank = mf.Bank(wl.m1, wl.m2)
+    monkeypatch.setenv("MFGB_SCHED", "batch")
+    a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)]
+    assert bank.check() == 0
+    monkeypatch.setenv("MFGB_SCHED", "fused")
+    for split in ("0.5", "0.7"):
+        monkeypatch.setenv("MFGB_SPLIT", split)
+        b = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)]
+        assert bank.check() == 0
+        n = int(a[2][0])
+        assert int(b[2][0]) == n and n > 0
+        assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8))
+        assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
+    monkeypatch.delenv("MFGB_SPLIT")
+    bank.debug_stall(11, spin_limit=2000)
+    mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)
+    assert bank.check(allow_timeout=True) == mf._native.MF_ETIMEOUT
+    bank.debug_stall(-1)
+    c = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 5.0, trig_cap=1 << 18)]
+    assert bank.check() == 0
+    assert np.array_equal(a[0].view(np.uint8), c[0].view(np.uint8))
+    assert np.array_equal(a[1][:int(a[2][0])].view(np.uint8), c[1][:int(a[2][0])].view(np.uint8))
+
+
 @pytest.mark.parametrize("lg,fft", [(20, "fp32"), (21, "fp32"), (20, "tc_fp16"), (19, "tc_bf16")])
 def test_rows_kernel_timeout_reports_and_recovers(mf, monkeypatch, lg, fft):
     """The per-batch rows kernels (1024- and 2048-point rows, and the
