@@ -1,6 +1,7 @@
-// mf_rows.cu -- pass 2 of the filter (row IFFTs + rho epilogue) as a
-// persistent kernel in which a group of G warps owns whole rows: one warp for
-// row length N1 = 1024 (N = 2^19, 2^20), two for N1 = 2048 (N = 2^21, 2^22).
+// mf_rows.cu -- pass 2 of the filter (row IFFTs + rho epilogue) as
+// persistent kernels in which a group of warps owns whole rows: one warp for
+// row length N1 = 1024 (N = 2^19, 2^20), a pair for N1 = 2048 (N = 2^21,
+// 2^22, and the 512 x 2048 split of 2^20).
 //
 // Row j2 of batch entry b is E[b N + j2 N1 .. + N1), contiguous.  Each group
 // works through rows g, g + W, g + 2W, ... (W = groups in the grid) in its
@@ -8,14 +9,15 @@
 //   1. wait for the row's bulk copy (cp.async.bulk, completion counted on the
 //      group's mbarrier; bounded wait, status bit 1 and stop on expiry);
 //   2. stage 0 (radix 32) from the staged row, written back in the padded
-//      Stockham layout over the same region (then the middle stage, N1 = 2048);
-//   3. the last stage reads the region, then -- before its arithmetic -- the
-//      group's first thread starts the bulk copy of the group's next row into
-//      the region, so the copy runs under the last stage and the epilogue;
+//      Stockham layout over the same region;
+//   3. the remaining stages (k_pass2_rows, k_pass2_rows2048 below); once the
+//      region has been read for the last time, the group's first thread
+//      starts the bulk copy of the group's next row into it, so the copy runs
+//      under the remaining arithmetic and the epilogue;
 //   4. epilogue as in the per-tile pass 2 (argmax with the lowest-j rule,
 //      warp-aggregated trigger append), each warp's argmax of the row to
 //      partials[unit][j2][warp of the group].
-// The twiddle table is filled once per CTA; the stages of a row synchronise
+// The twiddle tables are copied once per CTA; the stages of a row synchronise
 // only its group (__syncwarp, or a named barrier for a pair of warps).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -24,21 +26,107 @@
 
 namespace mf {
 
+// 1024-point rows, one warp per row: stage 0, then the last stage with the
+// next row's copy started from the sink once the region has been read.
 template <int L>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
     using S = FftShape<L>;
-    constexpr int G = L / 1024;               // warps per row
-    constexpr int NG = kWarps / G;            // rows in flight per CTA
-    constexpr int T = L / 32;                 // threads per row (= 32 G)
-    static_assert(G >= 1 && kWarps % G == 0 && T == 32 * G, "1024- or 2048-point rows");
+    static_assert(L == 1024 && S::NST == 2 && S::T == 32, "1024-point rows (one warp each)");
+    constexpr int G = 1, T = 32;
     extern __shared__ __align__(16) float2 rows_smem[];
-    __shared__ int gfail[NG];                 // a warp of the group gave up waiting
-    float2 *tw = rows_smem + NG * S::STRIDE;
+    float2 *tw = rows_smem + kWarps * S::STRIDE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(tw + TwTable<L>::SIZE);
-    const int grp = (threadIdx.x >> 5) / G, t = threadIdx.x & (T - 1), lane = threadIdx.x & 31;
-    const int wig = (threadIdx.x >> 5) % G;   // warp within the group
+    const int grp = threadIdx.x >> 5, t = threadIdx.x & (T - 1);
     float2 *region = rows_smem + grp * S::STRIDE;
     fill_twiddles<L>(tw);
+    if (t == 0) mbar_init(&bars[grp], 1);
+    mbar_fence_init();
+    __syncthreads();
+    const int64_t total = (int64_t)p.n_units << p.log2N2;
+    const int64_t step = (int64_t)gridDim.x * kWarps;
+    int64_t r = (int64_t)blockIdx.x * kWarps + grp;
+    if (r < total && t == 0 && !row_withheld(p, r)) {
+        mbar_expect_tx(&bars[grp], L * sizeof(float2));
+        bulk_copy_g2s(region, row_src<L>(p, r), L * sizeof(float2), &bars[grp]);
+    }
+    uint32_t parity = 0;
+    for (; r < total; r += step) {
+        // 1. the row has landed (bounded wait)
+        long long it = 0;
+        bool ok = true;
+        while (!mbar_try_wait(&bars[grp], parity)) {
+            if (++it > p.spin_limit) { ok = false; break; }
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (t == 0) atomicOr(p.status, 2);
+            return;   // the copy into this warp's region never completed; nothing else is in flight
+        }
+        parity ^= 1u;
+        const int slot = (int)(r >> p.log2N2);
+        const int j2 = (int)(r & (((int64_t)1 << p.log2N2) - 1));
+        const int unit = p.unit0 + slot;
+        const UnitInfo u = p.units[unit];
+        // 2. stage 0 from the staged row (element t + T q of the row at t + T q)
+        float2 v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = region[t + T * q];
+        Dft<32, +1>::run(v);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
+        __syncwarp();
+        // 3./4. the last stage, next-row copy, epilogue
+        const int64_t rn = r + step;
+        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp],
+                               rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr);
+        stockham_stage<L, S::R1, 32, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
+        if (MF_DBG(slot < p.n_units && j2 < (1 << p.log2N2), kDbgRows))
+            snk.finish(&p.partials[((int64_t)unit << p.log2N2) + j2]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2048-point rows (N = 2^21, 2^22, and the 512 x 2048 split of 2^20) on a pair
+// of warps, with the arithmetic of the radix 32 x 32 x 2 Stockham schedule
+// (bit-identical to the per-tile pass 2) but one shared-memory round trip
+// fewer.  Stages 0 and 1 run as in the generic schedule; after stage 1, lane k
+// of warp h holds z[h 1024 + k + 32 r] (r < 32), the 1024-point transforms of
+// the even (h = 0) and odd (h = 1) samples.  The last stage,
+//   X[b] = z[b] + w^b z[b + 1024],  X[b + 1024] = z[b] - w^b z[b + 1024],
+// w = exp(2 pi i / 2048), b = k + 32 r, pairs lane k of both warps: warp 0
+// takes r < 16 and warp 1 r >= 16, each handing the other the 16 values it
+// needs through the front of the pair's region (stage 1 has read it by then);
+// the next row's bulk copy starts once the exchange has been read.  Shared
+// memory holds the stage-1 table and the used half of the last stage's table
+// (16 KB instead of 24).  Measured against the generic three-stage form at
+// N = 2^21: 4.2 against 4.9 us per template; a separate exchange area, with
+// the copy started right after stage 1's loads, needs the twiddles read
+// through L1 to keep two CTAs per SM and measured 4.7.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t rows2048_smem() {
+    return (size_t)(kWarps / 2) * FftShape<2048>::STRIDE * sizeof(float2) + 2048 * sizeof(float2) +
+           (kWarps / 2) * sizeof(uint64_t);
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows2048(RowsParams p) {
+    constexpr int L = 2048, G = 2, NG = kWarps / G, T = 64;
+    using S = FftShape<L>;
+    extern __shared__ __align__(16) float2 rows_smem[];
+    __shared__ int gfail[NG];
+    const int grp = (threadIdx.x >> 5) / G, t = threadIdx.x & (T - 1), lane = threadIdx.x & 31;
+    const int h = (threadIdx.x >> 5) % G;                     // warp within the pair
+    float2 *region = rows_smem + grp * S::STRIDE;
+    float2 *xb = region;                                        // the exchange, once stage 1 has read the region
+    float2 *tw1 = rows_smem + NG * S::STRIDE;                   // stage 1: [r 32 + k] = exp(2 pi i r k / 1024)
+    float2 *tw2 = tw1 + 1024;                                   // last stage: [b] = exp(2 pi i b / 2048)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tw2 + 1024);
+    {
+        const float2 *src = g_tw_tables + tw_offset<L>();
+        for (int m = threadIdx.x; m < 1024; m += blockDim.x) {
+            tw1[m] = __ldg(&src[m]);
+            tw2[m] = __ldg(&src[TwTable<L>::S1 + 1024 + m]);   // row r = 1 of the last stage's table
+        }
+    }
     if (t == 0) {
         mbar_init(&bars[grp], 1);
         gfail[grp] = 0;
@@ -54,51 +142,77 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
     }
     uint32_t parity = 0;
     for (; r < total; r += step) {
-        // 1. the row has landed (bounded wait; every warp of the group waits on the same barrier)
         long long it = 0;
         bool ok = true;
-        // 2048-point rows: the 16 KB copy is issued only in the last stage, so the
-        // wait may be long; the sleep hint keeps the waiting warps off the issue slots
-        while (!(G > 1 ? mbar_try_wait_sleep(&bars[grp], parity, 500u) : mbar_try_wait(&bars[grp], parity))) {
+        while (!mbar_try_wait_sleep(&bars[grp], parity, 500u)) {
             if (++it > p.spin_limit) { ok = false; break; }
         }
         ok = __all_sync(0xffffffffu, ok);
-        if constexpr (G > 1) {   // the group leaves together: no warp may wait at a group barrier alone
-            if (!ok && lane == 0) atomicOr(&gfail[grp], 1);
-            GroupSync<G>::sync();
-            ok = *(volatile int *)&gfail[grp] == 0;
-        }
-        if (!ok) {
-            if (lane == 0) atomicOr(p.status, 2);
-            return;   // the copy into this group's region never completed; nothing else is in flight
-        }
+        if (!ok && lane == 0) atomicOr(&gfail[grp], 1);
         parity ^= 1u;
         const int slot = (int)(r >> p.log2N2);
         const int j2 = (int)(r & (((int64_t)1 << p.log2N2) - 1));
         const int unit = p.unit0 + slot;
         const UnitInfo u = p.units[unit];
-        // 2. stage 0 from the staged row (element t + T q of the row at t + T q)
+        const int64_t rn = r + step;
+        const float2 *next = rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr;
+        auto issue_next = [&]() {
+            GroupSync<G>::sync();   // every read of the region is done
+            fence_proxy_async();
+            if (next != nullptr && t == 0) {
+                mbar_expect_tx(&bars[grp], L * sizeof(float2));
+                bulk_copy_g2s(region, next, L * sizeof(float2), &bars[grp]);
+            }
+        };
+        // stage 0 (radix 32, Ns = 1): butterfly t reads x[t + 64 q]
+        // (after a wait that ran out the region is stale; the pair leaves together at the barrier below)
         float2 v[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] = region[t + T * q];
         Dft<32, +1>::run(v);
-        GroupSync<G>::sync();
+        GroupSync<G>::sync();   // every read of the landed row is done; gfail is final
+        if (*(volatile int *)&gfail[grp] != 0) {
+            if (lane == 0) atomicOr(p.status, 2);
+            return;   // the copy into this pair's region never completed; nothing else is in flight
+        }
 #pragma unroll
         for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
         GroupSync<G>::sync();
-        // 3./4. the remaining stages, next-row copy, epilogue
-        const int64_t rn = r + step;
-        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp],
-                               rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr);
-        if constexpr (S::NST == 2) {
-            stockham_stage<L, S::R1, 32, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
+        // stage 1 (radix 32, Ns = 32): butterfly t = 32 h + k reads y[t + 64 r]
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = region[spad(t + 64 * q)];
+        GroupSync<G>::sync();   // the exchange below overwrites the region
+#pragma unroll
+        for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw1[q * 32 + lane]);
+        Dft<32, +1>::run(v);
+        // exchange: warp 0 keeps z0[k + 32 r], r < 16, and receives z1 there;
+        // warp 1 keeps z1[k + 32 r], r >= 16, and receives z0 there
+        if (h == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) xb[32 * i + lane] = v[16 + i];
         } else {
-            stockham_stage<L, S::R1, 32, +1, false, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
-            stockham_stage<L, S::R2, 32 * S::R1, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(
-                region, tw + TwTable<L>::S1, 0, t, snk);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) xb[512 + 32 * i + lane] = v[i];
         }
+        GroupSync<G>::sync();
+        float2 lo[16], hi[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float2 d[2];
+            d[0] = h == 0 ? v[i] : xb[32 * i + lane];
+            d[1] = h == 0 ? xb[512 + 32 * i + lane] : v[16 + i];
+            d[1] = cmul(d[1], tw2[lane + 32 * (i + 16 * h)]);
+            Dft<2, +1>::run(d);
+            lo[i] = d[0];
+            hi[i] = d[1];
+        }
+        issue_next();
+        // epilogue: outputs b = k + 32 (i + 16 h) and b + 1024
+        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp], nullptr);
+        snk.template store<16>(0, lane + 512 * h, 32, lo);
+        snk.template store<16>(0, lane + 512 * h + 1024, 32, hi);
         if (MF_DBG(slot < p.n_units && j2 < (1 << p.log2N2), kDbgRows))
-            snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + wig]);
+            snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + h]);
     }
 }
 
@@ -403,7 +517,8 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
             k_pass2_rows<1024><<<gr, kWarps * 32, rows_smem<1024>(), st>>>(p);
     } else {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 2 - 1) / (kWarps / 2));
-        k_pass2_rows<2048><<<(unsigned)std::max<int64_t>(grid, 1), kWarps * 32, rows_smem<2048>(), st>>>(p);
+        const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
+        k_pass2_rows2048<<<gr, kWarps * 32, rows2048_smem(), st>>>(p);
     }
     return cudaGetLastError();
 }
@@ -422,8 +537,7 @@ cudaError_t rows_kernel_attributes() {
     e = cudaFuncSetAttribute(k_pass2_rows_tc<MF_FFT_TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rows_smem_tc());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pass2_rows<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rows_smem<2048>());
+    return cudaFuncSetAttribute(k_pass2_rows2048, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows2048_smem());
 }
 
 }  // namespace mf
