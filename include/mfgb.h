@@ -303,10 +303,11 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
  * with bulk-copy prefetch, or one CTA per row tile) and keeps the fastest in
  * the bank for later calls (the default is per-batch launches with 1 GiB, the
  * staged pass 1 and the row pass 2 where they apply).  Before those it picks,
- * per segment length N = 2^18 .. 2^21, the four-step split N = N1 x N2 of the
+ * per segment length N = 2^18 .. 2^22, the four-step split N = N1 x N2 of the
  * per-batch schedule: the balanced one (N2 = 2^floor(log2 N / 2) columns) or
  * an alternative (2^18: 1024 x 256, 2^19: 512 x 1024, 2^20: 2048 x 512,
- * 2^21: 1024 x 2048 as N1 x N2), timing each on that length's segments.  It
+ * 2^21: 1024 x 2048, 2^22: 4096 x 1024 as N1 x N2), timing each on that
+ * length's segments.  It
  * runs each candidate 1 + repeats times on cuda_stream and synchronises; it
  * allocates temporary outputs and may grow the bank's workspace.  threshold
  * should be the one the search will use (it sets the trigger traffic).  If
@@ -342,7 +343,7 @@ int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold
  *   MFGB_P1TMA=0                 the persistent pass 1 stages W with per-thread
  *                                cp.async instead of TMA
  *   MFGB_SPLIT_ALT=1|0           per-batch schedule on the alternative split
- *                                of 2^18..2^21 (see mf_autotune) or the
+ *                                of 2^18..2^22 (see mf_autotune) or the
  *                                balanced one (this one changes rounding)
  *   MFGB_P2ROWS=0                pass 2 one CTA per row tile instead of
  *                                warp-owned rows (FP32 FFT form only)

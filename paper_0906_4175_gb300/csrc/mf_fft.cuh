@@ -275,7 +275,7 @@ __host__ __device__ constexpr int tw_offset() {
     if constexpr (L <= 32) return 0;
     else return tw_offset<L / 2>() + TwTable<L / 2>::SIZE;
 }
-constexpr int kTwTotal = tw_offset<4096>();
+constexpr int kTwTotal = tw_offset<8192>();   // the tables of L = 64 .. 4096
 static __device__ float2 g_tw_tables[kTwTotal];
 
 template <int L>
@@ -290,6 +290,7 @@ static inline cudaError_t init_twiddle_tables() {
     k_init_twiddles<512><<<1, 256>>>();
     k_init_twiddles<1024><<<1, 256>>>();
     k_init_twiddles<2048><<<1, 256>>>();
+    k_init_twiddles<4096><<<1, 256>>>();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaDeviceSynchronize();

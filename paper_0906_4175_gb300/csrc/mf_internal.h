@@ -54,12 +54,14 @@ __host__ __device__ inline int log2_n2(int log2N) { return log2N / 2; }
 // candidate): column length 2^alt_log2n2, or -1 where there is none.
 //   2^18: 256 x 1024 (balanced 512 x 512)     2^19: 1024 x 512 (512 x 1024)
 //   2^20: 512 x 2048 (1024 x 1024)            2^21: 2048 x 1024 (1024 x 2048)
+//   2^22: 1024 x 4096 (2048 x 2048)
 __host__ __device__ inline int alt_log2n2(int log2N) {
     switch (log2N) {
         case 18: return 8;
         case 19: return 10;
         case 20: return 9;
         case 21: return 11;
+        case 22: return 10;
         default: return -1;
     }
 }

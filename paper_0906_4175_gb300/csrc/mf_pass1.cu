@@ -38,7 +38,8 @@
 // every in-band bin is that of the per-tile kernel, so results are bit-identical.
 //
 // Applies to the FP64-anchor phase when the anchor spacing D is at least the
-// tile width C and at most N1, for N = 2^16 .. 2^21 (L = 256 .. 1024); every
+// tile width C and at most N1, for N = 2^16 .. 2^21 and the 1024-point columns
+// of the alternative split of 2^22, 4096 rows x 1024 (L = 256 .. 1024); every
 // other case launches the per-tile kernel.
 #include <algorithm>
 #include <cstdlib>
@@ -205,7 +206,7 @@ bool pass1_pf_applies(int log2N, int log2N2, int log2D, int phase_mode) {
     if (g_pf_sms <= 0 || phase_mode == MF_PHASE_FP32) return false;
     const char *env = std::getenv("MFGB_P1PF");   // "0": the per-tile kernel (comparisons)
     if (env && env[0] == '0') return false;
-    if (log2N < 16 || log2N > 21 || log2N2 < 8 || log2N2 > 10) return false;
+    if (log2N < 16 || log2N > 22 || log2N2 < 8 || log2N2 > 10) return false;
     const int log2N1 = log2N - log2N2;
     const int C = (8192 >> log2N2) < (1 << log2N1) ? (8192 >> log2N2) : (1 << log2N1);   // seqs_per_cta
     if ((1 << log2D) < C || log2D > log2N1) return false;
@@ -214,7 +215,7 @@ bool pass1_pf_applies(int log2N, int log2N2, int log2D, int phase_mode) {
 }
 
 bool make_w_tensor_maps(const float2 *W, int log2N, int log2N2, void *maps_out) {
-    if (log2N < 16 || log2N > 21 || log2N2 < 8 || log2N2 > 10 || W == nullptr || ((uintptr_t)W & 15u) != 0)
+    if (log2N < 16 || log2N > 22 || log2N2 < 8 || log2N2 > 10 || W == nullptr || ((uintptr_t)W & 15u) != 0)
         return false;
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
@@ -251,10 +252,10 @@ cudaError_t pass1_pf_kernel_attributes() {
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_pf_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    for (int lg = 16; lg <= 21; ++lg) {
+    for (int lg = 16; lg <= 22; ++lg) {   // 2^22: the alternative split only (2048-point columns use k_fft_pass)
         Pass1PfParams p{};
         PfOp op{&p, nullptr, 0, false, nullptr, true};
-        if ((e = dispatch_split(lg, op)) != cudaSuccess) return e;
+        if (lg <= 21 && (e = dispatch_split(lg, op)) != cudaSuccess) return e;
         if (alt_log2n2(lg) >= 8 && alt_log2n2(lg) <= 10 && (e = dispatch_split2(lg, alt_log2n2(lg), op)) != cudaSuccess)
             return e;
     }

@@ -90,6 +90,7 @@ cudaError_t dispatch_split2(int log2N, int log2N2, Op &op) {
         case 19: return op.template run<1024, 512>();
         case 20: return op.template run<512, 2048>();
         case 21: return op.template run<2048, 1024>();
+        case 22: return op.template run<1024, 4096>();
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,7 +1,8 @@
 // mf_rows.cu -- pass 2 of the filter (row IFFTs + rho epilogue) as
 // persistent kernels in which a group of warps owns whole rows: one warp for
-// row length N1 = 1024 (N = 2^19, 2^20), a pair for N1 = 2048 (N = 2^21,
-// 2^22, and the 512 x 2048 split of 2^20).
+// row length N1 = 1024 (N = 2^19, 2^20), two for N1 = 2048 (N = 2^21, 2^22,
+// and the 512 x 2048 split of 2^20), four for N1 = 4096 (the 1024 x 4096
+// split of 2^22).
 //
 // Row j2 of batch entry b is E[b N + j2 N1 .. + N1), contiguous.  Each group
 // works through rows g, g + W, g + 2W, ... (W = groups in the grid) in its
@@ -10,7 +11,7 @@
 //      group's mbarrier; bounded wait, status bit 1 and stop on expiry);
 //   2. stage 0 (radix 32) from the staged row, written back in the padded
 //      Stockham layout over the same region;
-//   3. the remaining stages (k_pass2_rows, k_pass2_rows2048 below); once the
+//   3. the remaining stages (k_pass2_rows, k_pass2_rows_group below); once the
 //      region has been read for the last time, the group's first thread
 //      starts the bulk copy of the group's next row into it, so the copy runs
 //      under the remaining arithmetic and the epilogue;
@@ -86,46 +87,50 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// 2048-point rows (N = 2^21, 2^22, and the 512 x 2048 split of 2^20) on a pair
-// of warps, with the arithmetic of the radix 32 x 32 x 2 Stockham schedule
-// (bit-identical to the per-tile pass 2) but one shared-memory round trip
-// fewer.  Stages 0 and 1 run as in the generic schedule; after stage 1, lane k
-// of warp h holds z[h 1024 + k + 32 r] (r < 32), the 1024-point transforms of
-// the even (h = 0) and odd (h = 1) samples.  The last stage,
-//   X[b] = z[b] + w^b z[b + 1024],  X[b + 1024] = z[b] - w^b z[b + 1024],
-// w = exp(2 pi i / 2048), b = k + 32 r, pairs lane k of both warps: warp 0
-// takes r < 16 and warp 1 r >= 16, each handing the other the 16 values it
-// needs through the front of the pair's region (stage 1 has read it by then);
-// the next row's bulk copy starts once the exchange has been read.  Shared
-// memory holds the stage-1 table and the used half of the last stage's table
-// (16 KB instead of 24).  Measured against the generic three-stage form at
-// N = 2^21: 4.2 against 4.9 us per template; a separate exchange area, with
-// the copy started right after stage 1's loads, needs the twiddles read
-// through L1 to keep two CTAs per SM and measured 4.7.
+// Rows of L = 1024 G points on a group of G = 2 or 4 warps: 2048-point rows
+// (N = 2^21, 2^22, and the 512 x 2048 split of 2^20) and 4096-point rows (the
+// 1024 x 4096 split of 2^22), with the arithmetic of the radix 32 x 32 x G
+// Stockham schedule of the per-tile kernel (bit-identical) but one
+// shared-memory round trip fewer.  Stages 0 and 1 run as in the generic
+// schedule; after stage 1, lane k of warp h holds z[1024 h + k + 32 r]
+// (r < 32), the 1024-point transform of the samples n = h (mod G).  The last
+// stage, for b = k + 32 r < 1024 and q < G,
+//   X[b + 1024 q] = sum_p w^(p b) z[1024 p + b] e^(2 pi i p q / G),
+// w = exp(2 pi i / L), needs lane k of every warp: warp h takes the
+// RW = 32 / G values of r in [RW h, RW h + RW) and receives the other warps'
+// values there through the front of the group's region (stage 1 has read it
+// by then); the next row's copy starts once that exchange has been read.
+// Shared memory keeps the stage-1 table and rows p = 1 .. G - 1 of the last
+// stage's table.  Pass 2 at N = 2^21: 4.2 us per template against 4.9 for
+// the generic three-stage row form; a separate exchange area, with the copy
+// started right after stage 1's loads, needs the twiddles read through L1 to
+// keep two CTAs per SM and measured 4.7.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr size_t rows2048_smem() {
-    return (size_t)(kWarps / 2) * FftShape<2048>::STRIDE * sizeof(float2) + 2048 * sizeof(float2) +
-           (kWarps / 2) * sizeof(uint64_t);
+template <int G>
+__host__ __device__ constexpr size_t rows_group_smem() {
+    return (size_t)(kWarps / G) * FftShape<1024 * G>::STRIDE * sizeof(float2) + (size_t)1024 * G * sizeof(float2) +
+           (kWarps / G) * sizeof(uint64_t);
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows2048(RowsParams p) {
-    constexpr int L = 2048, G = 2, NG = kWarps / G, T = 64;
+template <int G>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_group(RowsParams p) {
+    constexpr int L = 1024 * G, NG = kWarps / G, T = 32 * G, RW = 32 / G;
     using S = FftShape<L>;
+    static_assert((G == 2 || G == 4) && S::NST == 3 && S::R2 == G && S::T == T, "rows of 2048 or 4096 points");
+    static_assert(G * G * RW * 32 <= S::STRIDE, "the exchange fits the row region");
     extern __shared__ __align__(16) float2 rows_smem[];
     __shared__ int gfail[NG];
     const int grp = (threadIdx.x >> 5) / G, t = threadIdx.x & (T - 1), lane = threadIdx.x & 31;
-    const int h = (threadIdx.x >> 5) % G;                     // warp within the pair
+    const int h = (threadIdx.x >> 5) % G;                     // warp within the group
     float2 *region = rows_smem + grp * S::STRIDE;
     float2 *xb = region;                                        // the exchange, once stage 1 has read the region
     float2 *tw1 = rows_smem + NG * S::STRIDE;                   // stage 1: [r 32 + k] = exp(2 pi i r k / 1024)
-    float2 *tw2 = tw1 + 1024;                                   // last stage: [b] = exp(2 pi i b / 2048)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tw2 + 1024);
+    float2 *tw2 = tw1 + 1024;                                   // last stage: [(p - 1) 1024 + b] = w^(p b)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tw2 + 1024 * (G - 1));
     {
         const float2 *src = g_tw_tables + tw_offset<L>();
-        for (int m = threadIdx.x; m < 1024; m += blockDim.x) {
-            tw1[m] = __ldg(&src[m]);
-            tw2[m] = __ldg(&src[TwTable<L>::S1 + 1024 + m]);   // row r = 1 of the last stage's table
-        }
+        for (int m = threadIdx.x; m < 1024 * G; m += blockDim.x)   // rows p >= 1 of the last stage's table
+            tw1[m] = __ldg(&src[m < 1024 ? m : TwTable<L>::S1 + m]);
     }
     if (t == 0) {
         mbar_init(&bars[grp], 1);
@@ -156,16 +161,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows2048(RowsParams p)
         const UnitInfo u = p.units[unit];
         const int64_t rn = r + step;
         const float2 *next = rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr;
-        auto issue_next = [&]() {
-            GroupSync<G>::sync();   // every read of the region is done
-            fence_proxy_async();
-            if (next != nullptr && t == 0) {
-                mbar_expect_tx(&bars[grp], L * sizeof(float2));
-                bulk_copy_g2s(region, next, L * sizeof(float2), &bars[grp]);
-            }
-        };
-        // stage 0 (radix 32, Ns = 1): butterfly t reads x[t + 64 q]
-        // (after a wait that ran out the region is stale; the pair leaves together at the barrier below)
+        // stage 0 (radix 32, Ns = 1): butterfly t reads x[t + T q]
+        // (after a wait that ran out the region is stale; the group leaves together at the barrier below)
         float2 v[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] = region[t + T * q];
@@ -173,44 +170,49 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows2048(RowsParams p)
         GroupSync<G>::sync();   // every read of the landed row is done; gfail is final
         if (*(volatile int *)&gfail[grp] != 0) {
             if (lane == 0) atomicOr(p.status, 2);
-            return;   // the copy into this pair's region never completed; nothing else is in flight
+            return;   // the copy into this group's region never completed; nothing else is in flight
         }
 #pragma unroll
         for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
         GroupSync<G>::sync();
-        // stage 1 (radix 32, Ns = 32): butterfly t = 32 h + k reads y[t + 64 r]
+        // stage 1 (radix 32, Ns = 32): butterfly t = 32 h + k reads y[t + T r]
 #pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = region[spad(t + 64 * q)];
+        for (int q = 0; q < 32; ++q) v[q] = region[spad(t + T * q)];
         GroupSync<G>::sync();   // the exchange below overwrites the region
 #pragma unroll
         for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw1[q * 32 + lane]);
         Dft<32, +1>::run(v);
-        // exchange: warp 0 keeps z0[k + 32 r], r < 16, and receives z1 there;
-        // warp 1 keeps z1[k + 32 r], r >= 16, and receives z0 there
-        if (h == 0) {
+        // exchange: slot ((src G + dst) RW + i) 32 + k holds z_src[k + 32 (RW dst + i)]
 #pragma unroll
-            for (int i = 0; i < 16; ++i) xb[32 * i + lane] = v[16 + i];
-        } else {
+        for (int d = 0; d < G; ++d) {
+            if (d == h) continue;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) xb[512 + 32 * i + lane] = v[i];
+            for (int i = 0; i < RW; ++i) xb[((h * G + d) * RW + i) * 32 + lane] = v[RW * d + i];
         }
         GroupSync<G>::sync();
-        float2 lo[16], hi[16];
+        float2 o[G][RW];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            float2 d[2];
-            d[0] = h == 0 ? v[i] : xb[32 * i + lane];
-            d[1] = h == 0 ? xb[512 + 32 * i + lane] : v[16 + i];
-            d[1] = cmul(d[1], tw2[lane + 32 * (i + 16 * h)]);
-            Dft<2, +1>::run(d);
-            lo[i] = d[0];
-            hi[i] = d[1];
+        for (int i = 0; i < RW; ++i) {
+            const int b = lane + 32 * (RW * h + i);
+            float2 x[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) x[q] = q == h ? v[RW * h + i] : xb[((q * G + h) * RW + i) * 32 + lane];
+#pragma unroll
+            for (int q = 1; q < G; ++q) x[q] = cmul(x[q], tw2[(q - 1) * 1024 + b]);
+            Dft<G, +1>::run(x);
+#pragma unroll
+            for (int q = 0; q < G; ++q) o[q][i] = x[q];
         }
-        issue_next();
-        // epilogue: outputs b = k + 32 (i + 16 h) and b + 1024
+        GroupSync<G>::sync();   // every read of the region is done: start the next row's copy
+        fence_proxy_async();
+        if (next != nullptr && t == 0) {
+            mbar_expect_tx(&bars[grp], L * sizeof(float2));
+            bulk_copy_g2s(region, next, L * sizeof(float2), &bars[grp]);
+        }
+        // epilogue: outputs b + 1024 q, b = k + 32 (RW h + i)
         GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp], nullptr);
-        snk.template store<16>(0, lane + 512 * h, 32, lo);
-        snk.template store<16>(0, lane + 512 * h + 1024, 32, hi);
+#pragma unroll
+        for (int q = 0; q < G; ++q) snk.template store<RW>(0, lane + 32 * RW * h + 1024 * q, 32, o[q]);
         if (MF_DBG(slot < p.n_units && j2 < (1 << p.log2N2), kDbgRows))
             snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + h]);
     }
@@ -475,11 +477,11 @@ static size_t rows_smem_tc() {
 
 MF_DEBUG_READER(dbg_read_rows)
 
-bool pass2_rows_applies(int log2N1) { return log2N1 == 10 || log2N1 == 11; }
+bool pass2_rows_applies(int log2N1) { return log2N1 >= 10 && log2N1 <= 12; }
 
 int pass2_rows_partials(int log2N, int log2N2) {   // partials per unit: one per row and warp
     const int lg1 = log2N - log2N2;
-    return (1 << log2N2) * (lg1 == 11 ? 2 : 1);
+    return lg1 > 10 ? (1 << log2N2) << (lg1 - 10) : (1 << log2N2);   // warps per row: N1 / 1024
 }
 
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
@@ -515,10 +517,14 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
             k_pass2_rows_tc<MF_FFT_TC_BF16><<<gr, kWarps * 32, rows_smem_tc(), st>>>(p);
         else
             k_pass2_rows<1024><<<gr, kWarps * 32, rows_smem<1024>(), st>>>(p);
-    } else {
+    } else if (seg.log2N1 == 11) {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 2 - 1) / (kWarps / 2));
         const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
-        k_pass2_rows2048<<<gr, kWarps * 32, rows2048_smem(), st>>>(p);
+        k_pass2_rows_group<2><<<gr, kWarps * 32, rows_group_smem<2>(), st>>>(p);
+    } else {
+        int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 4 - 1) / (kWarps / 4));
+        const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
+        k_pass2_rows_group<4><<<gr, kWarps * 32, rows_group_smem<4>(), st>>>(p);
     }
     return cudaGetLastError();
 }
@@ -537,7 +543,11 @@ cudaError_t rows_kernel_attributes() {
     e = cudaFuncSetAttribute(k_pass2_rows_tc<MF_FFT_TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rows_smem_tc());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pass2_rows2048, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows2048_smem());
+    e = cudaFuncSetAttribute(k_pass2_rows_group<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rows_group_smem<2>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pass2_rows_group<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rows_group_smem<4>());
 }
 
 }  // namespace mf

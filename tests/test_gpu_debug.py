@@ -30,6 +30,7 @@ CASES = [
     ("n20_fused", 1 << 20, 4096.0, 6, {"MFGB_SCHED": "fused"}),
     ("n21", 1 << 21, 4096.0, 3, {"MFGB_SCHED": "batch"}),
     ("n22", 1 << 22, 4096.0, 2, {"MFGB_SCHED": "batch"}),
+    ("n22_alt_split", 1 << 22, 4096.0, 2, {"MFGB_SCHED": "batch", "MFGB_SPLIT_ALT": "1"}),
 ]
 
 CHILD = r'''

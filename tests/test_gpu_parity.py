@@ -65,12 +65,12 @@ def test_sizes_full_series(mf, lg, fs):
     _full_compare(mf, wl.m1, wl.m2, wl.segments[0])
 
 
-@pytest.mark.parametrize("lg", [18, 19, 20, 21])
+@pytest.mark.parametrize("lg", [18, 19, 20, 21, 22])
 def test_alternative_split_full_series(mf, monkeypatch, lg):
     """The autotuner's alternative four-step split of N (2^18: 256 x 1024,
-    2^19: 1024 x 512, 2^20: 512 x 2048, 2^21: 2048 x 1024 columns x rows)
-    through every kernel form of the per-batch schedule: every rho_j and z
-    against the oracle."""
+    2^19: 1024 x 512, 2^20: 512 x 2048, 2^21: 2048 x 1024, 2^22: 1024 x 4096
+    columns x rows) through every kernel form of the per-batch schedule:
+    every rho_j and z against the oracle."""
     monkeypatch.setenv("MFGB_SCHED", "batch")
     monkeypatch.setenv("MFGB_SPLIT_ALT", "1")
     wl = workloads.small(seed=100 + lg, N=1 << lg, fs=4096.0, n_templates=2 if lg >= 20 else 3,
@@ -493,11 +493,12 @@ def test_persistent_and_batch_schedulers_agree(mf, monkeypatch):
     assert np.array_equal(a[1][:n].view(np.uint8), b[1][:n].view(np.uint8))
 
 
-@pytest.mark.parametrize("lg", [19, 20, 21, 22])
-def test_pass2_rows_and_tiles_agree(mf, monkeypatch, lg):
+@pytest.mark.parametrize("lg,alt", [(19, 0), (20, 0), (21, 0), (22, 0), (20, 1), (22, 1)])
+def test_pass2_rows_and_tiles_agree(mf, monkeypatch, lg, alt):
     """Pass 2 with whole rows per warp group (bulk-copy prefetch; rows of 1024
-    points on one warp, 2048 on a pair) and the per-tile pass 2 give
-    bit-identical peaks and triggers."""
+    points on one warp, 2048 on two, 4096 on four: the alternative splits of
+    2^20 and 2^22) and the per-tile pass 2 give bit-identical peaks and
+    triggers."""
     import torch
     wl = workloads.small(seed=40 + lg, N=1 << lg, fs=4096.0, n_templates=11, m_lo=1.1, m_hi=9.0)
     spec = wl.segments[0]
@@ -505,6 +506,7 @@ def test_pass2_rows_and_tiles_agree(mf, monkeypatch, lg):
     seg = mf.Segment(torch.from_numpy(s32).cuda(), spec.fs)
     bank = mf.Bank(wl.m1, wl.m2)
     monkeypatch.setenv("MFGB_SCHED", "batch")
+    monkeypatch.setenv("MFGB_SPLIT_ALT", str(alt))
     monkeypatch.setenv("MFGB_BATCH", "4")          # ragged batches: 4 + 4 + 3
     a = [x.cpu().numpy().copy() for x in mf.filter_bank(bank, [seg], 3.5, trig_cap=1 << 20)]
     monkeypatch.setenv("MFGB_P2ROWS", "0")
@@ -574,15 +576,17 @@ def test_fused_scheduler_matches_batches_and_recovers(mf, monkeypatch, lg):
     assert np.array_equal(a[1][:int(a[2][0])].view(np.uint8), c[1][:int(a[2][0])].view(np.uint8))
 
 
-@pytest.mark.parametrize("lg,fft", [(20, "fp32"), (21, "fp32"), (20, "tc_fp16"), (19, "tc_bf16")])
-def test_rows_kernel_timeout_reports_and_recovers(mf, monkeypatch, lg, fft):
-    """The per-batch rows kernels (1024- and 2048-point rows, and the
+@pytest.mark.parametrize("lg,fft,alt", [(20, "fp32", 0), (21, "fp32", 0), (22, "fp32", 1), (20, "tc_fp16", 0),
+                                        (19, "tc_bf16", 0)])
+def test_rows_kernel_timeout_reports_and_recovers(mf, monkeypatch, lg, fft, alt):
+    """The per-batch rows kernels (1024-, 2048- and 4096-point rows, and the
     tensor-core form) with one template's row copies or MMA commits withheld
     (test hook): its waits run out, the call reports MF_ETIMEOUT, nothing
     faults, tensor memory is released, and the next call is bit-identical to
     one made before."""
     import torch
     monkeypatch.setenv("MFGB_SCHED", "batch")
+    monkeypatch.setenv("MFGB_SPLIT_ALT", str(alt))
     fm = {"fp32": mf.MF_FFT_FP32, "tc_fp16": mf.MF_FFT_TC_FP16, "tc_bf16": mf.MF_FFT_TC_BF16}[fft]
     wl = workloads.small(seed=40 + lg, N=1 << lg, fs=4096.0, n_templates=5, m_lo=1.2, m_hi=6.0)
     spec = wl.segments[0]
