@@ -13,6 +13,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mf_internal.h"
 #include "mf_tmpl.cuh"
 
@@ -196,7 +198,23 @@ struct mf_bank_s {
 };
 
 // Records an event before a launch when profiling; returns the record index or -1.
+// NVTX ranges: one per public call and one per stage launch of mf_filter_bank
+// (host-side markers a profiler can filter on, e.g. ncu --nvtx --nvtx-include
+// "mf_filter_bank/pass1/"; without a profiler attached they cost a call).
+struct NvtxRange {
+    int level;   // nesting level of this range (negative when no tool tracks ranges)
+    explicit NvtxRange(const char *name) : level(nvtxRangePushA(name)) {}
+    ~NvtxRange() {   // also ends a stage range that an error return left open
+        while (nvtxRangePop() > level) {
+        }
+    }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+static const char *const kStageNames[MF_N_STAGES] = {"setup", "anchors", "pass1", "pass2", "final", "fused"};
+
 static int prof_begin(mf_bank_s *b, int stage, double bytes, cudaStream_t st) {
+    nvtxRangePushA(stage >= 0 && stage < MF_N_STAGES ? kStageNames[stage] : "stage");   // popped by prof_end
     if (!b->prof_on) return -1;
     ProfRec r;
     r.stage = stage;
@@ -209,6 +227,7 @@ static int prof_begin(mf_bank_s *b, int stage, double bytes, cudaStream_t st) {
 }
 static void prof_end(mf_bank_s *b, int idx, cudaStream_t st) {
     if (idx >= 0) cudaEventRecord(b->prof[idx].b, st);
+    nvtxRangePop();
 }
 
 struct mf_segment_s {
@@ -407,6 +426,7 @@ extern "C" int mf_bank_size(mf_bank b, int64_t *n) {
 // ---------------------------------------------------------------------------
 extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const double *psd, double psd_f0,
                                  double psd_S0, int s_on_device, void *cuda_stream, mf_segment *out) {
+    NvtxRange nvtx("mf_segment_upload");
     if (!out) return set_err(MF_EINVAL, "out is NULL");
     *out = nullptr;
     if (!s) return set_err(MF_EINVAL, "s is NULL");
@@ -476,6 +496,7 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
 }
 
 extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device, void *cuda_stream) {
+    NvtxRange nvtx("mf_segment_refresh");
     if (!g || !s) return set_err(MF_EINVAL, "NULL argument");
     int cur = 0;
     cudaGetDevice(&cur);
@@ -733,6 +754,7 @@ static int sm_count() {
 
 extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, float threshold, mf_peak *peaks,
                               mf_trigger *trig, int64_t trig_cap, int64_t *n_trig, void *cuda_stream) {
+    NvtxRange nvtx("mf_filter_bank");
     if (!b || !segs || n_seg < 1) return set_err(MF_EINVAL, "need a bank and n_seg >= 1 segments");
     if (!peaks || !n_trig) return set_err(MF_EINVAL, "peaks and n_trig must not be NULL");
     if (trig_cap < 0 || trig_cap > ((int64_t)1 << 31)) return set_err(MF_EINVAL, "trig_cap out of range");
@@ -1027,6 +1049,7 @@ extern "C" int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int 
 
 extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, int64_t n, int p, float *chisq,
                                int64_t *edges, void *cuda_stream) {
+    NvtxRange nvtx("mf_chisq_series");
     if (!b || !seg || !tmpl || !chisq) return set_err(MF_EINVAL, "NULL argument");
     if (n < 1 || n > ((int64_t)1 << 24)) return set_err(MF_EINVAL, "n = %lld outside [1, 2^24]", (long long)n);
     if (p < 1 || p > kChisqMaxBands) return set_err(MF_EINVAL, "p = %d outside [1, %d]", p, kChisqMaxBands);
@@ -1273,6 +1296,7 @@ extern "C" int mf_bank_check(mf_bank b, void *cuda_stream) {
 // ---------------------------------------------------------------------------
 extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float threshold, int repeats,
                            const char *cache_path, void *cuda_stream) {
+    NvtxRange nvtx("mf_autotune");
     if (!b || !segs || n_seg < 1) return set_err(MF_EINVAL, "need a bank and n_seg >= 1 segments");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (repeats < 1) repeats = 2;
@@ -1506,6 +1530,7 @@ extern "C" int mf_synth_segment(const double *g, int64_t N, double fs, double f_
 // ---------------------------------------------------------------------------
 extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, const double *theta, int64_t n,
                                   const int64_t *band, double *obj, double *grad, void *cuda_stream) {
+    NvtxRange nvtx("mf_refine_triggers");
     if (!seg || !theta || !obj || !grad) return set_err(MF_EINVAL, "NULL argument");
     if (n < 0) return set_err(MF_EINVAL, "n < 0");
     if (n == 0) return MF_OK;
