@@ -443,7 +443,11 @@ int mf_launch_count(int64_t *n);
  * and the algorithmic bytes each launch moves (band reads, exchange write
  * and read; triggers excluded).  mf_bank_profile_read synchronises the events
  * recorded so far and returns, per stage, the summed device milliseconds,
- * bytes and launch counts (host arrays of MF_N_STAGES), then clears them. */
+ * bytes and launch counts (host arrays of MF_N_STAGES), then clears them.
+ * Independently of this switch, every public call pushes an NVTX range named
+ * after it ("mf_filter_bank", ...) and every stage launch of mf_filter_bank a
+ * nested range named after its stage ("setup", "anchors", "pass1", "pass2",
+ * "final", "fused"), for profilers that filter on NVTX. */
 int mf_bank_profile(mf_bank bank, int on);
 
 /* mf_bank_debug_stall -- test hook for the bounded device-side waits.  With
