@@ -464,6 +464,16 @@ int mf_bank_profile(mf_bank bank, int on);
  * invalid.  unit < 0 turns the hook off.  Nothing faults: the GPU context
  * stays usable. */
 int mf_bank_debug_stall(mf_bank bank, int64_t unit, int64_t spin_limit);
+
+/* mf_debug_fail_alloc -- test hook for the error paths of device allocations
+ * (host-side fault injection).  With countdown >= 0, the library's next
+ * `countdown` device allocations (cudaMalloc / cudaMallocAsync made by any
+ * entry point, on any thread) succeed and the one after fails as if the
+ * device were out of memory: that call returns MF_ENOMEM, frees what it had
+ * allocated, leaves its handles as they were before the call (a bank's
+ * workspace is released and regrown by the next call) and the hook disarms.
+ * countdown < 0 disarms it.  Never fails. */
+int mf_debug_fail_alloc(int64_t countdown);
 int mf_bank_profile_read(mf_bank bank, double *ms, double *bytes, int64_t *launches);
 
 #ifdef __cplusplus

@@ -57,6 +57,7 @@ SIGNATURES = {
     "mf_bank_profile": (_I, [_P, _I]),
     "mf_bank_profile_read": (_I, [_P, _P, _P, _P]),
     "mf_bank_debug_stall": (_I, [_P, _I64, _I64]),
+    "mf_debug_fail_alloc": (_I, [_I64]),
     "mf_autotune": (_I, [_P, _P, _I, _F, _I, ctypes.c_char_p, _P]),
 }
 STAGES = ("setup", "anchors", "pass1", "pass2", "final", "fused")

@@ -129,6 +129,35 @@ static double psi_deriv_bound(const double *rec, double f, int n) {
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
+// Device allocations of the library go through these two wrappers so that
+// mf_debug_fail_alloc can make one of them fail as if the device were out of
+// memory (a host-side fault injection for the error paths): after `countdown`
+// further allocations succeed, the next one returns cudaErrorMemoryAllocation
+// without allocating, and the hook disarms.  -1 = disarmed.
+static std::atomic<int64_t> g_fail_alloc{-1};
+static bool alloc_fault() {
+    int64_t v = g_fail_alloc.load();
+    while (v >= 0)
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+template <class T>
+static cudaError_t dev_malloc(T **p, size_t bytes) {
+    if (alloc_fault()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+template <class T>
+static cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st) {
+    if (alloc_fault()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
 struct Workspace {
     int64_t exch_elems = 0, n_t = 0, cap = 0, anc_elems = 0, nblk = 0;
     UnitInfo *units = nullptr;
@@ -332,9 +361,9 @@ static int bank_create_range(const double *m1, const double *m2, int64_t n, cons
                      [&](int x, int y) { return b->fisco[(size_t)x] > b->fisco[(size_t)y]; });
     for (int64_t i = 0; i < n; ++i) b->pos[(size_t)b->order[(size_t)i]] = (int)i;
     cudaGetDevice(&b->device);
-    cudaError_t e = cudaMalloc(&b->d_tmpl, sizeof(double) * rec.size());
+    cudaError_t e = dev_malloc(&b->d_tmpl, sizeof(double) * rec.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tmpl, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = dev_malloc(&b->d_order, sizeof(int) * (size_t)n);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -450,24 +479,24 @@ extern "C" int mf_segment_upload(const float *s, int64_t N, double fs, const dou
     float2 *exch = nullptr, *X = nullptr;
     double *q = nullptr, *btmp = nullptr, *psd_dev = nullptr;
     const int64_t nbt = prefix_block_tmp_count(half);
-    cudaError_t e = cudaMalloc(&g->W, sizeof(float2) * half);
+    cudaError_t e = dev_malloc(&g->W, sizeof(float2) * half);
     if (e == cudaSuccess) {   // pass 1's TMA views of W, both splits
         g->has_tmap[0] = make_w_tensor_maps(g->W, g->log2N, log2_n2(g->log2N), g->w_tmap[0]);
         g->has_tmap[1] = alt_log2n2(g->log2N) > 0 && make_w_tensor_maps(g->W, g->log2N, alt_log2n2(g->log2N), g->w_tmap[1]);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&g->fac, sizeof(float) * half);
-    if (e == cudaSuccess) e = cudaMalloc(&g->P, sizeof(double) * (half + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&g->consts, sizeof(SegConsts));
-    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * N, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&X, sizeof(float2) * (half + 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&q, sizeof(double) * half, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&btmp, sizeof(double) * nbt, st);
+    if (e == cudaSuccess) e = dev_malloc(&g->fac, sizeof(float) * half);
+    if (e == cudaSuccess) e = dev_malloc(&g->P, sizeof(double) * (half + 1));
+    if (e == cudaSuccess) e = dev_malloc(&g->consts, sizeof(SegConsts));
+    if (e == cudaSuccess) e = dev_malloc_async(&exch, sizeof(float2) * N, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&X, sizeof(float2) * (half + 1), st);
+    if (e == cudaSuccess) e = dev_malloc_async(&q, sizeof(double) * half, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&btmp, sizeof(double) * nbt, st);
     if (e == cudaSuccess && !s_on_device) {
-        e = cudaMallocAsync(&s_dev, sizeof(float) * N, st);
+        e = dev_malloc_async(&s_dev, sizeof(float) * N, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s_dev, s, sizeof(float) * N, cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess && psd) {   // kept by the segment for mf_segment_refresh
-        e = cudaMalloc(&g->psd, sizeof(double) * (half + 1));
+        e = dev_malloc(&g->psd, sizeof(double) * (half + 1));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g->psd, psd, sizeof(double) * (half + 1), cudaMemcpyHostToDevice, st);
         psd_dev = g->psd;
@@ -506,8 +535,8 @@ extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device,
     const int64_t N = g->N, half = N / 2;
     if (!g->r_exch) {
         if (capturing) return set_err(MF_EINVAL, "the first mf_segment_refresh of a segment must precede stream capture");
-        cudaError_t e = cudaMalloc(&g->r_exch, sizeof(float2) * N);
-        if (e == cudaSuccess) e = cudaMalloc(&g->r_X, sizeof(float2) * (half + 1));
+        cudaError_t e = dev_malloc(&g->r_exch, sizeof(float2) * N);
+        if (e == cudaSuccess) e = dev_malloc(&g->r_X, sizeof(float2) * (half + 1));
         if (e != cudaSuccess) {
             cudaFree(g->r_exch); cudaFree(g->r_X);
             g->r_exch = nullptr; g->r_X = nullptr;
@@ -518,7 +547,7 @@ extern "C" int mf_segment_refresh(mf_segment g, const float *s, int s_on_device,
     const float *s_use = s;
     if (!s_on_device) {
         if (capturing) return set_err(MF_EINVAL, "host samples cannot be refreshed inside a stream capture");
-        if (!g->r_s) MF_CUDA(cudaMalloc(&g->r_s, sizeof(float) * N));
+        if (!g->r_s) MF_CUDA(dev_malloc(&g->r_s, sizeof(float) * N));
         MF_CUDA(cudaMemcpyAsync(g->r_s, s, sizeof(float) * N, cudaMemcpyHostToDevice, st));
         s_use = g->r_s;
     }
@@ -616,23 +645,23 @@ static int ensure_workspace(mf_bank_s *b, int64_t exch_elems, int64_t cap, int64
     const int64_t nbl = std::max(w.nblk, nblk);
     MF_CUDA(cudaDeviceSynchronize());
     w.release();
-    MF_CUDA(cudaMalloc(&w.units, sizeof(UnitInfo) * b->n));
-    MF_CUDA(cudaMalloc(&w.exch, sizeof(float2) * ne));
-    MF_CUDA(cudaMalloc(&w.anchors, sizeof(float4) * na));
-    MF_CUDA(cudaMalloc(&w.anchors4, sizeof(float) * na));
-    MF_CUDA(cudaMalloc(&w.partials, sizeof(float4) * nbl * b->n));
-    MF_CUDA(cudaMalloc(&w.staged, sizeof(mf_trigger) * ncap));
-    MF_CUDA(cudaMalloc(&w.keys, sizeof(uint64_t) * ncap));
-    MF_CUDA(cudaMalloc(&w.keys_tmp, sizeof(uint64_t) * ncap));
-    MF_CUDA(cudaMalloc(&w.idx_a, sizeof(uint32_t) * ncap));
-    MF_CUDA(cudaMalloc(&w.idx_b, sizeof(uint32_t) * ncap));
-    MF_CUDA(cudaMalloc(&w.ghist, sizeof(uint32_t) * 256 * 8));
-    MF_CUDA(cudaMalloc(&w.tstat, sizeof(uint64_t) * sort_tile_words(ncap)));
-    MF_CUDA(cudaMalloc(&w.tickets, sizeof(unsigned) * 8));
-    MF_CUDA(cudaMalloc(&w.counter, sizeof(unsigned long long)));
-    MF_CUDA(cudaMalloc(&w.status, sizeof(int)));
+    MF_CUDA(dev_malloc(&w.units, sizeof(UnitInfo) * b->n));
+    MF_CUDA(dev_malloc(&w.exch, sizeof(float2) * ne));
+    MF_CUDA(dev_malloc(&w.anchors, sizeof(float4) * na));
+    MF_CUDA(dev_malloc(&w.anchors4, sizeof(float) * na));
+    MF_CUDA(dev_malloc(&w.partials, sizeof(float4) * nbl * b->n));
+    MF_CUDA(dev_malloc(&w.staged, sizeof(mf_trigger) * ncap));
+    MF_CUDA(dev_malloc(&w.keys, sizeof(uint64_t) * ncap));
+    MF_CUDA(dev_malloc(&w.keys_tmp, sizeof(uint64_t) * ncap));
+    MF_CUDA(dev_malloc(&w.idx_a, sizeof(uint32_t) * ncap));
+    MF_CUDA(dev_malloc(&w.idx_b, sizeof(uint32_t) * ncap));
+    MF_CUDA(dev_malloc(&w.ghist, sizeof(uint32_t) * 256 * 8));
+    MF_CUDA(dev_malloc(&w.tstat, sizeof(uint64_t) * sort_tile_words(ncap)));
+    MF_CUDA(dev_malloc(&w.tickets, sizeof(unsigned) * 8));
+    MF_CUDA(dev_malloc(&w.counter, sizeof(unsigned long long)));
+    MF_CUDA(dev_malloc(&w.status, sizeof(int)));
     MF_CUDA(cudaMemset(w.status, 0, sizeof(int)));
-    MF_CUDA(cudaMalloc(&w.ctl, sizeof(unsigned) * (4 + 3 * b->n)));
+    MF_CUDA(dev_malloc(&w.ctl, sizeof(unsigned) * (4 + 3 * b->n)));
     w.exch_elems = ne; w.n_t = b->n; w.cap = ncap; w.anc_elems = na; w.nblk = nbl;
     return MF_OK;
 }
@@ -916,7 +945,7 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             P.stats = nullptr;
             const bool want_stats = getenv("MFGB_SCHED_STATS") != nullptr && !capturing;
             if (want_stats) {
-                MF_CUDA(cudaMallocAsync(&P.stats, sizeof(unsigned long long) * 12, st));
+                MF_CUDA(dev_malloc_async(&P.stats, sizeof(unsigned long long) * 12, st));
                 MF_CUDA(cudaMemsetAsync(P.stats, 0, sizeof(unsigned long long) * 12, st));
             }
             double by = 16.0 * (double)sd.N * n_t;
@@ -1033,7 +1062,7 @@ extern "C" int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int 
     if (stream_capturing(st)) return set_err(MF_EINVAL, "mf_fft_c2c allocates its exchange and cannot be captured");
     const int64_t chunk = std::min<int64_t>({batch, std::max<int64_t>(1, kExchBudget / (8 * N)), 65535});
     float2 *exch = nullptr;
-    cudaError_t e = cudaMallocAsync(&exch, sizeof(float2) * N * chunk, st);
+    cudaError_t e = dev_malloc_async(&exch, sizeof(float2) * N * chunk, st);
     int launches = 0;
     for (int64_t b0 = 0; b0 < batch && e == cudaSuccess; b0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, batch - b0);
@@ -1075,17 +1104,17 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     const int64_t batch = rows ? std::max<int64_t>(1, std::min<int64_t>(n, budget / (8 * seg->N * (p + 1))))
                                : std::min<int64_t>(n, choose_batch(seg->N, n, b->tuned_exch));
     const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
-    if (rows && !b->chi_status) MF_CUDA(cudaMalloc(&b->chi_status, sizeof(int)));
+    if (rows && !b->chi_status) MF_CUDA(dev_malloc(&b->chi_status, sizeof(int)));
     if (b->chi_status) MF_CUDA(cudaMemsetAsync(b->chi_status, 0, sizeof(int), st));
     UnitInfo *all = nullptr, *units = nullptr;
     float4 *anc = nullptr;
     float *anc4 = nullptr;
     float2 *exch = nullptr;
-    cudaError_t e = cudaMallocAsync(&all, sizeof(UnitInfo) * n_t, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&units, sizeof(UnitInfo) * (size_t)(p + 1) * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&anc, sizeof(float4) * man * batch, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&anc4, sizeof(float) * man * batch, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * seg->N * batch * (rows ? p + 1 : 1), st);
+    cudaError_t e = dev_malloc_async(&all, sizeof(UnitInfo) * n_t, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&units, sizeof(UnitInfo) * (size_t)(p + 1) * n, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&anc, sizeof(float4) * man * batch, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&anc4, sizeof(float) * man * batch, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&exch, sizeof(float2) * seg->N * batch * (rows ? p + 1 : 1), st);
     int launches = 0;
     if (e == cudaSuccess) e = launch_units(sd, b->d_tmpl, n_t, b->params.f_low, 0.f, lgD, nullptr, all, st);
     if (e == cudaSuccess) e = launch_chisq_units(sd, all, n_t, tmpl, (int)n, p, units, edges, st);
@@ -1153,7 +1182,7 @@ extern "C" int mf_cluster_triggers(const mf_trigger *trig, const int64_t *n_trig
     cudaError_t e = cudaSuccess;
     auto get = [&](auto **ptr, size_t bytes) {
         void *q = nullptr;
-        if (e == cudaSuccess) e = cudaMallocAsync(&q, bytes, st);
+        if (e == cudaSuccess) e = dev_malloc_async(&q, bytes, st);
         if (e == cudaSuccess) bufs.push_back(q);
         *ptr = (std::remove_pointer_t<decltype(ptr)>)q;
     };
@@ -1207,7 +1236,7 @@ extern "C" int mf_chisq_points(mf_bank b, const mf_segment *segs, int n_seg, con
     const int64_t chunk = std::min<int64_t>(n, 65535);
     const int bpr = (int)std::max<int64_t>(4, std::min<int64_t>(64, (4 * (int64_t)sm_count() + chunk - 1) / chunk));
     double2 *partial = nullptr;
-    cudaError_t e = cudaMallocAsync(&partial, sizeof(double2) * (size_t)bpr * chunk * p, st);
+    cudaError_t e = dev_malloc_async(&partial, sizeof(double2) * (size_t)bpr * chunk * p, st);
     int launches = 0;
     for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += chunk) {
         const int64_t m = std::min<int64_t>(chunk, n - i0);
@@ -1335,9 +1364,18 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     mf_peak *pk = nullptr;
     mf_trigger *tr = nullptr;
     int64_t *nt = nullptr;
-    MF_CUDA(cudaMalloc(&pk, sizeof(mf_peak) * b->n * n_seg));
-    MF_CUDA(cudaMalloc(&tr, sizeof(mf_trigger) * cap));
-    MF_CUDA(cudaMalloc(&nt, sizeof(int64_t)));
+    {
+        cudaError_t ea = dev_malloc(&pk, sizeof(mf_peak) * b->n * n_seg);
+        if (ea == cudaSuccess) ea = dev_malloc(&tr, sizeof(mf_trigger) * cap);
+        if (ea == cudaSuccess) ea = dev_malloc(&nt, sizeof(int64_t));
+        if (ea != cudaSuccess) {
+            cudaFree(pk);
+            cudaFree(tr);
+            cudaFree(nt);
+            return set_err(ea == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA, "autotune: %s",
+                           cudaGetErrorString(ea));
+        }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1494,15 +1532,15 @@ extern "C" int mf_synth_segment(const double *g, int64_t N, double fs, double f_
     double *inj_dev = nullptr, *q = nullptr, *P = nullptr, *btmp = nullptr, *psd_dev = nullptr;
     float2 *Y = nullptr, *exch = nullptr;
     const int64_t nbt = prefix_block_tmp_count(half);
-    cudaError_t e = cudaMallocAsync(&inj_dev, sizeof(double) * rec.size(), st);
+    cudaError_t e = dev_malloc_async(&inj_dev, sizeof(double) * rec.size(), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(inj_dev, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&q, sizeof(double) * half, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&P, sizeof(double) * (half + 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&btmp, sizeof(double) * nbt, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&Y, sizeof(float2) * half, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&exch, sizeof(float2) * N, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&q, sizeof(double) * half, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&P, sizeof(double) * (half + 1), st);
+    if (e == cudaSuccess) e = dev_malloc_async(&btmp, sizeof(double) * nbt, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&Y, sizeof(float2) * half, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&exch, sizeof(float2) * N, st);
     if (e == cudaSuccess && psd) {
-        e = cudaMallocAsync(&psd_dev, sizeof(double) * (half + 1), st);
+        e = dev_malloc_async(&psd_dev, sizeof(double) * (half + 1), st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(psd_dev, psd, sizeof(double) * (half + 1), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess) e = launch_psd_weights(nullptr, psd_dev, psd_f0, psd_S0, N, fs, q, st);
@@ -1546,7 +1584,7 @@ extern "C" int mf_refine_triggers(mf_segment seg, const mf_bank_params *params, 
     const SegDev sd = seg_dev(seg);
     const int bpr = refine_blocks_for(n, sm_count());
     double *partial = nullptr;
-    cudaError_t e = cudaMallocAsync(&partial, refine_scratch_bytes(n, bpr), st);
+    cudaError_t e = dev_malloc_async(&partial, refine_scratch_bytes(n, bpr), st);
     if (e == cudaSuccess) e = launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial, bpr, st);
     if (e == cudaSuccess) count_launches(refine_launches(n));
     if (partial) cudaFreeAsync(partial, st);
@@ -1580,7 +1618,7 @@ extern "C" int mf_refine_triggers_multi(const mf_segment *segs, int n_seg, const
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int bpr = refine_blocks_for(n, sm_count());
     double *partial = nullptr;
-    cudaError_t e = cudaMallocAsync(&partial, refine_scratch_bytes(n, bpr), st);
+    cudaError_t e = dev_malloc_async(&partial, refine_scratch_bytes(n, bpr), st);
     if (e == cudaSuccess)
         e = launch_refine_multi(sd.data(), n_seg, row_seg, p.f_low, p.phase_mode, theta, n, band, obj, grad, partial,
                                 bpr, st);
@@ -1652,5 +1690,10 @@ extern "C" int mf_refine_triggers_static(mf_segment seg, const mf_bank_params *p
     MF_CUDA(launch_refine(sd, p.f_low, p.phase_mode, theta, n, band, obj, grad, scratch, kRefineStaticBpr,
                           (cudaStream_t)cuda_stream));
     count_launches(refine_launches(n));
+    return MF_OK;
+}
+
+extern "C" int mf_debug_fail_alloc(int64_t countdown) {
+    g_fail_alloc.store(countdown < 0 ? -1 : countdown);
     return MF_OK;
 }
