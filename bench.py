@@ -65,11 +65,18 @@ def _args():
     ap.add_argument("--fft-mode", default="fp32", choices=["fp32", "tc_fp16", "tc_bf16"],
                     help="FFT form of the scale workload: FP32 butterflies (the benchmark line) or the tensor-core "
                          "DFT stage of pass 2 with FP16 / BF16 splits (precision-sweep forms)")
+    ap.add_argument("--seed", type=int, default=0, help="seed of the synthetic workload (bank order, noise, injections)")
+    ap.add_argument("--config", type=int, default=0, choices=[0, 2, 3, 4, 5],
+                    help="the workload by its configuration number: 2 = scale (the benchmark line), 3 = uneven, "
+                         "4 = precision, 5 = refine (config 1, the 16-template case, is a parity test)")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "uneven", "precision", "refine", "chisq", "fft", "events"],
                     help="scale: the benchmark line; the others print their own measurement line "
                          "(uneven bank over mixed segment lengths, phase precision forms, trigger refinement)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.config:
+        a.workload = {2: "scale", 3: "uneven", 4: "precision", 5: "refine"}[a.config]
+    return a
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -242,7 +249,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import workloads
-    wl = workloads.scale(0)
+    wl = workloads.scale(args.seed)
     import numpy as np
     import oracle
     oracle.build()
@@ -270,7 +277,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections)",
-            "config": {"workload": WORKLOAD, "step_sample_templates": per_step},
+            "config": {"workload": WORKLOAD, "seed": args.seed, "step_sample_templates": per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle",
                              "sample": "%d random templates of 1024 per step, full N=2^20 segment" % per_step},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -309,7 +316,7 @@ def run_uneven(args, mf, torch, dev):
     (2^19 and 2^20 segments; the others per batch), per-template launches,
     and the autotuner's choice."""
     import workloads
-    wl = workloads.uneven(0)
+    wl = workloads.uneven(args.seed)
     segs = [mf.Segment(mf.synth_segment(sp.normals(), sp.N, sp.fs, wl.f_low, sp.injections), sp.fs)
             for sp in wl.segments]
     bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
@@ -394,7 +401,7 @@ def run_precision(args, mf, torch, dev):
     oracle-synthesised input)."""
     import numpy as np
     import workloads
-    wl = workloads.scale(0)
+    wl = workloads.scale(args.seed)
     spec = wl.segments[0]
     seg = mf.Segment(mf.synth_segment(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections), spec.fs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -547,7 +554,7 @@ def run_events(args, mf, torch, dev):
     stage over the timed steps."""
     import numpy as np
     import workloads
-    wl = workloads.scale(0)
+    wl = workloads.scale(args.seed)
     spec = wl.segments[0]
     seg = mf.Segment(mf.synth_segment(spec.normals(), spec.N, spec.fs, wl.f_low, spec.injections), spec.fs)
     bank = mf.Bank(wl.m1, wl.m2, f_low=wl.f_low)
@@ -621,7 +628,7 @@ def run_chisq(args, mf, torch, dev):
     GPU's chi^2 error on the same (oracle-synthesised) input."""
     import numpy as np
     import workloads
-    wl = workloads.scale(0)
+    wl = workloads.scale(args.seed)
     spec = wl.segments[0]
     N = spec.N
     s_dev = mf.synth_segment(spec.normals(), N, spec.fs, wl.f_low, spec.injections)
@@ -789,7 +796,7 @@ def run_refine(args, mf, torch, dev):
     throughput, the SNR gain and the recovered-mass error."""
     import numpy as np
     import workloads
-    wl = workloads.refine_bank(0)
+    wl = workloads.refine_bank(args.seed)
     fs = wl.segments[0].fs
     N = wl.segments[0].N
     segs = [mf.Segment(mf.synth_segment(sp.normals(), sp.N, sp.fs, wl.f_low, sp.injections), sp.fs)
@@ -958,7 +965,7 @@ def main():
     import paper_0906_4175_gb300 as mf
     import workloads
 
-    wl = workloads.scale(seed=rank)
+    wl = workloads.scale(seed=args.seed + rank)
     if args.templates > 0:
         wl.m1, wl.m2 = wl.m1[:args.templates], wl.m2[:args.templates]
     spec = wl.segments[0]
@@ -1200,7 +1207,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded coloured Gaussian noise, Eq. 2 PSD, 8 injections; no LIGO data)",
-            "config": {"workload": WORKLOAD, "templates": wl.n_templates, "N": spec.N, "fs": spec.fs,
+            "config": {"workload": WORKLOAD, "seed": args.seed, "templates": wl.n_templates, "N": spec.N, "fs": spec.fs,
                        "segments": 1, "threshold": wl.threshold, "n_trig_per_step": n_trig,
                        "l2": "flushed before every timed step (256 MiB write)",
                        "step": "mf_segment_refresh (device s) + mf_filter_bank, one CUDA-graph replay"
