@@ -293,7 +293,7 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
 /* mf_autotune -- times the candidate schedules of mf_filter_bank for this
  * bank on these segments (the persistent scheduler with 55/60/65% of the SMs
  * starting on template generation + column FFTs; where some segment is
- * N = 2^19 or 2^20, the fused scheduler with 55/60/65% of the SMs on pass 1;
+ * N = 2^19 or 2^20, the fused scheduler with 58/60/62% of the SMs on pass 1;
  * and per-batch launches with
  * 128 MiB..1 GiB of exchange in flight, i.e. 16..128 templates per batch at
  * N = 2^20 and proportionally more at shorter segments, each with the kernel
@@ -336,6 +336,8 @@ int mf_autotune(mf_bank bank, const mf_segment *segs, int n_seg, float threshold
  *   MFGB_SPLIT=x                 fraction of the SMs the persistent scheduler
  *                                starts on queue 1 (anchors + pass 1), or the
  *                                fused scheduler gives to pass 1
+ *   MFGB_FUSED_ROLE=cta          the fused scheduler's first CTAs run pass 1
+ *                                instead of whole SMs (both CTAs of an SM)
  *   MFGB_P1PF=0                  pass 1 one CTA per column tile instead of the
  *                                persistent kernel with staged inputs
  *   MFGB_P1TILE=half             the persistent pass 1 with tiles of half the

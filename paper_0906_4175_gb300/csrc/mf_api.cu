@@ -1353,7 +1353,7 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
         b->sched = saved;
     }
     if (any_fused)
-        for (double sp : {0.55, 0.60, 0.65}) cands.push_back({2, 0, sp, 0, 0});
+        for (double sp : {0.58, 0.60, 0.62}) cands.push_back({2, 0, sp, 0, 0});
     for (int64_t mib : {128, 256, 512, 1024}) {
         cands.push_back({1, mib << 20, 0.60, 0, 0});
         if (any_pf) cands.push_back({1, mib << 20, 0.60, 1, 0});

@@ -2,12 +2,13 @@
 // runs pass 1 and pass 2 of every (template, segment) unit through a ring of S
 // exchange slots small enough to stay in L2.
 //
-// The grid holds the resident CTAs (two per SM).  CTAs [0, n_p1) are pass-1
-// workers: they loop over the column tiles of the units in order (one atomic
+// The grid holds the resident CTAs (two per SM).  The CTAs of a fraction of the
+// SMs (the split) are pass-1 workers: they loop over the column tiles of the
+// units in order (one atomic
 // queue), exactly as the per-batch k_pass1_pf does -- the next tile's W by TMA
 // and its anchor rows by bulk copy, issued under the current tile's second
-// stage -- and write unit u's exchange into ring slot u % S.  The other CTAs are
-// pass-2 workers: every warp takes rows from a second atomic queue, exactly as
+// stage -- and write unit u's exchange into ring slot u % S.  The CTAs of the
+// other SMs are pass-2 workers: every warp takes rows from a second atomic queue, exactly as
 // k_pass2_rows does (row bulk-copied into the warp's region, the next row's
 // copy issued under the current row's last stage, rho epilogue, one partial per
 // row).  Dependencies, both on per-unit counters:
@@ -23,6 +24,7 @@
 // the launch (slot u of the anchor array is unit u).  The arithmetic of every
 // tile and row is that of the per-batch kernels, so results are bit-identical.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "mf_pass1.cuh"
@@ -67,6 +69,7 @@ struct FusedParams {
     unsigned *done2;       // per unit: rows copied out of the ring
     int S;                 // ring slots
     int n_p1;              // CTAs [0, n_p1) run pass 1
+    float sm_frac;         // > 0: roles by SM instead (see k_filter_fused)
 };
 
 // ---------------------------------------------------------------------------
@@ -103,7 +106,7 @@ __device__ __forceinline__ void fused_p1(const FusedParams &F, const CUtensorMap
     int item = s_next;
     uint32_t parity = 0;
     bool in_flight = false;                      // a copy of this CTA has not been waited for
-    int pending = -1;                            // unit whose finished tile is released at the next barrier
+    int pending = -1;                            // unit whose finished tile is released in the next item
     int4 band = make_int4(0, 0, 0, 0);
     __syncthreads();                             // every thread has read s_next
     if (item < p.n_items) {
@@ -126,14 +129,17 @@ __device__ __forceinline__ void fused_p1(const FusedParams &F, const CUtensorMap
             }
             break;
         }
-        if (threadIdx.x == 0 && pending >= 0) {   // the previous tile's writes, ordered by the barrier
+        const int next = s_next;
+        const int4 nband = next < p.n_items ? pf_band(p, next / TILES) : make_int4(0, 0, 0, 0);
+        pf_stage1<L, C, LG1>(tile, seq, t, k_lo, k_hi, p.log2D, wbuf, abuf, abuf4, sq);
+        // release the previous tile: its writes were ordered by the barrier above, and by now (a stage later)
+        // they have mostly landed, so the fence waits little; it precedes the slot wait below, so a CTA never
+        // waits while holding an unreleased tile
+        if (threadIdx.x == 0 && pending >= 0) {
             __threadfence();
             atomicAdd(&F.done1[pending], 1u);
             pending = -1;
         }
-        const int next = s_next;
-        const int4 nband = next < p.n_items ? pf_band(p, next / TILES) : make_int4(0, 0, 0, 0);
-        pf_stage1<L, C, LG1>(tile, seq, t, k_lo, k_hi, p.log2D, wbuf, abuf, abuf4, sq);
         // ring slot u % S is free once every row of unit u - S has been copied out
         bool slot_ok = true;
         if (threadIdx.x == 0 && u >= F.S)
@@ -166,32 +172,24 @@ __device__ __forceinline__ void fused_p1(const FusedParams &F, const CUtensorMap
 // ---------------------------------------------------------------------------
 // pass-2 worker (each warp on its own; 1024-point rows)
 // ---------------------------------------------------------------------------
-// Rows are handed out kRowChunk at a time (consecutive rows, of one unit: N2
-// is a multiple of the chunk); lane 0 of a warp keeps its chunk.  One row at a
-// time spreads each unit's rows over the most warps: chunks of four rows left
-// the pass-2 warps waiting for units in turn and measured 10 % slower.
-constexpr int kRowChunk = 1;
-struct RowCursor {
-    int64_t r = 0, end = 0;   // rows [r, end) of the current chunk
-    int checked = -1;         // unit whose column tiles were last seen all written
-};
+// Rows are handed out one at a time from an atomic queue (one row at a time
+// spreads each unit's rows over the most warps: chunks of four rows left the
+// pass-2 warps waiting for units in turn and measured 10 % slower).  Lane 0
+// claims a warp's next row at the top of the current one and reads the claim
+// after stage 0, so the atomic's latency overlaps the row's first stage.
+__device__ __forceinline__ unsigned fz_claim_row(const FusedParams &F) { return atomicAdd(&F.ctl[1], 1u); }
 
-// lane 0: the next row index, and its unit's column tiles all written (false: abort)
-__device__ __forceinline__ bool fz_take_row(const FusedParams &F, unsigned tiles, int64_t total, RowCursor &c,
-                                            int64_t &r) {
+// lane 0: row r's unit has all its column tiles written (false: abort)
+__device__ __forceinline__ bool fz_row_ready(const FusedParams &F, unsigned tiles, int64_t total, int &checked,
+                                             int64_t r) {
     const RowsParams &p = F.p2;
-    if (c.r >= c.end) {
-        c.r = (int64_t)atomicAdd(&F.ctl[1], (unsigned)kRowChunk);
-        c.end = c.r + kRowChunk;
-    }
-    r = c.r++;
     if (r >= total) return true;
     const int u = (int)(r >> p.log2N2);
-    if (u == c.checked) return true;
+    if (u == checked) return true;
     const unsigned target = tiles + (u == p.stall_unit ? 1u : 0u);   // the test hook never completes
     if (!fz_wait_geq(&F.done1[u], target, F.ctl + 2, p.status, p.spin_limit)) return false;
     fence_proxy_async_global();
-    c.checked = u;
+    checked = u;
     return true;
 }
 
@@ -216,10 +214,13 @@ __device__ __forceinline__ void fused_p2(const FusedParams &F, unsigned n_tiles,
     mbar_fence_init();
     __syncthreads();
     const int64_t total = (int64_t)p.n_units << p.log2N2;
-    RowCursor cur;
+    int checked = -1;
     int64_t r = 0;
     bool ok = true;
-    if (t == 0) ok = fz_take_row(F, n_tiles, total, cur, r);
+    if (t == 0) {
+        r = fz_claim_row(F);
+        ok = fz_row_ready(F, n_tiles, total, checked, r);
+    }
     ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
     r = __shfl_sync(0xffffffffu, r, 0);
     if (!ok) return;
@@ -230,6 +231,8 @@ __device__ __forceinline__ void fused_p2(const FusedParams &F, unsigned n_tiles,
     bool in_flight = r < total;
     uint32_t parity = 0;
     while (r < total) {
+        unsigned claim = 0;
+        if (t == 0) claim = fz_claim_row(F);   // read after stage 0
         long long it = 0;
         bool got = true;
         while (!mbar_try_wait(&bars[w], parity)) {
@@ -260,7 +263,10 @@ __device__ __forceinline__ void fused_p2(const FusedParams &F, unsigned n_tiles,
         // the next row, once its unit is written (its copy is issued in the last stage)
         int64_t rn = 0;
         bool nok = true;
-        if (t == 0) nok = fz_take_row(F, n_tiles, total, cur, rn);
+        if (t == 0) {
+            rn = claim;
+            nok = fz_row_ready(F, n_tiles, total, checked, rn);
+        }
         nok = __shfl_sync(0xffffffffu, (int)nok, 0) != 0;
         rn = __shfl_sync(0xffffffffu, rn, 0);
         const bool issue = nok && rn < total;
@@ -282,7 +288,17 @@ __device__ __forceinline__ void fused_p2(const FusedParams &F, unsigned n_tiles,
 template <int L, int C, int LG1>
 __global__ void __launch_bounds__(256, 2) k_filter_fused(const FusedParams F, const __grid_constant__ CUtensorMap wmap) {
     extern __shared__ __align__(128) float2 fz_smem[];
-    if ((int)blockIdx.x < F.n_p1) fused_p1<L, C, LG1>(F, &wmap, fz_smem);
+    // Roles: by SM (both CTAs of an SM run the same pass, so each SM's instruction cache holds one pass's
+    // code; SMs with %smid below the split fraction of %nsmid run pass 1, CTA 0 always pass 1 and the last
+    // CTA always pass 2, so each role has a worker), or the first n_p1 CTAs on pass 1.
+    bool p1 = (int)blockIdx.x < F.n_p1;
+    if (F.sm_frac > 0.f) {
+        unsigned smid, nsmid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+        p1 = blockIdx.x == 0 || (blockIdx.x + 1 < gridDim.x && (float)smid < F.sm_frac * (float)nsmid);
+    }
+    if (p1) fused_p1<L, C, LG1>(F, &wmap, fz_smem);
     else fused_p2(F, (unsigned)((1 << LG1) / C), fz_smem);
 }
 
@@ -361,6 +377,10 @@ cudaError_t launch_fused(const SegDev &seg, const UnitInfo *units, int n_units, 
     F.S = S;
     const int grid = fused_grid(seg.log2N);
     F.n_p1 = std::min(grid - 1, std::max(1, (int)(split * grid + 0.5)));
+    {   // roles by SM unless MFGB_FUSED_ROLE=cta asks for the first n_p1 CTAs
+        const char *e = getenv("MFGB_FUSED_ROLE");
+        F.sm_frac = (e && e[0] == 'c') ? 0.f : (float)split;
+    }
     FusedOp op{&F, (const CUtensorMap *)seg.w_tmap, st};
     return dispatch_split(seg.log2N, op);
 }
