@@ -1069,8 +1069,10 @@ def main():
     d_ms, d_bytes, d_n = stages[dom]
     peak, peak_kind = _hbm_peak()
     achieved = d_bytes / (d_ms / 1e3) / 1e9
-    traffic, _ = _ncu_traffic(dom)
+    traffic, traffic_tmpl = _ncu_traffic(dom)
     tmpl_per_launch = wl.n_templates * args.steps / max(1, d_n) if dom in ("pass1", "pass2", "anchors", "fused") else None
+    if traffic is not None and traffic_tmpl and tmpl_per_launch:
+        traffic *= tmpl_per_launch / traffic_tmpl   # the exchange traffic grows with the templates per launch
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
             "timed_on": "the eager steps (same workload, per-stage CUDA events on the launching stream)",

@@ -295,13 +295,13 @@ int mf_bank_check(mf_bank bank, void *cuda_stream);
  * starting on template generation + column FFTs; where some segment is
  * N = 2^19 or 2^20, the fused scheduler with 58/60/62% of the SMs on pass 1;
  * and per-batch launches with
- * 128 MiB..1 GiB of exchange in flight, i.e. 16..128 templates per batch at
+ * 512 MiB..8 GiB of exchange in flight, i.e. 64..1024 templates per batch at
  * N = 2^20 and proportionally more at shorter segments, each with the kernel
  * forms of the two passes: pass 1 persistent with the next tile's inputs
  * staged by TMA and bulk copies, in tiles of C = 8192/N2 columns or of C/2
  * (the CTA tile), or one CTA per column tile; pass 2 in warp-owned rows
  * with bulk-copy prefetch, or one CTA per row tile) and keeps the fastest in
- * the bank for later calls (the default is per-batch launches with 1 GiB, the
+ * the bank for later calls (the default is per-batch launches with 4 GiB, the
  * staged pass 1 and the row pass 2 where they apply).  Before those it picks,
  * per segment length N = 2^18 .. 2^22, the four-step split N = N1 x N2 of the
  * per-batch schedule: the balanced one (N2 = 2^floor(log2 N / 2) columns) or

@@ -615,10 +615,13 @@ static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
 }
 
 // templates in flight per batch (exchange ring of batch * N complex64)
-// Default exchange budget of the per-batch launches: 1 GiB (128 templates in
-// flight at N = 2^20), the fastest budget measured on GB300 at 2^18..2^21;
-// mf_autotune replaces it per bank.
-constexpr int64_t kExchBudget = (int64_t)1 << 30;
+// Default exchange budget of the per-batch launches: 4 GiB (512 templates in
+// flight at N = 2^20).  Fewer, longer launches leave fewer partly idle tails
+// (bench workload: 1 GiB 247k, 2 GiB 250k, 4 GiB 252k, 8 GiB 253k
+// templates/s); mf_autotune replaces it per bank.  mf_chisq_series and
+// mf_fft_c2c, which allocate their exchange per call, default to 1 GiB.
+constexpr int64_t kExchBudget = (int64_t)4 << 30;
+constexpr int64_t kScratchBudget = (int64_t)1 << 30;
 
 static int64_t choose_batch(int64_t N, int64_t n_t, int64_t tuned_exch) {
     int64_t b = (tuned_exch > 0 ? tuned_exch : kExchBudget) / (8 * N);
@@ -1060,7 +1063,7 @@ extern "C" int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int 
         return MF_OK;
     }
     if (stream_capturing(st)) return set_err(MF_EINVAL, "mf_fft_c2c allocates its exchange and cannot be captured");
-    const int64_t chunk = std::min<int64_t>({batch, std::max<int64_t>(1, kExchBudget / (8 * N)), 65535});
+    const int64_t chunk = std::min<int64_t>({batch, std::max<int64_t>(1, kScratchBudget / (8 * N)), 65535});
     float2 *exch = nullptr;
     cudaError_t e = dev_malloc_async(&exch, sizeof(float2) * N * chunk, st);
     int launches = 0;
@@ -1100,9 +1103,9 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     // 1024-point rows: every sub-band's exchange of a batch first, then one
     // rows kernel over all of them (p + 1 exchanges per template in flight)
     const bool rows = chisq_rows_applies(seg->log2N);
-    const int64_t budget = b->tuned_exch > 0 ? b->tuned_exch : kExchBudget;
+    const int64_t budget = b->tuned_exch > 0 ? b->tuned_exch : kScratchBudget;
     const int64_t batch = rows ? std::max<int64_t>(1, std::min<int64_t>(n, budget / (8 * seg->N * (p + 1))))
-                               : std::min<int64_t>(n, choose_batch(seg->N, n, b->tuned_exch));
+                               : std::min<int64_t>(n, choose_batch(seg->N, n, budget));
     const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
     if (rows && !b->chi_status) MF_CUDA(dev_malloc(&b->chi_status, sizeof(int)));
     if (b->chi_status) MF_CUDA(cudaMemsetAsync(b->chi_status, 0, sizeof(int), st));
@@ -1354,7 +1357,7 @@ extern "C" int mf_autotune(mf_bank b, const mf_segment *segs, int n_seg, float t
     }
     if (any_fused)
         for (double sp : {0.58, 0.60, 0.62}) cands.push_back({2, 0, sp, 0, 0});
-    for (int64_t mib : {128, 256, 512, 1024}) {
+    for (int64_t mib : {512, 1024, 2048, 4096, 8192}) {
         cands.push_back({1, mib << 20, 0.60, 0, 0});
         if (any_pf) cands.push_back({1, mib << 20, 0.60, 1, 0});
         if (any_pf) cands.push_back({1, mib << 20, 0.60, 2, 0});
