@@ -618,8 +618,9 @@ static int choose_log2D(const mf_bank_s *b, const mf_segment_s *g) {
 // Default exchange budget of the per-batch launches: 4 GiB (512 templates in
 // flight at N = 2^20).  Fewer, longer launches leave fewer partly idle tails
 // (bench workload: 1 GiB 247k, 2 GiB 250k, 4 GiB 252k, 8 GiB 253k
-// templates/s); mf_autotune replaces it per bank.  mf_chisq_series and
-// mf_fft_c2c, which allocate their exchange per call, default to 1 GiB.
+// templates/s; the chi^2 series at p = 16: 1 GiB 13.3k, 4 GiB 14.4k
+// templates/s); mf_autotune replaces it per bank.  mf_fft_c2c, which
+// allocates its exchange per call, keeps 1 GiB.
 constexpr int64_t kExchBudget = (int64_t)4 << 30;
 constexpr int64_t kScratchBudget = (int64_t)1 << 30;
 
@@ -1103,7 +1104,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     // 1024-point rows: every sub-band's exchange of a batch first, then one
     // rows kernel over all of them (p + 1 exchanges per template in flight)
     const bool rows = chisq_rows_applies(seg->log2N);
-    const int64_t budget = b->tuned_exch > 0 ? b->tuned_exch : kScratchBudget;
+    const int64_t budget = b->tuned_exch > 0 ? b->tuned_exch : kExchBudget;
     const int64_t batch = rows ? std::max<int64_t>(1, std::min<int64_t>(n, budget / (8 * seg->N * (p + 1))))
                                : std::min<int64_t>(n, choose_batch(seg->N, n, budget));
     const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
