@@ -861,6 +861,10 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const int man = (int)anchor_slot_records(segs[s]->log2N, lgD);   // records per anchor slot
         const bool rows = (!use_persistent(b, segs[s]) && use_rows(b, segs[s], sd.log2N1)) || use_fused(b, segs[s]);
         const int nbk = rows ? pass2_rows_partials(sd.log2N, sd.log2N2) : pass2_blocks(sd.log2N, sd.log2N2);
+        // per-batch 1024-point FP32 rows: each row keeps only its maximum and
+        // the batch's peaks are found right after its pass 2 (launch_peaks_rows)
+        const bool peaks_later = rows && !use_persistent(b, segs[s]) && !use_fused(b, segs[s]) &&
+                                 pass2_rows_peaks_later(sd.log2N1, b->params.fft_mode);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
         // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
         std::vector<double> band_bytes, anc_bytes;
@@ -1028,17 +1032,25 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
             if (rows)
                 MF_CUDA(launch_pass2_rows(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                           std::max<int64_t>(trig_cap, 0), w.status, b->spin_limit, sm_count(),
-                                          b->params.fft_mode, stall_pos, st));
+                                          b->params.fft_mode, stall_pos, peaks_later, st));
             else
                 MF_CUDA(launch_pass2(sd, w.units, u0, nb, w.exch, w.partials, s, kl, w.staged, w.keys, w.counter,
                                      std::max<int64_t>(trig_cap, 0), st));
             prof_end(b, pi, st);
             count_launches(2);
+            if (peaks_later) {   // the batch's peaks, while its exchange is still there
+                pi = prof_begin(b, MF_STAGE_FINAL, 16.0 * nbk * nb, st);
+                MF_CUDA(launch_peaks_rows(sd, w.units, u0, nb, n_t, w.exch, w.partials, s, n_seg, peaks, st));
+                prof_end(b, pi, st);
+                count_launches(1);
+            }
         }
-        pi = prof_begin(b, MF_STAGE_FINAL, 16.0 * nbk * n_t, st);
-        MF_CUDA(launch_reduce_peaks(sd, w.units, n_t, w.partials, nbk, s, n_seg, peaks, st));
-        prof_end(b, pi, st);
-        count_launches(1);
+        if (!peaks_later) {
+            pi = prof_begin(b, MF_STAGE_FINAL, 16.0 * nbk * n_t, st);
+            MF_CUDA(launch_reduce_peaks(sd, w.units, n_t, w.partials, nbk, s, n_seg, peaks, st));
+            prof_end(b, pi, st);
+            count_launches(1);
+        }
     }
     int pf = prof_begin(b, MF_STAGE_FINAL, 0.0, st);
     MF_CUDA(launch_sort_triggers(w.counter, std::max<int64_t>(trig_cap, 0), key_bits, w.staged, w.keys,

@@ -245,7 +245,13 @@ int pass2_rows_partials(int log2N, int log2N2);        // partials per unit: one
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,
-                              int fft_mode, int stall_unit, cudaStream_t st);
+                              int fft_mode, int stall_unit, bool peaks_later, cudaStream_t st);
+// peaks_later: 1024-point FP32 rows keep only each row's maximum, and the
+// batch's peaks come from launch_peaks_rows (before the exchange is reused)
+bool pass2_rows_peaks_later(int log2N1, int fft_mode);
+cudaError_t launch_peaks_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int n_all,
+                              const float2 *exch, const float4 *partials, int seg_idx, int n_seg, mf_peak *peaks,
+                              cudaStream_t st);
 cudaError_t launch_reduce_peaks(const SegDev &seg, const UnitInfo *units, int n_units, const float4 *partials,
                                 int nblk, int seg_idx, int n_seg, mf_peak *peaks, cudaStream_t st);
 cudaError_t launch_sort_triggers(const unsigned long long *counter, int64_t cap, int key_bits,

@@ -29,7 +29,9 @@ namespace mf {
 
 // 1024-point rows, one warp per row: stage 0, then the last stage with the
 // next row's copy started from the sink once the region has been read.
-template <int L>
+// FULL = false: each row's partial holds only its largest |raw|^2 (k_peaks_rows
+// then finds the peak's sample and z).
+template <int L, bool FULL>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
     using S = FftShape<L>;
     static_assert(L == 1024 && S::NST == 2 && S::T == 32, "1024-point rows (one warp each)");
@@ -78,11 +80,103 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows(RowsParams p) {
         __syncwarp();
         // 3./4. the last stage, next-row copy, epilogue
         const int64_t rn = r + step;
-        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp],
-                               rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr);
-        stockham_stage<L, S::R1, 32, +1, true, GroupRhoSink<L, G>, GroupSync<G>>(region, tw, 0, t, snk);
+        GroupRhoSink<L, G, FULL> snk(p, u, j2, region, &bars[grp],
+                                     rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr);
+        stockham_stage<L, S::R1, 32, +1, true, GroupRhoSink<L, G, FULL>, GroupSync<G>>(region, tw, 0, t, snk);
         if (MF_DBG(slot < p.n_units && j2 < (1 << p.log2N2), kDbgRows))
             snk.finish(&p.partials[((int64_t)unit << p.log2N2) + j2]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Peaks of a batch after k_pass2_rows<1024, false>: one warp per unit.  M = the
+// largest of the unit's row maxima; every row whose maximum equals M (one,
+// unless rows tie) is transformed again from the exchange, with the very
+// arithmetic of k_pass2_rows (stage 0, the padded write, the last stage with
+// the same table), and the lowest sample j with |raw|^2 == M gives the peak's
+// j and z -- the record the per-row argmax would have produced.
+// ---------------------------------------------------------------------------
+struct CaptureSink {
+    float2 v[32];
+    template <int R>
+    __device__ __forceinline__ void store(int, int, int, const float2 *x) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[r];
+    }
+};
+
+__global__ void __launch_bounds__(kWarps * 32) k_peaks_rows(const float2 *__restrict__ exch,
+                                                            const UnitInfo *__restrict__ units, int unit0,
+                                                            int n_units, int n_all, int log2N, int log2N2,
+                                                            const float4 *__restrict__ partials, int seg_idx,
+                                                            int n_seg, mf_peak *__restrict__ peaks) {
+    constexpr int L = 1024;
+    using S = FftShape<L>;
+    extern __shared__ __align__(16) float2 rows_smem[];
+    float2 *tw = rows_smem + kWarps * S::STRIDE;
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+    float2 *region = rows_smem + w * S::STRIDE;
+    fill_twiddles<L>(tw);
+    __syncthreads();
+    const int b = blockIdx.x * kWarps + w;   // unit within the batch
+    if (b >= n_units) return;
+    const int unit = unit0 + b;
+    const int n2 = 1 << log2N2;
+    const float4 *pp = partials + ((int64_t)unit << log2N2);
+    float M = -1.f;
+    for (int j2 = t; j2 < n2; j2 += 32) M = fmaxf(M, pp[j2].x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+    int bj = 0x7fffffff;
+    float2 bz = make_float2(0.f, 0.f);
+    for (int r0 = 0; r0 < n2; r0 += 32) {
+        unsigned cand = __ballot_sync(0xffffffffu, pp[r0 + t].x == M);
+        while (cand != 0u) {
+            const int j2 = r0 + __ffs(cand) - 1;
+            cand &= cand - 1u;
+            if (!MF_DBG(b < n_units && (int64_t)(j2 + 1) * L <= ((int64_t)1 << log2N), kDbgRows)) continue;
+            const float2 *row = exch + ((int64_t)b << log2N) + (int64_t)j2 * L;
+            float2 v[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = row[t + 32 * q];
+            Dft<32, +1>::run(v);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
+            __syncwarp();
+            CaptureSink cs;
+            stockham_stage<L, S::R1, 32, +1, true, CaptureSink, GroupSync<1>>(region, tw, 0, t, cs);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {   // outputs t + 32 r of the row (j increases with r)
+                const float pw = fmaf(cs.v[r].x, cs.v[r].x, cs.v[r].y * cs.v[r].y);
+                const int j = j2 + ((t + 32 * r) << log2N2);
+                if (pw == M && j < bj) {
+                    bj = j;
+                    bz = cs.v[r];
+                }
+            }
+            __syncwarp();   // the region is read before the next candidate row overwrites it
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        const float ox = __shfl_xor_sync(0xffffffffu, bz.x, o);
+        const float oy = __shfl_xor_sync(0xffffffffu, bz.y, o);
+        if (oj < bj) {
+            bj = oj;
+            bz = make_float2(ox, oy);
+        }
+    }
+    if (t == 0) {
+        const UnitInfo u = units[unit];
+        mf_peak pk;
+        pk.rho = sqrtf(M) * u.rho_scale;
+        pk.j = bj;
+        pk.z_re = bz.x * u.z_scale;
+        pk.z_im = bz.y * u.z_scale;
+        if (MF_DBG(u.tmpl >= 0 && u.tmpl < n_all && seg_idx < n_seg, kDbgOut))
+            peaks[(int64_t)u.tmpl * n_seg + seg_idx] = pk;
     }
 }
 
@@ -487,8 +581,9 @@ int pass2_rows_partials(int log2N, int log2N2) {   // partials per unit: one per
 cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, const float2 *exch,
                               float4 *partials, int seg_idx, KeyLayout kl, mf_trigger *staged, uint64_t *keys,
                               unsigned long long *counter, int64_t cap, int *status, long long spin_limit, int n_sm,
-                              int fft_mode, int stall_unit, cudaStream_t st) {
+                              int fft_mode, int stall_unit, bool peaks_later, cudaStream_t st) {
     if (!pass2_rows_applies(seg.log2N1)) return cudaErrorInvalidValue;
+    if (peaks_later && !pass2_rows_peaks_later(seg.log2N1, fft_mode)) return cudaErrorInvalidValue;
     if (fft_mode != MF_FFT_FP32 && seg.log2N1 != 10) return cudaErrorInvalidValue;
     RowsParams p;
     p.exch = exch;
@@ -515,8 +610,10 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
             k_pass2_rows_tc<MF_FFT_TC_FP16><<<gr, kWarps * 32, rows_smem_tc(), st>>>(p);
         else if (fft_mode == MF_FFT_TC_BF16)
             k_pass2_rows_tc<MF_FFT_TC_BF16><<<gr, kWarps * 32, rows_smem_tc(), st>>>(p);
+        else if (peaks_later)
+            k_pass2_rows<1024, false><<<gr, kWarps * 32, rows_smem<1024>(), st>>>(p);
         else
-            k_pass2_rows<1024><<<gr, kWarps * 32, rows_smem<1024>(), st>>>(p);
+            k_pass2_rows<1024, true><<<gr, kWarps * 32, rows_smem<1024>(), st>>>(p);
     } else if (seg.log2N1 == 11) {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 2 - 1) / (kWarps / 2));
         const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
@@ -529,13 +626,30 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
     return cudaGetLastError();
 }
 
+bool pass2_rows_peaks_later(int log2N1, int fft_mode) { return log2N1 == 10 && fft_mode == MF_FFT_FP32; }
+
+cudaError_t launch_peaks_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int n_all,
+                              const float2 *exch, const float4 *partials, int seg_idx, int n_seg, mf_peak *peaks,
+                              cudaStream_t st) {
+    if (seg.log2N1 != 10 || n_units <= 0) return n_units <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)((n_units + kWarps - 1) / kWarps);
+    k_peaks_rows<<<grid, kWarps * 32, rows_smem<1024>(), st>>>(exch, units, unit0, n_units, n_all, seg.log2N,
+                                                               seg.log2N2, partials, seg_idx, n_seg, peaks);
+    return cudaGetLastError();
+}
+
 cudaError_t rows_kernel_attributes() {
     {
         cudaError_t e0 = init_twiddle_tables();
         if (e0 != cudaSuccess) return e0;
     }
-    cudaError_t e = cudaFuncSetAttribute(k_pass2_rows<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_pass2_rows<1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rows_smem<1024>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pass2_rows<1024, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rows_smem<1024>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_peaks_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem<1024>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_pass2_rows_tc<MF_FFT_TC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rows_smem_tc());

@@ -39,8 +39,12 @@ struct RowsParams {
     int stall_unit;             // test hook: rows of this unit never arrive (bounded-wait tests), -1 = none
 };
 
-// epilogue of one row: per-butterfly argmax (lowest j on ties), triggers
-template <int L, int G>
+// epilogue of one row: per-butterfly argmax (lowest j on ties), triggers.
+// FULL = false keeps only the row's largest |raw|^2 (the sample and z of the
+// peak are found afterwards by k_peaks_rows, which recomputes the winning
+// rows): the per-thread index and z search is the costliest part of the
+// epilogue, and it would run on every row for one peak per template.
+template <int L, int G, bool FULL = true>
 struct GroupRhoSink {
     const RowsParams &p;
     const UnitInfo &u;
@@ -69,7 +73,9 @@ struct GroupRhoSink {
 #pragma unroll
         for (int r = 0; r < R; ++r) pw[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
         const float m = tree_max0<R>(pw);
-        if (m >= bp) {
+        if constexpr (!FULL) {
+            bp = fmaxf(bp, m);
+        } else if (m >= bp) {
             int rs = R - 1;
 #pragma unroll
             for (int r = R - 2; r >= 0; --r) rs = (pw[r] == m) ? r : rs;
@@ -114,6 +120,12 @@ struct GroupRhoSink {
         }
     }
     __device__ __forceinline__ void finish(float4 *out) {
+        if constexpr (!FULL) {   // the row's largest |raw|^2 only (j = -1: found later)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bp = fmaxf(bp, __shfl_xor_sync(0xffffffffu, bp, o));
+            if ((threadIdx.x & 31) == 0) *out = make_float4(bp, __int_as_float(-1), 0.f, 0.f);
+            return;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float op = __shfl_xor_sync(0xffffffffu, bp, o);
