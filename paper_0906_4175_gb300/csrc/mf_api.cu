@@ -863,8 +863,9 @@ extern "C" int mf_filter_bank(mf_bank b, const mf_segment *segs, int n_seg, floa
         const int nbk = rows ? pass2_rows_partials(sd.log2N, sd.log2N2) : pass2_blocks(sd.log2N, sd.log2N2);
         // per-batch 1024-point FP32 rows: each row keeps only its maximum and
         // the batch's peaks are found right after its pass 2 (launch_peaks_rows)
+        // (not for batches of one template, where the extra launch costs more than the search)
         const bool peaks_later = rows && !use_persistent(b, segs[s]) && !use_fused(b, segs[s]) &&
-                                 pass2_rows_peaks_later(sd.log2N1, b->params.fft_mode);
+                                 seg_batch[(size_t)s] > 1 && pass2_rows_peaks_later(sd.log2N1, b->params.fft_mode);
         const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
         // algorithmic bytes per template (profiling only): band of W and anchors read in pass 1
         std::vector<double> band_bytes, anc_bytes;

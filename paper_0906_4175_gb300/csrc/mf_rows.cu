@@ -206,7 +206,61 @@ __host__ __device__ constexpr size_t rows_group_smem() {
            (kWarps / G) * sizeof(uint64_t);
 }
 
+// The transform of one landed row by its group (all G warps): stage 0 from
+// the unpadded row in the region, stages 1 and the radix-G last stage through
+// the region, outputs o[q][i] = X[b + 1024 q], b = k + 32 (RW h + i).  gfail:
+// the group's wait flag, checked once every warp has read the row (the group
+// then leaves: returns false); the region is free when it returns.
 template <int G>
+__device__ __forceinline__ bool group_row(float2 *region, const float2 *tw1, const float2 *tw2, int h, int lane,
+                                          const volatile int *gfail, float2 (&o)[G][32 / G]) {
+    constexpr int L = 1024 * G, T = 32 * G, RW = 32 / G;
+    const int t = 32 * h + lane;
+    float2 *xb = region;   // the exchange, once stage 1 has read the region
+    // stage 0 (radix 32, Ns = 1): butterfly t reads x[t + T q]
+    // (after a wait that ran out the region is stale; the group leaves together at the barrier below)
+    float2 v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = region[t + T * q];
+    Dft<32, +1>::run(v);
+    GroupSync<G>::sync();   // every read of the landed row is done; gfail is final
+    if (gfail != nullptr && *gfail != 0) return false;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
+    GroupSync<G>::sync();
+    // stage 1 (radix 32, Ns = 32): butterfly t = 32 h + k reads y[t + T r]
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = region[spad(t + T * q)];
+    GroupSync<G>::sync();   // the exchange below overwrites the region
+#pragma unroll
+    for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw1[q * 32 + lane]);
+    Dft<32, +1>::run(v);
+    // exchange: slot ((src G + dst) RW + i) 32 + k holds z_src[k + 32 (RW dst + i)]
+#pragma unroll
+    for (int d = 0; d < G; ++d) {
+        if (d == h) continue;
+#pragma unroll
+        for (int i = 0; i < RW; ++i) xb[((h * G + d) * RW + i) * 32 + lane] = v[RW * d + i];
+    }
+    GroupSync<G>::sync();
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+        const int b = lane + 32 * (RW * h + i);
+        float2 x[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) x[q] = q == h ? v[RW * h + i] : xb[((q * G + h) * RW + i) * 32 + lane];
+#pragma unroll
+        for (int q = 1; q < G; ++q) x[q] = cmul(x[q], tw2[(q - 1) * 1024 + b]);
+        Dft<G, +1>::run(x);
+#pragma unroll
+        for (int q = 0; q < G; ++q) o[q][i] = x[q];
+    }
+    GroupSync<G>::sync();   // every read of the region is done
+    static_assert(L == 1024 * G, "row length");
+    return true;
+}
+
+template <int G, bool FULL>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_group(RowsParams p) {
     constexpr int L = 1024 * G, NG = kWarps / G, T = 32 * G, RW = 32 / G;
     using S = FftShape<L>;
@@ -217,7 +271,6 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_group(RowsParams 
     const int grp = (threadIdx.x >> 5) / G, t = threadIdx.x & (T - 1), lane = threadIdx.x & 31;
     const int h = (threadIdx.x >> 5) % G;                     // warp within the group
     float2 *region = rows_smem + grp * S::STRIDE;
-    float2 *xb = region;                                        // the exchange, once stage 1 has read the region
     float2 *tw1 = rows_smem + NG * S::STRIDE;                   // stage 1: [r 32 + k] = exp(2 pi i r k / 1024)
     float2 *tw2 = tw1 + 1024;                                   // last stage: [(p - 1) 1024 + b] = w^(p b)
     uint64_t *bars = reinterpret_cast<uint64_t *>(tw2 + 1024 * (G - 1));
@@ -255,60 +308,122 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_pass2_rows_group(RowsParams 
         const UnitInfo u = p.units[unit];
         const int64_t rn = r + step;
         const float2 *next = rn < total && !row_withheld(p, rn) ? row_src<L>(p, rn) : nullptr;
-        // stage 0 (radix 32, Ns = 1): butterfly t reads x[t + T q]
-        // (after a wait that ran out the region is stale; the group leaves together at the barrier below)
-        float2 v[32];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = region[t + T * q];
-        Dft<32, +1>::run(v);
-        GroupSync<G>::sync();   // every read of the landed row is done; gfail is final
-        if (*(volatile int *)&gfail[grp] != 0) {
+        float2 o[G][RW];
+        if (!group_row<G>(region, tw1, tw2, h, lane, &gfail[grp], o)) {
             if (lane == 0) atomicOr(p.status, 2);
             return;   // the copy into this group's region never completed; nothing else is in flight
         }
-#pragma unroll
-        for (int q = 0; q < 32; ++q) region[spad(32 * t + q)] = v[q];
-        GroupSync<G>::sync();
-        // stage 1 (radix 32, Ns = 32): butterfly t = 32 h + k reads y[t + T r]
-#pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = region[spad(t + T * q)];
-        GroupSync<G>::sync();   // the exchange below overwrites the region
-#pragma unroll
-        for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw1[q * 32 + lane]);
-        Dft<32, +1>::run(v);
-        // exchange: slot ((src G + dst) RW + i) 32 + k holds z_src[k + 32 (RW dst + i)]
-#pragma unroll
-        for (int d = 0; d < G; ++d) {
-            if (d == h) continue;
-#pragma unroll
-            for (int i = 0; i < RW; ++i) xb[((h * G + d) * RW + i) * 32 + lane] = v[RW * d + i];
-        }
-        GroupSync<G>::sync();
-        float2 o[G][RW];
-#pragma unroll
-        for (int i = 0; i < RW; ++i) {
-            const int b = lane + 32 * (RW * h + i);
-            float2 x[G];
-#pragma unroll
-            for (int q = 0; q < G; ++q) x[q] = q == h ? v[RW * h + i] : xb[((q * G + h) * RW + i) * 32 + lane];
-#pragma unroll
-            for (int q = 1; q < G; ++q) x[q] = cmul(x[q], tw2[(q - 1) * 1024 + b]);
-            Dft<G, +1>::run(x);
-#pragma unroll
-            for (int q = 0; q < G; ++q) o[q][i] = x[q];
-        }
-        GroupSync<G>::sync();   // every read of the region is done: start the next row's copy
+        // every read of the region is done: start the next row's copy
         fence_proxy_async();
         if (next != nullptr && t == 0) {
             mbar_expect_tx(&bars[grp], L * sizeof(float2));
             bulk_copy_g2s(region, next, L * sizeof(float2), &bars[grp]);
         }
         // epilogue: outputs b + 1024 q, b = k + 32 (RW h + i)
-        GroupRhoSink<L, G> snk(p, u, j2, region, &bars[grp], nullptr);
+        GroupRhoSink<L, G, FULL> snk(p, u, j2, region, &bars[grp], nullptr);
 #pragma unroll
         for (int q = 0; q < G; ++q) snk.template store<RW>(0, lane + 32 * RW * h + 1024 * q, 32, o[q]);
         if (MF_DBG(slot < p.n_units && j2 < (1 << p.log2N2), kDbgRows))
             snk.finish(&p.partials[(((int64_t)unit << p.log2N2) + j2) * G + h]);
+    }
+}
+
+// Peaks of a batch after k_pass2_rows_group<G, false>: one group of G warps
+// per unit, as k_peaks_rows does for 1024-point rows -- M = the largest of the
+// unit's row maxima (G partials per row), and every row that reaches it is
+// loaded into the group's region and transformed again by group_row, the
+// code of the row kernel, for the lowest sample with |raw|^2 == M.
+template <int G>
+__global__ void __launch_bounds__(kWarps * 32) k_peaks_rows_group(const float2 *__restrict__ exch,
+                                                                  const UnitInfo *__restrict__ units, int unit0,
+                                                                  int n_units, int n_all, int log2N, int log2N2,
+                                                                  const float4 *__restrict__ partials, int seg_idx,
+                                                                  int n_seg, mf_peak *__restrict__ peaks) {
+    constexpr int L = 1024 * G, NG = kWarps / G, T = 32 * G, RW = 32 / G;
+    using S = FftShape<L>;
+    extern __shared__ __align__(16) float2 rows_smem[];
+    __shared__ int s_j[kWarps];
+    __shared__ float2 s_z[kWarps];
+    const int grp = (threadIdx.x >> 5) / G, t = threadIdx.x & (T - 1), lane = threadIdx.x & 31;
+    const int h = (threadIdx.x >> 5) % G;
+    float2 *region = rows_smem + grp * S::STRIDE;
+    float2 *tw1 = rows_smem + NG * S::STRIDE;
+    float2 *tw2 = tw1 + 1024;
+    {
+        const float2 *src = g_tw_tables + tw_offset<L>();
+        for (int m = threadIdx.x; m < 1024 * G; m += blockDim.x)
+            tw1[m] = __ldg(&src[m < 1024 ? m : TwTable<L>::S1 + m]);
+    }
+    __syncthreads();
+    const int b = blockIdx.x * NG + grp;   // unit within the batch (the group's warps agree)
+    if (b >= n_units) return;              // whole groups leave: no group barrier is left waiting
+    const int unit = unit0 + b;
+    const int n2 = 1 << log2N2;
+    const float4 *pp = partials + ((int64_t)unit << log2N2) * G;
+    // every warp of the group computes M and the candidate rows itself (same values)
+    float M = -1.f;
+    for (int e = lane; e < n2 * G; e += 32) M = fmaxf(M, pp[e].x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+    int bj = 0x7fffffff;
+    float2 bz = make_float2(0.f, 0.f);
+    for (int r0 = 0; r0 < n2; r0 += 32) {
+        float rm = -1.f;
+#pragma unroll
+        for (int q = 0; q < G; ++q) rm = fmaxf(rm, pp[(int64_t)(r0 + lane) * G + q].x);
+        unsigned cand = __ballot_sync(0xffffffffu, rm == M);
+        while (cand != 0u) {
+            const int j2 = r0 + __ffs(cand) - 1;
+            cand &= cand - 1u;
+            const bool in_range = MF_DBG(b < n_units && (int64_t)(j2 + 1) * L <= ((int64_t)1 << log2N), kDbgRows);
+            const float2 *row = exch + ((int64_t)b << log2N) + (in_range ? (int64_t)j2 * L : 0);
+            for (int e = t; e < L; e += T) region[e] = row[e];   // the row as its bulk copy lands it
+            GroupSync<G>::sync();
+            float2 o[G][RW];
+            group_row<G>(region, tw1, tw2, h, lane, nullptr, o);
+#pragma unroll
+            for (int q = 0; q < G; ++q)
+#pragma unroll
+                for (int i = 0; i < RW; ++i) {   // output b + 1024 q, b = k + 32 (RW h + i)
+                    const float pw = fmaf(o[q][i].x, o[q][i].x, o[q][i].y * o[q][i].y);
+                    const int j = j2 + ((lane + 32 * (RW * h + i) + 1024 * q) << log2N2);
+                    if (in_range && pw == M && j < bj) {
+                        bj = j;
+                        bz = o[q][i];
+                    }
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        const float ox = __shfl_xor_sync(0xffffffffu, bz.x, o);
+        const float oy = __shfl_xor_sync(0xffffffffu, bz.y, o);
+        if (oj < bj) {
+            bj = oj;
+            bz = make_float2(ox, oy);
+        }
+    }
+    const int wi = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_j[wi] = bj;
+        s_z[wi] = bz;
+    }
+    GroupSync<G>::sync();
+    if (h == 0 && lane == 0) {
+        for (int q = 1; q < G; ++q)
+            if (s_j[wi + q] < bj) {
+                bj = s_j[wi + q];
+                bz = s_z[wi + q];
+            }
+        const UnitInfo u = units[unit];
+        mf_peak pk;
+        pk.rho = sqrtf(M) * u.rho_scale;
+        pk.j = bj;
+        pk.z_re = bz.x * u.z_scale;
+        pk.z_im = bz.y * u.z_scale;
+        if (MF_DBG(u.tmpl >= 0 && u.tmpl < n_all && seg_idx < n_seg, kDbgOut))
+            peaks[(int64_t)u.tmpl * n_seg + seg_idx] = pk;
     }
 }
 
@@ -617,24 +732,40 @@ cudaError_t launch_pass2_rows(const SegDev &seg, const UnitInfo *units, int unit
     } else if (seg.log2N1 == 11) {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 2 - 1) / (kWarps / 2));
         const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
-        k_pass2_rows_group<2><<<gr, kWarps * 32, rows_group_smem<2>(), st>>>(p);
+        if (peaks_later) k_pass2_rows_group<2, false><<<gr, kWarps * 32, rows_group_smem<2>(), st>>>(p);
+        else k_pass2_rows_group<2, true><<<gr, kWarps * 32, rows_group_smem<2>(), st>>>(p);
     } else {
         int64_t grid = std::min<int64_t>(2 * (int64_t)n_sm, (rows + kWarps / 4 - 1) / (kWarps / 4));
         const unsigned gr = (unsigned)std::max<int64_t>(grid, 1);
-        k_pass2_rows_group<4><<<gr, kWarps * 32, rows_group_smem<4>(), st>>>(p);
+        if (peaks_later) k_pass2_rows_group<4, false><<<gr, kWarps * 32, rows_group_smem<4>(), st>>>(p);
+        else k_pass2_rows_group<4, true><<<gr, kWarps * 32, rows_group_smem<4>(), st>>>(p);
     }
     return cudaGetLastError();
 }
 
-bool pass2_rows_peaks_later(int log2N1, int fft_mode) { return log2N1 == 10 && fft_mode == MF_FFT_FP32; }
+bool pass2_rows_peaks_later(int log2N1, int fft_mode) {
+    return log2N1 >= 10 && log2N1 <= 12 && fft_mode == MF_FFT_FP32;
+}
 
 cudaError_t launch_peaks_rows(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int n_all,
                               const float2 *exch, const float4 *partials, int seg_idx, int n_seg, mf_peak *peaks,
                               cudaStream_t st) {
-    if (seg.log2N1 != 10 || n_units <= 0) return n_units <= 0 ? cudaSuccess : cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)((n_units + kWarps - 1) / kWarps);
-    k_peaks_rows<<<grid, kWarps * 32, rows_smem<1024>(), st>>>(exch, units, unit0, n_units, n_all, seg.log2N,
-                                                               seg.log2N2, partials, seg_idx, n_seg, peaks);
+    if (n_units <= 0) return cudaSuccess;
+    if (seg.log2N1 == 10) {
+        const unsigned grid = (unsigned)((n_units + kWarps - 1) / kWarps);
+        k_peaks_rows<<<grid, kWarps * 32, rows_smem<1024>(), st>>>(exch, units, unit0, n_units, n_all, seg.log2N,
+                                                                   seg.log2N2, partials, seg_idx, n_seg, peaks);
+    } else if (seg.log2N1 == 11) {
+        const unsigned grid = (unsigned)((n_units + kWarps / 2 - 1) / (kWarps / 2));
+        k_peaks_rows_group<2><<<grid, kWarps * 32, rows_group_smem<2>(), st>>>(
+            exch, units, unit0, n_units, n_all, seg.log2N, seg.log2N2, partials, seg_idx, n_seg, peaks);
+    } else if (seg.log2N1 == 12) {
+        const unsigned grid = (unsigned)((n_units + kWarps / 4 - 1) / (kWarps / 4));
+        k_peaks_rows_group<4><<<grid, kWarps * 32, rows_group_smem<4>(), st>>>(
+            exch, units, unit0, n_units, n_all, seg.log2N, seg.log2N2, partials, seg_idx, n_seg, peaks);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -657,11 +788,24 @@ cudaError_t rows_kernel_attributes() {
     e = cudaFuncSetAttribute(k_pass2_rows_tc<MF_FFT_TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rows_smem_tc());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pass2_rows_group<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_pass2_rows_group<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rows_group_smem<2>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pass2_rows_group<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rows_group_smem<4>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pass2_rows_group<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rows_group_smem<2>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pass2_rows_group<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rows_group_smem<4>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pass2_rows_group<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rows_group_smem<4>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_peaks_rows_group<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rows_group_smem<2>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_peaks_rows_group<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rows_group_smem<4>());
+    return e;
 }
 
 }  // namespace mf
