@@ -207,7 +207,9 @@ int mf_segment_info(mf_segment seg, int64_t *N, double *fs);
  * cuda_stream and returns; mf_bank_check() reports overflow and device-side
  * timeouts of the last call on this bank.
  * The first call for a given (segment length, bank size, trig_cap) allocates
- * the bank's workspace; later calls allocate nothing and queue only kernels
+ * the bank's workspace (mostly the exchange of the templates in flight:
+ * min(bank size, 4 GiB / 8N) x 8N bytes by default, the autotuned budget after
+ * mf_autotune); later calls allocate nothing and queue only kernels
  * and memsets, so a call may be captured in a CUDA graph once an identical
  * call has run outside the capture (the graph keeps the segment, output and
  * workspace pointers; replays recompute from the segments' current contents).
