@@ -186,7 +186,7 @@ int pass2_blocks(int log2N, int log2N2) {
 
 cudaError_t filter_kernel_attributes() {
     {
-        cudaError_t e0 = init_twiddle_tables();
+        cudaError_t e0 = init_pass_tables();
         if (e0 != cudaSuccess) return e0;
     }
     for (int lg = 10; lg <= 22; ++lg) {

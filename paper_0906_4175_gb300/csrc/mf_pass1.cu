@@ -246,7 +246,7 @@ cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0,
 }
 
 cudaError_t pass1_pf_kernel_attributes() {
-    cudaError_t e = init_twiddle_tables();   // this translation unit's copy of the Stockham tables
+    cudaError_t e = init_pass_tables();   // this translation unit's copies of the Stockham tables and four-step roots
     if (e != cudaSuccess) return e;
     int dev = 0;
     e = cudaGetDevice(&dev);

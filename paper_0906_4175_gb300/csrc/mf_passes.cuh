@@ -146,6 +146,54 @@ struct ColRealSrc {         // real samples s[n] (imaginary part zero)
     }
 };
 
+// Roots exp(+2 pi i m / 2^p), p = 10 .. 22, for the four-step twiddles of the
+// exchange sinks, whose exponents stay below N / 32: per p a low table
+// lo[j] = e^{2 pi i j / 2^p}, j < 1024, then a high table
+// hi[i] = e^{2 pi i 1024 i / 2^p}, i < max(1, 2^(p - 15)); a root is
+// hi[m >> 10] lo[m & 1023].  Entries are FP64 sincospi of exact arguments
+// rounded to FP32 (once per device, per translation unit like the Stockham
+// tables, by init_pass_tables).
+__host__ __device__ constexpr int fs_hi_count(int p) { return p > 15 ? 1 << (p - 15) : 1; }
+// start of the tables of p: the lengths 1024 + fs_hi_count(q) summed over q = 10 .. p - 1
+__host__ __device__ constexpr int fs_offset(int p) {
+    return 1024 * (p - 10) + (p - 10 < 6 ? p - 10 : 6) + (p >= 17 ? (1 << (p - 15)) - 2 : 0);
+}
+constexpr int kFsTotal = fs_offset(23);
+static_assert(fs_offset(11) == 1025 && fs_offset(17) == fs_offset(16) + 1026 && fs_offset(18) == fs_offset(17) + 1028 &&
+                  fs_offset(23) == fs_offset(22) + 1024 + 128,
+              "root table layout");
+static __device__ float2 g_fs_roots[kFsTotal];
+
+static __global__ void k_init_fs_roots() {
+    for (int p = 10; p <= 22; ++p) {
+        float2 *tab = g_fs_roots + fs_offset(p);   // lo then hi
+        const double P = (double)(1 << p);
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 1024 + fs_hi_count(p); j += gridDim.x * blockDim.x) {
+            const double m = j < 1024 ? (double)j : 1024.0 * (double)(j - 1024);
+            double sn, cs;
+            sincospi(2.0 * m / P, &sn, &cs);
+            tab[j] = make_float2((float)cs, (float)sn);
+        }
+    }
+}
+
+// exp(SIGN 2 pi i m / 2^p) for 0 <= m < 2^(p - 5), from lo = g_fs_roots + fs_offset(p)
+template <int SIGN>
+__device__ __forceinline__ float2 fs_root(const float2 *lo, uint32_t m) {
+    const float2 a = __ldg(&lo[1024 + (m >> 10)]), b = __ldg(&lo[m & 1023u]);
+    const float2 r = make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+    return make_float2(r.x, SIGN > 0 ? r.y : -r.y);
+}
+
+// The Stockham tables and the four-step roots of this translation unit (every
+// unit that launches kernels with an ExchSink calls this once per device).
+static inline cudaError_t init_pass_tables() {
+    k_init_fs_roots<<<8, 256>>>();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return init_twiddle_tables();
+}
+
 // Column sink: multiply by the four-step twiddle exp(SIGN 2 pi i j2 k1 / N)
 // and write E[j2 * N1 + k1] (batch blockIdx.y at E + blockIdx.y * N).
 template <int L, int C, int SIGN, int LG1>
@@ -158,9 +206,13 @@ struct ExchSink {
     __device__ __forceinline__ void store(int seq, int b, int stride, const float2 *v) const {
         const int k1 = tile * C + seq;
         float2 *E = p.E + ((int64_t)slot << p.log2N) + ((int64_t)b << LG1) + k1;   // row j2 = b
-        if (!MF_DBG(k1 < (1 << LG1) && b + (R - 1) * stride < (1 << (p.log2N - LG1)), kDbgExch)) return;
-        float2 w = unit_root<SIGN>((uint32_t)(b * k1), p.log2N);
-        const float2 step = unit_root<SIGN>((uint32_t)(stride * k1), p.log2N);
+        if (!MF_DBG(k1 < (1 << LG1) && b + (R - 1) * stride < (1 << (p.log2N - LG1)) && p.log2N >= 10 &&
+                        p.log2N <= 22 && (int64_t)max(b, stride) * k1 < ((int64_t)1 << (p.log2N - 5)),
+                    kDbgExch))
+            return;
+        const float2 *roots = g_fs_roots + fs_offset(p.log2N);   // b k1, stride k1 < N / 32
+        float2 w = fs_root<SIGN>(roots, (uint32_t)(b * k1));
+        const float2 step = fs_root<SIGN>(roots, (uint32_t)(stride * k1));
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             __stcg(&E[((int64_t)r * stride) << LG1], cmul(v[r], w));   // row j2 = b + r stride

@@ -369,7 +369,7 @@ MF_DEBUG_READER(dbg_read_persist)
 
 cudaError_t persist_kernel_attributes() {
     {
-        cudaError_t e0 = init_twiddle_tables();
+        cudaError_t e0 = init_pass_tables();
         if (e0 != cudaSuccess) return e0;
     }
     for (int lg = 13; lg <= 22; ++lg) {

@@ -175,7 +175,7 @@ cudaError_t launch_fft_c2c(const float2 *x, float2 *y, int64_t N, int batch, int
 
 cudaError_t prep_kernel_attributes() {
     {
-        cudaError_t e0 = init_twiddle_tables();
+        cudaError_t e0 = init_pass_tables();
         if (e0 != cudaSuccess) return e0;
     }
     for (int lg = 10; lg <= 22; ++lg) {

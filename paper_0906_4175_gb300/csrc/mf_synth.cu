@@ -113,7 +113,7 @@ cudaError_t launch_inverse_real_fft(const float2 *Y, int64_t N, double scale, fl
 
 cudaError_t synth_kernel_attributes() {
     {
-        cudaError_t e0 = init_twiddle_tables();
+        cudaError_t e0 = init_pass_tables();
         if (e0 != cudaSuccess) return e0;
     }
     for (int lg = 10; lg <= 22; ++lg) {
