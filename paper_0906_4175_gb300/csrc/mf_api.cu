@@ -1123,14 +1123,21 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     const bool anchors = b->params.phase_mode != MF_PHASE_FP32;
     if (rows && !b->chi_status) MF_CUDA(dev_malloc(&b->chi_status, sizeof(int)));
     if (b->chi_status) MF_CUDA(cudaMemsetAsync(b->chi_status, 0, sizeof(int), st));
-    UnitInfo *all = nullptr, *units = nullptr;
+    // With the persistent pass 1, one launch per batch covers all p + 1 bands:
+    // unit slot l nb + s is band l of template u0 + s (a band-major copy of the
+    // batch's units), reading the copy of its template's anchors that the
+    // anchor launch stores for each band.
+    const bool merged = rows && p1_form(b) != 1 && pass1_pf_applies(sd.log2N, sd.log2N2, lgD, b->params.phase_mode);
+    UnitInfo *all = nullptr, *units = nullptr, *mu = nullptr;
     float4 *anc = nullptr;
     float *anc4 = nullptr;
     float2 *exch = nullptr;
     cudaError_t e = dev_malloc_async(&all, sizeof(UnitInfo) * n_t, st);
     if (e == cudaSuccess) e = dev_malloc_async(&units, sizeof(UnitInfo) * (size_t)(p + 1) * n, st);
-    if (e == cudaSuccess) e = dev_malloc_async(&anc, sizeof(float4) * man * batch, st);
-    if (e == cudaSuccess) e = dev_malloc_async(&anc4, sizeof(float) * man * batch, st);
+    if (e == cudaSuccess && merged) e = dev_malloc_async(&mu, sizeof(UnitInfo) * (size_t)(p + 1) * batch, st);
+    const int64_t anc_slots = batch * (merged ? p + 1 : 1);
+    if (e == cudaSuccess) e = dev_malloc_async(&anc, sizeof(float4) * man * anc_slots, st);
+    if (e == cudaSuccess) e = dev_malloc_async(&anc4, sizeof(float) * man * anc_slots, st);
     if (e == cudaSuccess) e = dev_malloc_async(&exch, sizeof(float2) * seg->N * batch * (rows ? p + 1 : 1), st);
     int launches = 0;
     if (e == cudaSuccess) e = launch_units(sd, b->d_tmpl, n_t, b->params.f_low, 0.f, lgD, nullptr, all, st);
@@ -1140,11 +1147,20 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     for (int64_t u0 = 0; u0 < n && e == cudaSuccess; u0 += batch) {
         const int nb = (int)std::min<int64_t>(batch, n - u0);
         if (anchors) {
-            e = launch_anchors(sd, b->d_tmpl, full, (int)u0, nb, lgD, man, anc, anc4, st);
+            e = launch_anchors(sd, b->d_tmpl, full, (int)u0, nb, lgD, man, anc, anc4, st, merged ? p + 1 : 1);
             ++launches;
         }
         if (rows) {
-            for (int l = 0; l <= p && e == cudaSuccess; ++l) {
+            if (merged) {
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(mu, sizeof(UnitInfo) * nb, units + u0, sizeof(UnitInfo) * n,
+                                          sizeof(UnitInfo) * nb, p + 1, cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess)
+                    e = launch_pass1(sd, mu, 0, (p + 1) * nb, lgD, man, anc, anc4, exch, b->params.phase_mode,
+                                     b->d_tmpl, p1_form(b), b->chi_status, b->spin_limit, st);
+                ++launches;
+            }
+            for (int l = 0; !merged && l <= p && e == cudaSuccess; ++l) {
                 e = launch_pass1(sd, units + (size_t)l * n, (int)u0, nb, lgD, man, anc, anc4,
                                  exch + (size_t)l * nb * seg->N, b->params.phase_mode, b->d_tmpl, p1_form(b),
                                  b->chi_status, b->spin_limit, st);
@@ -1167,6 +1183,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
     }
     if (all) cudaFreeAsync(all, st);
     if (units) cudaFreeAsync(units, st);
+    if (mu) cudaFreeAsync(mu, st);
     if (anc) cudaFreeAsync(anc, st);
     if (anc4) cudaFreeAsync(anc4, st);
     if (exch) cudaFreeAsync(exch, st);

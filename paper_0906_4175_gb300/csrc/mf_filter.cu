@@ -52,13 +52,14 @@ __global__ void k_units(SegDev seg, const double *__restrict__ tmpl, int n_t, do
 
 __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const UnitInfo *__restrict__ units,
                           int unit0, int log2D, int max_anc, float4 *__restrict__ anchors,
-                          float *__restrict__ anchors4) {
+                          float *__restrict__ anchors4, int reps) {
     const int b = blockIdx.y;
     const UnitInfo u = units[unit0 + b];
     const double *T = tmpl + (int64_t)u.tmpl * kTmplStride;
     const double c1 = T[TF_C1], c2 = T[TF_C2], c3 = T[TF_C3], c5 = T[TF_C5];
     float4 *out = anchors + (int64_t)b * max_anc;
     float *out4 = anchors4 + (int64_t)b * max_anc;
+    const int64_t rep_stride = (int64_t)gridDim.y * max_anc;   // copy k of slot b is slot b + k n_units
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < u.n_anc; i += gridDim.x * blockDim.x) {
         float4 r;
         float r4;
@@ -66,8 +67,10 @@ __global__ void k_anchors(SegDev seg, const double *__restrict__ tmpl, const Uni
         anchor_record(c1, c2, c3, c5, g, log2D, seg.df, r, r4);
         const int64_t a = anchor_slot_index(g, seg.log2N, seg.log2N1, log2D);
         if (!MF_DBG(a >= 0 && a < max_anc, kDbgAnchor)) continue;
-        out[a] = r;
-        out4[a] = r4;
+        for (int k = 0; k < reps; ++k) {
+            out[a + k * rep_stride] = r;
+            out4[a + k * rep_stride] = r4;
+        }
     }
 }
 
@@ -83,11 +86,12 @@ cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double 
 }
 
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0, int n_units,
-                           int log2D, int max_anc, float4 *anchors, float *anchors4, cudaStream_t st) {
+                           int log2D, int max_anc, float4 *anchors, float *anchors4, cudaStream_t st, int reps) {
+    if (reps < 1) return cudaErrorInvalidValue;
     const int per = 256;
     int gx = (max_anc + per - 1) / per;
     if (gx > 64) gx = 64;
-    k_anchors<<<dim3(gx, n_units), per, 0, st>>>(seg, tmpl, units, unit0, log2D, max_anc, anchors, anchors4);
+    k_anchors<<<dim3(gx, n_units), per, 0, st>>>(seg, tmpl, units, unit0, log2D, max_anc, anchors, anchors4, reps);
     return cudaGetLastError();
 }
 

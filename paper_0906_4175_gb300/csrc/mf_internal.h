@@ -213,7 +213,9 @@ cudaError_t launch_units(const SegDev &seg, const double *tmpl, int n_t, double 
                          int log2D, const int *order, UnitInfo *units, cudaStream_t st);
 cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo *units, int unit0,
                            int n_units, int log2D, int max_anc, float4 *anchors, float *anchors4,
-                           cudaStream_t st);
+                           cudaStream_t st, int reps = 1);
+// (reps > 1: every record is also stored reps - 1 more times, n_units slots
+// apart, for launches that cover several bands of the same templates)
 // p1_form: 0 the persistent form with staged inputs (tiles of C columns),
 // 1 one CTA per column tile, 2 the persistent form with tiles of C/2 columns
 // (the persistent form only where it applies; every form gives bit-identical
