@@ -1157,7 +1157,7 @@ extern "C" int mf_chisq_series(mf_bank b, mf_segment seg, const int32_t *tmpl, i
                                           sizeof(UnitInfo) * nb, p + 1, cudaMemcpyDeviceToDevice, st);
                 if (e == cudaSuccess)
                     e = launch_pass1(sd, mu, 0, (p + 1) * nb, lgD, man, anc, anc4, exch, b->params.phase_mode,
-                                     b->d_tmpl, p1_form(b), b->chi_status, b->spin_limit, st);
+                                     b->d_tmpl, p1_form(b), b->chi_status, b->spin_limit, st, true);
                 ++launches;
             }
             for (int l = 0; !merged && l <= p && e == cudaSuccess; ++l) {

@@ -167,10 +167,11 @@ struct AttrOp {
 
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D, int max_anc,
                          const float4 *anchors, const float *anchors4, float2 *exch, int phase_mode,
-                         const double *tmpl, int p1_form, int *status, long long spin_limit, cudaStream_t st) {
+                         const double *tmpl, int p1_form, int *status, long long spin_limit, cudaStream_t st,
+                         bool narrow) {
     if (p1_form != 1 && pass1_pf_applies(seg.log2N, seg.log2N2, log2D, phase_mode))
         return launch_pass1_pf(seg, units, unit0, n_units, log2D, max_anc, anchors, anchors4, exch, p1_form == 2,
-                               status, spin_limit, st);
+                               status, spin_limit, st, narrow);
     Pass1Op op{seg, units, unit0, n_units, log2D, max_anc, phase_mode, anchors, anchors4, exch, tmpl, st};
     return dispatch_split2(seg.log2N, seg.log2N2, op);
 }

@@ -224,7 +224,11 @@ cudaError_t launch_anchors(const SegDev &seg, const double *tmpl, const UnitInfo
 cudaError_t launch_pass1(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                          int max_anc, const float4 *anchors, const float *anchors4, float2 *exch,
                          int phase_mode, const double *tmpl, int p1_form, int *status, long long spin_limit,
-                         cudaStream_t st);
+                         cudaStream_t st, bool narrow = false);
+// narrow: bands of a few rows per column (the chi^2 sub-bands); the staged form
+// then starts a column with a cheaper first stage wherever each lane of a warp
+// holds at most one row of the band (other forms ignore it; rounding differs
+// from the half-zero DFT, within the FP32 error of the transform).
 cudaError_t launch_pass2(const SegDev &seg, const UnitInfo *units, int unit0, int n_units,
                          const float2 *exch, float4 *partials, int seg_idx, KeyLayout kl,
                          mf_trigger *staged, uint64_t *keys, unsigned long long *counter, int64_t cap,
@@ -235,7 +239,7 @@ int pass2_blocks(int log2N, int log2N2);   // pass-2 tiles per unit for the spli
 bool pass1_pf_applies(int log2N, int log2N2, int log2D, int phase_mode);
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                             int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, bool half_tile,
-                            int *status, long long spin_limit, cudaStream_t st);
+                            int *status, long long spin_limit, cudaStream_t st, bool narrow = false);
 // the two tensor maps over W (2 x 128 bytes at maps_out: boxes of C and C/2
 // columns) for the persistent pass 1; false if it does not apply (N outside
 // 2^16..2^21) or they cannot be made

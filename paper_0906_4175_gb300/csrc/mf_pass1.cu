@@ -52,7 +52,7 @@ namespace {
 
 // two CTAs per SM with tiles of C = 8192/L columns (256 threads); three with
 // half-width tiles (128 threads, half the column data and W staging)
-template <int L, int C, int LG1, bool TMA>
+template <int L, int C, int LG1, bool TMA, bool NARROW = false>
 __global__ void __launch_bounds__(C *(L / 32), (C * (L / 32) >= 256) ? 2 : 3)
     k_pass1_pf(const Pass1PfParams p, const __grid_constant__ CUtensorMap wmap) {
     using S = FftShape<L>;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(C *(L / 32), (C * (L / 32) >= 256) ? 2 : 3)
             if (threadIdx.x == 0) atomicOr(p.status, 2);
             return;   // the W copy of this item never completed; no other copy is in flight
         }
-        pf_stage1<L, C, LG1>(tile, seq, t, k_lo, k_hi, p.log2D, wbuf, abuf, abuf4, sq);
+        pf_stage1<L, C, LG1, NARROW>(tile, seq, t, k_lo, k_hi, p.log2D, wbuf, abuf, abuf4, sq, tw);
         __syncthreads();   // column data complete; every thread has consumed the staged inputs
         if (next < p.n_items) pf_issue<L, C, LG1, TMA>(p, &wmap, next, nband, wbuf, abuf, abuf4, bar);
         ExchSink<L, C, +1, LG1> snk(kp, tile, p.unit0 + slot, slot);
@@ -122,21 +122,23 @@ int g_pf_sms = 0;
 template <int L>
 constexpr int pf_index() { return L == 256 ? 0 : (L == 512 ? 1 : 2); }
 
-template <int N2, int C, int LG1, bool TMA>
+template <int N2, int C, int LG1, bool TMA, bool NARROW = false>
 cudaError_t pf_attrs(int &nb) {
     constexpr int SM = (int)pf_smem_bytes<N2, C>();
-    cudaError_t e = cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pass1_pf<N2, C, LG1, TMA>, C * (N2 / 32), SM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_pass1_pf<N2, C, LG1, TMA, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pass1_pf<N2, C, LG1, TMA, NARROW>, C * (N2 / 32), SM);
     return e;
 }
 
-template <int N2, int N1, int C, bool TMA>
+template <int N2, int N1, int C, bool TMA, bool NARROW = false>
 cudaError_t pf_launch(const Pass1PfParams &p, const CUtensorMap &map, int n_units, int per_sm, cudaStream_t st) {
     constexpr int LG1 = cx_ilog2(N1);
     Pass1PfParams q = p;
     q.n_items = n_units * (N1 / C);
     const int grid = (int)std::min<int64_t>(q.n_items, (int64_t)per_sm * g_pf_sms);
-    k_pass1_pf<N2, C, LG1, TMA><<<grid, C * (N2 / 32), pf_smem_bytes<N2, C>(), st>>>(q, map);
+    k_pass1_pf<N2, C, LG1, TMA, NARROW><<<grid, C * (N2 / 32), pf_smem_bytes<N2, C>(), st>>>(q, map);
     return cudaGetLastError();
 }
 
@@ -147,6 +149,7 @@ struct PfOp {
     bool half;                  // tiles of C/2 columns (with a tensor map only)
     cudaStream_t st;
     bool attrs = false;
+    bool narrow = false;        // narrow bands: the single-row first stage (full tiles with a tensor map, N2 >= 512)
     template <int N2, int N1>
     cudaError_t run() {
         if constexpr (N2 >= 256 && N2 <= 1024) {
@@ -158,6 +161,10 @@ struct PfOp {
                 cudaError_t e = pf_attrs<N2, C, LG1, false>(a);
                 if (e == cudaSuccess) e = pf_attrs<N2, C, LG1, true>(b);
                 if (e == cudaSuccess) e = pf_attrs<N2, C / 2, LG1, true>(h);
+                if constexpr (N2 >= 512) {
+                    int d = 0;
+                    if (e == cudaSuccess) e = pf_attrs<N2, C, LG1, true, true>(d);
+                }
                 if (e != cudaSuccess) return e;
                 nb[0] = std::min(a, b);
                 nb[1] = h;
@@ -166,6 +173,9 @@ struct PfOp {
             const char *env = std::getenv("MFGB_P1TMA");   // "0": cp.async staging of W (comparisons)
             if (wmaps != nullptr && !(env && env[0] == '0')) {
                 if (half && nb[1] >= 1) return pf_launch<N2, N1, C / 2, true>(*p, wmaps[1], n_units, nb[1], st);
+                if constexpr (N2 >= 512) {
+                    if (narrow) return pf_launch<N2, N1, C, true, true>(*p, wmaps[0], n_units, nb[0], st);
+                }
                 return pf_launch<N2, N1, C, true>(*p, wmaps[0], n_units, nb[0], st);
             }
             CUtensorMap none;
@@ -238,10 +248,10 @@ bool make_w_tensor_maps(const float2 *W, int log2N, int log2N2, void *maps_out) 
 
 cudaError_t launch_pass1_pf(const SegDev &seg, const UnitInfo *units, int unit0, int n_units, int log2D,
                             int max_anc, const float4 *anchors, const float *anchors4, float2 *exch, bool half_tile,
-                            int *status, long long spin_limit, cudaStream_t st) {
+                            int *status, long long spin_limit, cudaStream_t st, bool narrow) {
     if (n_units <= 0) return cudaSuccess;
     Pass1PfParams p{seg.W, units, anchors, anchors4, exch, max_anc, log2D, seg.log2N, unit0, 0, status, spin_limit};
-    PfOp op{&p, (const CUtensorMap *)seg.w_tmap, n_units, half_tile, st};
+    PfOp op{&p, (const CUtensorMap *)seg.w_tmap, n_units, half_tile, st, false, narrow};
     return dispatch_split2(seg.log2N, seg.log2N2, op);
 }
 

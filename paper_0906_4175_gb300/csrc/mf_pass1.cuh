@@ -114,14 +114,34 @@ __device__ __forceinline__ void pf_issue(const Pass1PfParams &p, const CUtensorM
     }
 }
 
+// 32-point DFT X_q = sum_r v_r e^{2 pi i r q / 32} of a vector whose only
+// non-zero entry is x at r = rs < 16, given w = e^{2 pi i rs / 32}:
+// X_q = x w^q for q < 8 by a running product, then X_{q+8} = i^rs X_q and
+// X_{q+16} = (-1)^rs X_q, both exact.
+__device__ __forceinline__ void dft32_single(float2 *v, float2 x, int rs, float2 w) {
+    v[0] = x;
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v[q] = cmul(v[q - 1], w);
+    const int k = rs & 3;   // i^rs = c + i s
+    const float c = k == 0 ? 1.f : (k == 2 ? -1.f : 0.f), s = k == 1 ? 1.f : (k == 3 ? -1.f : 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q + 8] = make_float2(c * v[q].x - s * v[q].y, c * v[q].y + s * v[q].x);
+    const float sg = (rs & 1) ? -1.f : 1.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q + 16] = make_float2(sg * v[q].x, sg * v[q].y);
+}
+
 // Stage 1 of one column tile: template generation and weighting for this
 // thread's 16 rows n = t + 32 r of column k1 = tile C + seq (warps skip groups
 // of four rows outside every lane's band), the half-zero radix-32 DFT, and the
 // store into the sequence's shared-memory column sq.  Reads the staged W tile,
-// anchors and q4 terms.
-template <int L, int C, int LG1>
+// anchors and q4 terms.  NARROW (bands of a few rows, the chi^2 sub-bands):
+// where no lane of the warp holds more than one row of the band, the DFT is
+// dft32_single with w from the stage-1 table tw (exp(2 pi i r k / L), row L/64).
+template <int L, int C, int LG1, bool NARROW = false>
 __device__ __forceinline__ void pf_stage1(int tile, int seq, int t, int k_lo, int k_hi, int log2D,
-                                          const float2 *wbuf, const float4 *abuf, const float *abuf4, float2 *sq) {
+                                          const float2 *wbuf, const float4 *abuf, const float *abuf4, float2 *sq,
+                                          const float2 *tw = nullptr) {
     constexpr int T = L / 32;
     const int D = 1 << log2D;
     float2 v[32];
@@ -156,7 +176,19 @@ __device__ __forceinline__ void pf_stage1(int tile, int seq, int t, int k_lo, in
             for (int r = 4 * g; r < 4 * g + 4; ++r) v[r] = czero();
         }
     }
-    dft32_halfzero<+1>(v);
+    bool single = false;
+    if constexpr (NARROW) {
+        static_assert(L >= 512, "the row L/64 of the stage-1 table holds the 32nd roots for L >= 512");
+        single = __reduce_max_sync(0xffffffffu, (unsigned)(rhi > rlo ? rhi - rlo : 0)) <= 1u;
+        if (single) {
+            float2 x = v[0];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) x = cadd(x, v[r]);   // the one non-zero entry (or 0)
+            const int rs = min(rlo, 15);
+            dft32_single(v, x, rs, tw[(L / 64) * 32 + 2 * rs]);
+        }
+    }
+    if (!single) dft32_halfzero<+1>(v);
 #pragma unroll
     for (int r = 0; r < 32; ++r) sq[spad(32 * t + r)] = v[r];
 }
