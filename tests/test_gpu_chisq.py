@@ -121,9 +121,11 @@ def test_chisq_bench_segment_sampled(mf):
 
 
 def test_chisq_two_batches_at_2p20(mf):
-    """N = 2^20, p = 16: 9 templates make two batches of the rows kernel (7
-    templates' 17 exchanges fill the 1 GiB budget), every sample checked."""
-    wl = workloads.small(seed=2020, N=1 << 20, fs=4096.0, n_templates=9, m_lo=1.2, m_hi=6.0)
+    """N = 2^20, p = 16: 34 templates make two batches of the rows kernel (30
+    templates' 17 exchanges fill the 4 GiB default budget; the second batch of
+    4 runs its one pass-1 launch over all bands in under two waves), every
+    sample checked."""
+    wl = workloads.small(seed=2020, N=1 << 20, fs=4096.0, n_templates=34, m_lo=1.2, m_hi=6.0)
     _compare(mf, wl.m1, wl.m2, wl.segments[0], p=16)
 
 
