@@ -245,8 +245,9 @@ int mf_fft_c2c(const void *x, void *y, int64_t N, int64_t batch, int sign, void 
  * chisq: device FP32 [n][N] (row i for template tmpl[i]); edges: NULL or
  * device int64 [n][p+1] receiving b_0..b_p.  A template index outside the
  * bank gives an empty band (a zero row).  1 <= p <= 64, 1 <= n <= 2^24.
- * Cost: p + 1 inverse FFTs of length N per template (at N = 2^19, 2^20 their
- * second passes run as one kernel that sums the sub-bands in registers).
+ * Cost: p + 1 inverse FFTs of length N per template (at N = 2^19, 2^20 the
+ * first passes of a batch's p + 1 bands run as one launch and the second
+ * passes as one kernel that sums the sub-bands in registers).
  * Allocates scratch on cuda_stream (p + 1 exchanges of 8 N bytes per
  * template of a batch, batches sized to the bank's exchange budget: 4 GiB
  * unless mf_autotune chose another), so it cannot be captured in a graph, and
