@@ -57,6 +57,10 @@ for name, N, fs, nt, env in CASES:
         chi, edges = mf.chisq_series(bank, seg, torch.arange(2, dtype=torch.int32, device="cuda"), p=4)
         out["chisq"] = chi.cpu().numpy()
         out["edges"] = edges.cpu().numpy()
+    if name in ("n20_staged", "n19_fused"):   # p = 16: sub-bands narrow enough for the single-row first stage
+        chi, edges = mf.chisq_series(bank, seg, torch.arange(2, dtype=torch.int32, device="cuda"), p=16)
+        out[name + "_chisq16"] = chi.cpu().numpy()
+        out[name + "_edges16"] = edges.cpu().numpy()
 w = ctypes.c_uint32(); en = ctypes.c_int()
 assert L.mf_debug_status(ctypes.byref(w), ctypes.byref(en)) == 0
 out["status"] = np.array([w.value, en.value])
